@@ -1,0 +1,190 @@
+/*
+ * sac.h -- C ABI of the GB300 (sm_103a) library for face-staggered
+ * susceptibility artifact correction of EPI-MRI.
+ *
+ * The operations follow Macdonald & Ruthotto, "Efficient Numerical
+ * Optimization for Susceptibility Artifact Correction of EPI-MRI"
+ * (arXiv 1607.00531):
+ *   - the discrete problem  min J(b) = D(b) + alpha S(b)  s.t. -1 <= D1 b <= 1
+ *     on the face-staggered grid (Sec. 3, Eqs. D, S, discprob);
+ *   - its penalty form J_GN = J + P (Sec. 3, Eqs. P, JGN);
+ *   - ADMM on the split f(b) + g(z), b = z (Sec. 4.2, Eqs. fg, admmprob,
+ *     admmStep1-3, admmStop);
+ *   - inexact Gauss-Newton with block-Jacobi PCG (Sec. 4.1, Eqs. GNstep,
+ *     inexactGNsolve, Pblock, stopping1-3).
+ *
+ * Conventions (all entry points):
+ *   Layout.    Row-major arrays over the grid axes (axis 0 slowest).  Cell
+ *              arrays (the two images) have m[0] x m[1] (x m[2]) entries;
+ *              face arrays (b, z, u, gradients) have m[pe]+1 entries along
+ *              the phase-encoding axis pe and m[a] along the others.
+ *   Units.     h[a] is the voxel edge along axis a; b is a displacement in
+ *              the same length unit; the constraint |D1 b| <= 1 is unitless.
+ *   Images.    I1 is the image acquired with phase encoding +v (displaced by
+ *              +b), I2 the one acquired with -v (Sec. 2, Eq. reversedGradient).
+ *              Element type: double for SAC_F64, float for SAC_MIXED.
+ *   Memory.    Every array pointer is a DEVICE pointer owned by the caller
+ *              (the library never allocates, frees or retains it).  Scalars
+ *              returned through `double*`/`int*` outputs are HOST pointers.
+ *              `ws` is caller-owned device scratch of at least the size that
+ *              the matching *_workspace_bytes call returns, 256-byte aligned.
+ *   Streams.   `stream` is a cudaStream_t (NULL = legacy default stream).
+ *              Work is enqueued on it; calls that return host scalars
+ *              synchronise that stream before returning.
+ *   Errors.    A negative sac_status means the call failed; outputs are then
+ *              unspecified.  SAC_ENOTCONV (positive) means an iterative
+ *              solver stopped at its iteration cap: outputs are valid.
+ *   Threads.   Calls on different streams with different workspaces may run
+ *              concurrently.
+ *   Sizes.     m[pe] <= 479 (one warp holds one PE line in registers);
+ *              1 <= m[a] <= 4096 on the other axes.
+ */
+#ifndef SAC_H
+#define SAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAC_VERSION 1
+
+typedef enum {
+    SAC_OK = 0,
+    SAC_ENOTCONV = 1,      /* iteration cap reached; results valid */
+    SAC_EINVAL = -1,       /* bad grid, parameter, pointer or size */
+    SAC_ENOMEM = -2,       /* workspace too small / admission refused */
+    SAC_ECUDA = -3,        /* a CUDA runtime call failed */
+    SAC_EINFEASIBLE = -4,  /* starting field violates |D1 b| <= 1 */
+    SAC_ETIMEOUT = -5,     /* a bounded device wait gave up */
+    SAC_ENAN = -6,         /* non-finite value produced */
+    SAC_ELSFAIL = -7       /* GN line search found no acceptable step */
+} sac_status;
+
+typedef enum { SAC_F64 = 0, SAC_MIXED = 1 } sac_precision;
+
+/* Grid (Sec. 3): ndim in {2,3}; m[a] cells and h[a] voxel edge along axis a;
+   pe_axis is the 0-based phase-encoding axis.  Unused entries are ignored. */
+typedef struct {
+    int ndim;
+    int m[3];
+    double h[3];
+    int pe_axis;
+} sac_grid;
+
+/* Method parameters.  sac_params_default() fills the paper's values:
+   gamma = 1e-3 (Sec. 3), eta = 0.1, eps_obj = 1e-3, eps_iter = eps_grad = 1e-2,
+   max_gn = 10 (Sec. 4.1), eps_abs = eps_rel = 0.2 (Sec. 4.2), rho = 1e2,
+   beta = 10 (Sec. 5), alpha = 50. */
+typedef struct {
+    double alpha;        /* regularisation weight (Eq. discprob) */
+    double beta;         /* penalty weight (Eq. P); GN-PCG only */
+    double gamma;        /* Hessian shift (Eq. dJ) */
+    double rho;          /* ADMM augmentation (Eq. Lp) */
+    double eps_abs;      /* ADMM absolute tolerance (Eq. admmStop) */
+    double eps_rel;      /* ADMM relative tolerance */
+    double eta;          /* PCG forcing term (Eq. inexactGNsolve) */
+    double eps_obj, eps_iter, eps_grad;  /* GN stopping (Eqs. stopping1-3) */
+    double gn_rel_grad;  /* > 0: GN stops when ||grad|| <= gn_rel_grad ||grad(b0)|| */
+    int max_iter;        /* ADMM iteration cap */
+    int n_sqp;           /* SQP passes per b-step (>= 1) */
+    int max_pcg;         /* PCG iteration cap */
+    int precond;         /* 0 none, 1 Jacobi, 2 block-Jacobi (Eq. Pblock) */
+    int max_gn;          /* GN iteration cap */
+    int prec;            /* sac_precision */
+    double near_bound;   /* SAC_MIXED: lines with 1 - max|D1 b| < near_bound are
+                            re-solved in FP64 after the FP32 b-step */
+    int check_every;     /* ADMM: test the stopping rule every k iterations */
+    int reserved[3];
+} sac_params;
+
+void sac_params_default(sac_params* p);
+int sac_version(void);
+const char* sac_status_string(int status);
+
+/* Workspace for the single-volume entry points below. */
+size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p);
+
+/* Objective (Sec. 3, Eqs. D, S, P, JGN): out[0..3] = {J_GN, D, S, P} with
+   J_GN = D + alpha S + P; P = 0 when beta == 0 and +inf when beta > 0 and
+   some |D1 b| >= 1.  b: face array (double). */
+int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                  const double* b, double* out4, void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient of J_GN (Sec. 3: grad D = h^d J_r^T r, grad S = h^d sum_a D_a^T D_a b,
+   grad P = beta h^d D1^T phi'(D1 b)) into grad (face array, double). */
+int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                 const double* b, double* grad, void* ws, size_t ws_bytes, void* stream);
+
+/* One ADMM b-step (Sec. 4.2, Eq. admmStep1): per PE line, p->n_sqp SQP passes,
+   each a constrained Gauss-Newton step solved by the primal active-set method
+   (Eqs. qp, schurasqp).  b_in must satisfy |D1 b_in| <= 1.  b_out may equal
+   b_in.  *qp_capped (host, may be NULL) = 1 if some line's QP hit its pass cap. */
+int sac_bstep(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+              const double* b_in, const double* z, const double* u, double* b_out,
+              int* qp_capped, void* ws, size_t ws_bytes, void* stream);
+
+/* ADMM z-step and dual step (Sec. 4.2, Eqs. admmStep2-3, dctdiag):
+   z = C^T diag(rho/(alpha Lambda + rho)) C (b + u), u_out = u + b - z.
+   z is read as z^k (for the dual residual) and overwritten with z^{k+1};
+   u_out may equal u.  norms5 (host, may be NULL) = {||b - z^{k+1}||^2,
+   ||z^{k+1} - z^k||^2, ||b||^2, ||z^{k+1}||^2, ||u_out||^2}. */
+int sac_zstep(const sac_grid* g, const sac_params* p, const double* b, const double* u,
+              double* z, double* u_out, double* norms5, void* ws, size_t ws_bytes, void* stream);
+
+/* ADMM (Sec. 4.2).  b: in b^0 (feasible), out b^K.  z, u: in/out; pass NULL
+   to start from z^0 = b^0, u^0 = 0 (then they live in ws).  Stops when
+   ||b - z|| <= eps_pri and rho h^d ||z^k - z^{k+1}|| <= eps_dual (Eq.
+   admmStop, k+1 iterates) or after max_iter iterations.  hist (host, may be
+   NULL): 6 doubles per iteration {r_pri, r_dual, eps_pri, eps_dual, rho, 0}.
+   Returns SAC_OK (converged), SAC_ENOTCONV (cap) or an error. */
+int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                   double* b, double* z, double* u, int* iters, double* r_pri, double* r_dual,
+                   double* hist, void* ws, size_t ws_bytes, void* stream);
+
+/* Gauss-Newton Hessian-vector product (Sec. 3, Eq. dJGN):
+   out = [H_D(b) + alpha grad^2 S + grad^2 P(b) + gamma I] v.  Double arrays. */
+int sac_hessvec(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                const double* b, const double* v, double* out, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* Preconditioner solve out = P^{-1} rhs at b (Sec. 4.1): p->precond = 2:
+   block-Jacobi P_block = H_D + alpha h^d (D1^T D1 + M) + grad^2 P + gamma I
+   (Eq. Pblock, one tridiagonal system per PE line); 1: Jacobi diag(H); 0: none. */
+int sac_precond_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                      const double* b, const double* rhs, double* out, void* ws,
+                      size_t ws_bytes, void* stream);
+
+/* Inexact GN-PCG (Sec. 4.1) on J_GN from b (in: feasible b^0, out: result).
+   Armijo backtracking (c1 = 1e-4, halving, <= 10 trials, infeasible trial
+   points rejected).  Stops by Eqs. stopping1-3, or by gn_rel_grad when > 0.
+   hist (host, may be NULL): 5 doubles per GN iteration {J, ||grad||,
+   PCG iterations, PCG relative residual, step}. */
+int sac_gnpcg_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                    double* b, int* iters, double* J_out, double* gnorm, double* hist,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- tracing
+ * Instrumentation (not part of the method).  With profiling enabled, the ADMM
+ * driver brackets every kernel phase with CUDA events recorded on the stream
+ * it launches on; sac_profile_read returns, per phase, the summed device time
+ * in milliseconds and the number of launches since the last reset (it
+ * synchronises the recorded events).  Phases:
+ *   0 b-step (main precision)      1 b-step FP64 re-solve of near-bound lines
+ *   2 z-step pass 0 (DCT along the first non-PE axis, fused b + u)
+ *   3 z-step pass 1 (DCT along the second non-PE axis, spectral scaling)
+ *   4 z-step pass 2 (inverse DCT along the second non-PE axis)
+ *   5 z-step pass 3 (inverse DCT along the first non-PE axis, dual update,
+ *     residual-norm partial sums and their reduction)
+ * sac_launch_count returns the number of kernels this library has launched
+ * in the process so far. */
+#define SAC_NPHASES 6
+int sac_profile_enable(int on);
+int sac_profile_read(double* ms, long long* launches, int reset);
+long long sac_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAC_H */

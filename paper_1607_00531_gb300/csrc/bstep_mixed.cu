@@ -1,0 +1,13 @@
+// bstep_mixed.cu -- b-step computed in FP64 on FP32 storage: the re-solve of
+// lines near the invertibility bound in the mixed-precision path.
+#include "line_kernels.cuh"
+
+namespace sac {
+cudaError_t launch_bstep_mixed(const LineLaunch& L) { return launch_bstep_t<double, float>(L); }
+
+cudaError_t launch_bstep(int prec, const LineLaunch& L) {
+    if (prec == 0) return launch_bstep_f64(L);
+    if (prec == 1) return launch_bstep_f32(L);
+    return launch_bstep_mixed(L);
+}
+}  // namespace sac

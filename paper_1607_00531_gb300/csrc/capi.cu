@@ -1,0 +1,766 @@
+// capi.cu -- the C ABI (include/sac.h): argument checks, workspace layout,
+// and the host drivers of ADMM (Sec. 4.2) and GN-PCG (Sec. 4.1) around the
+// kernels.  Every step of the method runs in the kernels of this library.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "plan.h"
+
+namespace sac {
+
+// ---------------------------------------------------------------- instrumentation
+
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Per-phase device timers: CUDA events recorded on the launching stream
+// around each phase of the ADMM iteration.
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    struct Rec { cudaEvent_t a, b; int phase; };
+    std::vector<Rec> recs;        // recorded, not yet read
+    std::vector<cudaEvent_t> pool;
+    double ms[SAC_NPHASES] = {0};
+    long long n[SAC_NPHASES] = {0};
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void drain() {
+        for (auto& r : recs) {
+            float t = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+                ms[r.phase] += t;
+                n[r.phase] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+};
+static Profiler g_prof;
+
+struct PhaseScope {
+    cudaEvent_t a = nullptr;
+    cudaStream_t st;
+    int phase;
+    PhaseScope(int ph, cudaStream_t s) : st(s), phase(ph) {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (!g_prof.on) return;
+        if (g_prof.recs.size() > 4096) g_prof.drain();
+        a = g_prof.get();
+        cudaEventRecord(a, st);
+    }
+    ~PhaseScope() {
+        if (!a) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        cudaEvent_t b = g_prof.get();
+        cudaEventRecord(b, st);
+        g_prof.recs.push_back({a, b, phase});
+    }
+};
+
+#define SAC_CUDA(x)                                  \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return SAC_ECUDA;     \
+    } while (0)
+#define SAC_TRY(x)                                   \
+    do {                                             \
+        int s_ = (x);                                \
+        if (s_ < 0) return s_;                       \
+    } while (0)
+
+int make_geometry(const sac_grid* g, Geometry* G) {
+    if (!g || (g->ndim != 2 && g->ndim != 3)) return SAC_EINVAL;
+    if (g->pe_axis < 0 || g->pe_axis >= g->ndim) return SAC_EINVAL;
+    G->nd = g->ndim;
+    G->pe = g->pe_axis;
+    G->hd = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        G->M[a] = (a < g->ndim) ? g->m[a] : 1;
+        G->h[a] = (a < g->ndim) ? g->h[a] : 1.0;
+        if (G->M[a] < 1 || G->M[a] > 4096) return SAC_EINVAL;
+        if (!(G->h[a] > 0) || !isfinite(G->h[a])) return SAC_EINVAL;
+        if (a < g->ndim) G->hd *= G->h[a];
+        G->F[a] = G->M[a] + (a == G->pe ? 1 : 0);
+    }
+    G->mpe = G->M[G->pe];
+    if (faces_per_lane(G->mpe) == 0) return SAC_EINVAL;
+    G->hpe = G->h[G->pe];
+    G->n_outer = 1;
+    G->n_inner = 1;
+    for (int a = 0; a < G->pe; ++a) G->n_outer *= G->M[a];
+    for (int a = G->pe + 1; a < 3; ++a) G->n_inner *= G->M[a];
+    int k = 0, ax[2] = {0, 0};
+    for (int a = 0; a < 3; ++a)
+        if (a != G->pe) ax[k++] = a;
+    G->ax1 = ax[0];
+    G->ax2 = ax[1];
+    G->nf = (long long)G->F[0] * G->F[1] * G->F[2];
+    G->nc = (long long)G->M[0] * G->M[1] * G->M[2];
+    return SAC_OK;
+}
+
+int check_params(const sac_params* p) {
+    if (!p) return SAC_EINVAL;
+    if (!(p->alpha >= 0) || !(p->rho > 0) || !(p->beta >= 0) || !(p->gamma >= 0)) return SAC_EINVAL;
+    if (!(p->eps_abs >= 0) || !(p->eps_rel >= 0) || !(p->eta > 0)) return SAC_EINVAL;
+    if (p->n_sqp < 1 || p->n_sqp > 64 || p->max_iter < 0 || p->max_pcg < 0 || p->max_gn < 0) return SAC_EINVAL;
+    if (p->precond < 0 || p->precond > 2) return SAC_EINVAL;
+    if (p->prec != SAC_F64 && p->prec != SAC_MIXED) return SAC_EINVAL;
+    if (!(p->near_bound >= 0)) return SAC_EINVAL;
+    return SAC_OK;
+}
+
+void dct2_matrix(int L, double* C) {
+    for (int k = 0; k < L; ++k) {
+        const double s = (k == 0) ? sqrt(1.0 / L) : sqrt(2.0 / L);
+        for (int j = 0; j < L; ++j) {
+            // angle pi k (2j+1) / (2L), reduced exactly modulo 2 pi
+            const long long num = ((long long)k * (2 * j + 1)) % (4LL * L);
+            C[(size_t)k * L + j] = s * cos(M_PI * (double)num / (2.0 * L));
+        }
+    }
+}
+
+void neumann_eigs(int L, double h, double* lam) {
+    for (int k = 0; k < L; ++k) {
+        const double s = sin(M_PI * (double)k / (2.0 * L));
+        lam[k] = (L < 2) ? 0.0 : 4.0 / (h * h) * s * s;
+    }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
+    memset(P, 0, sizeof(*P));
+    SAC_TRY(make_geometry(g, &P->G));
+    SAC_TRY(check_params(p));
+    const Geometry& G = P->G;
+    P->prec = p->prec;
+    P->K = faces_per_lane(G.mpe);
+    // lines per CTA: 8, fewer when the staged tile would not fit
+    const size_t ssz = (p->prec == SAC_MIXED) ? 4 : 8;
+    int W = 8;
+    for (;;) {
+        int RL = smem_row(G.mpe + 1, W, 8);
+        size_t need = line_smem_bstep(W, RL, RL, 8, ssz);
+        if (need <= 200 * 1024 || W == 1) break;
+        W >>= 1;
+    }
+    P->W = W;
+    P->RLf = smem_row(G.mpe + 1, W, 8);
+    P->line_tiles = line_tiles(G.n_outer, G.n_inner, W);
+    const int axes[4] = {G.ax1, G.ax2, G.ax2, G.ax1};
+    for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
+    P->elem_blocks = (G.nf + 255) / 256;
+    const long long nlines = (long long)G.n_outer * G.n_inner;
+    P->rcap = (int)(nlines < (1 << 20) ? nlines : (1 << 20));
+    long long np = 4 * P->line_tiles;
+    if (5 * P->pass_tiles[3] > np) np = 5 * P->pass_tiles[3];
+    if (P->elem_blocks > np) np = P->elem_blocks;
+    if (2 * 1216 > np) np = 2 * 1216;
+    P->n_part = np;
+    const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+    // carve
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    size_t o_job = take(sizeof(Job));
+    size_t o_pref = take(sizeof(long long) * 2 * 6);
+    size_t o_stat = take(256);
+    size_t o_out = take(sizeof(double) * 64);
+    size_t o_rlist = take(sizeof(unsigned long long) * (size_t)P->rcap);
+    size_t o_part = take(sizeof(double) * (size_t)np);
+    size_t o_C1 = take(sizeof(double) * (size_t)L1 * L1);
+    size_t o_C2 = take(sizeof(double) * (size_t)L2 * L2);
+    size_t o_C1f = take(sizeof(float) * (size_t)L1 * L1);
+    size_t o_C2f = take(sizeof(float) * (size_t)L2 * L2);
+    size_t o_l1 = take(sizeof(double) * (size_t)L1);
+    size_t o_l2 = take(sizeof(double) * (size_t)L2);
+    size_t o_arr[10];
+    for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
+    P->bytes = off;
+    if (!ws) return SAC_OK;
+    if (((uintptr_t)ws) & 255) return SAC_EINVAL;
+    char* base = (char*)ws;
+    P->d_job = (Job*)(base + o_job);
+    long long* pref = (long long*)(base + o_pref);
+    P->d_pref_line = pref;
+    for (int q = 0; q < 4; ++q) P->d_pref_pass[q] = pref + 2 * (1 + q);
+    P->d_pref_elem = pref + 10;
+    P->d_status = (int*)(base + o_stat);
+    P->d_rcount = P->d_status + 1;
+    P->d_out = (double*)(base + o_out);
+    P->d_rlist = (unsigned long long*)(base + o_rlist);
+    P->d_part = (double*)(base + o_part);
+    P->d_C1 = (double*)(base + o_C1);
+    P->d_C2 = (double*)(base + o_C2);
+    P->d_C1f = (float*)(base + o_C1f);
+    P->d_C2f = (float*)(base + o_C2f);
+    P->d_lam1 = (double*)(base + o_l1);
+    P->d_lam2 = (double*)(base + o_l2);
+    for (int i = 0; i < 10; ++i) P->arr[i] = (double*)(base + o_arr[i]);
+    return SAC_OK;
+}
+
+int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, void* b, void* z, void* u, void* t1,
+                void* t2, cudaStream_t st) {
+    const Geometry& G = P->G;
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.nd = G.nd; J.pe = G.pe;
+    for (int a = 0; a < 3; ++a) { J.M[a] = G.M[a]; J.F[a] = G.F[a]; J.h[a] = G.h[a]; }
+    J.ax1 = G.ax1; J.ax2 = G.ax2;
+    J.nf = G.nf; J.nc = G.nc;
+    J.n_outer = G.n_outer; J.mpe = G.mpe; J.n_inner = G.n_inner;
+    J.hd = G.hd; J.hpe = G.hpe;
+    J.alpha = p->alpha; J.rho = p->rho; J.beta = p->beta; J.gamma = p->gamma;
+    J.I1 = I1; J.I2 = I2; J.b = b; J.z = z; J.u = u; J.t1 = t1; J.t2 = t2;
+    const bool f32 = (p->prec == SAC_MIXED);
+    J.C1 = f32 ? (const void*)P->d_C1f : (const void*)P->d_C1;
+    J.C2 = f32 ? (const void*)P->d_C2f : (const void*)P->d_C2;
+    J.lam1 = P->d_lam1; J.lam2 = P->d_lam2;
+    J.part = P->d_part;
+    J.active = 1;
+    long long pref[12] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
+                          0, P->pass_tiles[3], 0, P->elem_blocks};
+    SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
+    const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+    std::vector<double> C1((size_t)L1 * L1), C2((size_t)L2 * L2), l1(L1), l2(L2);
+    dct2_matrix(L1, C1.data());
+    dct2_matrix(L2, C2.data());
+    neumann_eigs(L1, G.h[G.ax1], l1.data());
+    neumann_eigs(L2, G.h[G.ax2], l2.data());
+    std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end());
+    SAC_CUDA(cudaMemcpyAsync(P->d_C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C1f, C1f.data(), C1f.size() * 4, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C2f, C2f.data(), C2f.size() * 4, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_lam1, l1.data(), l1.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_lam2, l2.data(), l2.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemsetAsync(P->d_status, 0, 256, st));
+    // the host copies above read pageable memory: the runtime has consumed it on return
+    return SAC_OK;
+}
+
+LineLaunch plan_line_launch(const Plan* P, int n_sqp, double near_bound, cudaStream_t st) {
+    LineLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.jobs = P->d_job;
+    L.njobs = 1;
+    L.prefix = P->d_pref_line;
+    L.total_tiles = P->line_tiles;
+    L.W = P->W;
+    L.K = P->K;
+    L.RLc = P->RLf;
+    L.RLf = P->RLf;
+    L.n_sqp = n_sqp;
+    L.near_bound = near_bound;
+    L.mode = 0;
+    L.rlist = P->d_rlist;
+    L.rcount = P->d_rcount;
+    L.rlist_out = P->d_rlist;
+    L.rcount_out = P->d_rcount;
+    L.rcap = P->rcap;
+    L.list_blocks = (P->rcap + P->W - 1) / P->W;
+    L.status = P->d_status;
+    L.stream = st;
+    return L;
+}
+
+// ---------------------------------------------------------------- helpers
+
+static int read_back(void* host, const void* dev, size_t bytes, cudaStream_t st) {
+    SAC_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
+    SAC_CUDA(cudaStreamSynchronize(st));
+    return SAC_OK;
+}
+
+static int status_of(const Plan& P, cudaStream_t st, int* qp_capped) {
+    int s[2] = {0, 0};
+    SAC_TRY(read_back(s, P.d_status, sizeof(s), st));
+    if (qp_capped) *qp_capped = (s[0] & kStQpCap) ? 1 : 0;
+    if (s[0] & kStNaN) return SAC_ENAN;
+    return SAC_OK;
+}
+
+struct Ws {
+    void* ws;
+    size_t bytes;
+};
+
+static int setup(const sac_grid* g, const sac_params* p, void* ws, size_t ws_bytes, Plan* P) {
+    if (!ws) return SAC_EINVAL;
+    SAC_TRY(plan_layout(g, p, ws, P));
+    if (ws_bytes < P->bytes) return SAC_ENOMEM;
+    return SAC_OK;
+}
+
+// objective pieces at b (double, device): out4 = {J, D, S, P}
+static int objective_dev(Plan& P, const sac_params* p, const double* b, double* out4, cudaStream_t st) {
+    LineLaunch L = plan_line_launch(&P, 1, 0.0, st);
+    const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
+    SAC_CUDA(launch_line_eval(prec, L, 1, b, nullptr, nullptr, P.d_part));
+    SAC_CUDA(launch_reduce(P.d_part, (int)P.line_tiles, 4, P.d_out, st));
+    SAC_CUDA(launch_cross_lap(P.d_job, 1, P.d_pref_elem, P.elem_blocks, b, nullptr, 0.0, 0, P.d_part, st));
+    SAC_CUDA(launch_reduce(P.d_part, (int)P.elem_blocks, 1, P.d_out + 4, st));
+    double s[5];
+    SAC_TRY(read_back(s, P.d_out, sizeof(s), st));
+    const double hd = P.G.hd;
+    const double D = 0.5 * hd * s[0];
+    const double S = 0.5 * hd * (s[1] + s[4]);
+    double Pen = 0.0;
+    if (p->beta > 0) Pen = (s[3] > 0) ? INFINITY : p->beta * hd * s[2];
+    out4[0] = D + p->alpha * S + Pen;
+    out4[1] = D;
+    out4[2] = S;
+    out4[3] = Pen;
+    return SAC_OK;
+}
+
+static int gradient_dev(Plan& P, const sac_params* p, const double* b, double* grad, cudaStream_t st) {
+    LineLaunch L = plan_line_launch(&P, 1, 0.0, st);
+    const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
+    SAC_CUDA(launch_line_eval(prec, L, 2, b, grad, nullptr, nullptr));
+    SAC_CUDA(launch_cross_lap(P.d_job, 1, P.d_pref_elem, P.elem_blocks, b, grad, p->alpha * P.G.hd, 1, nullptr, st));
+    return SAC_OK;
+}
+
+static int linearize_dev(Plan& P, const double* b, double* diag, double* off, cudaStream_t st) {
+    LineLaunch L = plan_line_launch(&P, 1, 0.0, st);
+    const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
+    SAC_CUDA(launch_line_eval(prec, L, 4, b, diag, off, nullptr));
+    return SAC_OK;
+}
+
+static int dot_dev(Plan& P, const double* x, const double* y, double* out, cudaStream_t st) {
+    SAC_CUDA(launch_dot2(P.G.nf, x, y, nullptr, P.d_part, 1216, st));
+    SAC_CUDA(launch_reduce(P.d_part, 1216, 2, P.d_out + 8, st));
+    double s[2];
+    SAC_TRY(read_back(s, P.d_out + 8, sizeof(s), st));
+    *out = s[0];
+    return SAC_OK;
+}
+
+static int max_abs_d1_dev(Plan& P, const double* b, double* out, cudaStream_t st) {
+    SAC_CUDA(launch_max_abs_d1(P.d_job, 1, P.d_pref_elem, P.elem_blocks, b, P.d_part, st));
+    SAC_CUDA(launch_reduce(P.d_part, (int)P.elem_blocks, -1, P.d_out + 12, st));
+    SAC_TRY(read_back(out, P.d_out + 12, sizeof(double), st));
+    return SAC_OK;
+}
+
+// z-step passes on the plan's job (arrays already bound in the job)
+static int zstep_passes(Plan& P, cudaStream_t st) {
+    const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
+    for (int q = 0; q < 4; ++q) {
+        PhaseScope ps(2 + q, st);
+        AxisLaunch A;
+        A.jobs = P.d_job;
+        A.njobs = 1;
+        A.prefix = P.d_pref_pass[q];
+        A.total_tiles = P.pass_tiles[q];
+        A.pass = q;
+        A.prec = prec;
+        A.part = P.d_part;
+        A.stream = st;
+        SAC_CUDA(launch_axis_pass(A));
+        if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
+    }
+    return SAC_OK;
+}
+
+// b-step on the plan's job; mixed: FP32 pass then FP64 re-solve of near-bound lines
+static int bstep_dev(Plan& P, const sac_params* p, cudaStream_t st) {
+    if (P.prec == SAC_MIXED) {
+        SAC_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int), st));
+        LineLaunch L = plan_line_launch(&P, p->n_sqp, p->near_bound, st);
+        {
+            PhaseScope ps(0, st);
+            SAC_CUDA(launch_bstep(1, L));
+        }
+        if (p->near_bound > 0) {
+            PhaseScope ps(1, st);
+            L.mode = 1;
+            L.near_bound = 0.0;
+            SAC_CUDA(launch_bstep(2, L));
+        }
+    } else {
+        PhaseScope ps(0, st);
+        LineLaunch L = plan_line_launch(&P, p->n_sqp, 0.0, st);
+        SAC_CUDA(launch_bstep(0, L));
+    }
+    return SAC_OK;
+}
+
+}  // namespace sac
+
+using namespace sac;
+
+extern "C" {
+
+void sac_params_default(sac_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->alpha = 50.0;
+    p->beta = 10.0;
+    p->gamma = 1e-3;
+    p->rho = 1e2;
+    p->eps_abs = 0.2;
+    p->eps_rel = 0.2;
+    p->eta = 0.1;
+    p->eps_obj = 1e-3;
+    p->eps_iter = 1e-2;
+    p->eps_grad = 1e-2;
+    p->gn_rel_grad = 0.0;
+    p->max_iter = 50;
+    p->n_sqp = 1;
+    p->max_pcg = 50;
+    p->precond = 2;
+    p->max_gn = 10;
+    p->prec = SAC_F64;
+    p->near_bound = 1e-3;
+    p->check_every = 1;
+}
+
+int sac_version(void) { return SAC_VERSION; }
+
+int sac_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = on != 0;
+    return SAC_OK;
+}
+
+int sac_profile_read(double* ms, long long* launches, int reset) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.drain();
+    for (int i = 0; i < SAC_NPHASES; ++i) {
+        if (ms) ms[i] = g_prof.ms[i];
+        if (launches) launches[i] = g_prof.n[i];
+        if (reset) { g_prof.ms[i] = 0.0; g_prof.n[i] = 0; }
+    }
+    return SAC_OK;
+}
+
+long long sac_launch_count(void) { return g_launches.load(); }
+
+const char* sac_status_string(int s) {
+    switch (s) {
+        case SAC_OK: return "ok";
+        case SAC_ENOTCONV: return "iteration cap reached";
+        case SAC_EINVAL: return "invalid argument";
+        case SAC_ENOMEM: return "workspace too small";
+        case SAC_ECUDA: return "CUDA error";
+        case SAC_EINFEASIBLE: return "infeasible starting field";
+        case SAC_ETIMEOUT: return "bounded wait expired";
+        case SAC_ENAN: return "non-finite value";
+        case SAC_ELSFAIL: return "line search failed";
+        default: return "unknown status";
+    }
+}
+
+size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p) {
+    Plan P;
+    if (plan_layout(g, p, nullptr, &P) != SAC_OK) return 0;
+    return P.bytes;
+}
+
+int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
+                  double* out4, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b || !out4) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, (void*)b, nullptr, nullptr, nullptr, nullptr, st));
+    SAC_TRY(objective_dev(P, p, b, out4, st));
+    return status_of(P, st, nullptr);
+}
+
+int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
+                 double* grad, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b || !grad) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, (void*)b, nullptr, nullptr, nullptr, nullptr, st));
+    SAC_TRY(gradient_dev(P, p, b, grad, st));
+    return status_of(P, st, nullptr);
+}
+
+int sac_bstep(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b_in,
+              const double* z, const double* u, double* b_out, int* qp_capped, void* ws, size_t ws_bytes,
+              void* stream) {
+    if (!I1 || !I2 || !b_in || !z || !u || !b_out) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    const long long nf = P.G.nf;
+    if (P.prec == SAC_MIXED) {
+        float* bf = (float*)P.arr[0];
+        float* zf = (float*)P.arr[1];
+        float* uf = (float*)P.arr[2];
+        SAC_CUDA(launch_cast(nf, b_in, bf, st));
+        SAC_CUDA(launch_cast(nf, z, zf, st));
+        SAC_CUDA(launch_cast(nf, u, uf, st));
+        SAC_TRY(plan_upload(&P, p, I1, I2, bf, zf, uf, nullptr, nullptr, st));
+        SAC_TRY(bstep_dev(P, p, st));
+        SAC_CUDA(launch_cast_back(nf, bf, b_out, st));
+    } else {
+        if (b_out != b_in) SAC_CUDA(cudaMemcpyAsync(b_out, b_in, nf * 8, cudaMemcpyDeviceToDevice, st));
+        SAC_TRY(plan_upload(&P, p, I1, I2, b_out, (void*)z, (void*)u, nullptr, nullptr, st));
+        SAC_TRY(bstep_dev(P, p, st));
+    }
+    return status_of(P, st, qp_capped);
+}
+
+int sac_zstep(const sac_grid* g, const sac_params* p, const double* b, const double* u, double* z, double* u_out,
+              double* norms5, void* ws, size_t ws_bytes, void* stream) {
+    if (!b || !u || !z || !u_out) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    const long long nf = P.G.nf;
+    if (P.prec == SAC_MIXED) {
+        float* bf = (float*)P.arr[0];
+        float* zf = (float*)P.arr[1];
+        float* uf = (float*)P.arr[2];
+        SAC_CUDA(launch_cast(nf, b, bf, st));
+        SAC_CUDA(launch_cast(nf, z, zf, st));
+        SAC_CUDA(launch_cast(nf, u, uf, st));
+        SAC_TRY(plan_upload(&P, p, nullptr, nullptr, bf, zf, uf, P.arr[3], P.arr[4], st));
+        SAC_TRY(zstep_passes(P, st));
+        SAC_CUDA(launch_cast_back(nf, zf, z, st));
+        SAC_CUDA(launch_cast_back(nf, uf, u_out, st));
+    } else {
+        if (u_out != u) SAC_CUDA(cudaMemcpyAsync(u_out, u, nf * 8, cudaMemcpyDeviceToDevice, st));
+        SAC_TRY(plan_upload(&P, p, nullptr, nullptr, (void*)b, z, u_out, P.arr[3], P.arr[4], st));
+        SAC_TRY(zstep_passes(P, st));
+    }
+    double s[5];
+    SAC_TRY(read_back(s, P.d_out + 16, sizeof(s), st));
+    if (norms5) memcpy(norms5, s, sizeof(s));
+    return status_of(P, st, nullptr);
+}
+
+int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, double* b, double* z,
+                   double* u, int* iters, double* r_pri, double* r_dual, double* hist, void* ws, size_t ws_bytes,
+                   void* stream) {
+    if (!I1 || !I2 || !b) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    const long long nf = P.G.nf;
+    // feasibility of b^0 (the set C of Eq. admmprob)
+    SAC_TRY(plan_upload(&P, p, I1, I2, b, nullptr, nullptr, nullptr, nullptr, st));
+    double mx = 0.0;
+    SAC_TRY(max_abs_d1_dev(P, b, &mx, st));
+    if (!(mx <= 1.0)) return SAC_EINFEASIBLE;
+    double* zd = z ? z : P.arr[5];
+    double* ud = u ? u : P.arr[6];
+    if (!z) SAC_CUDA(cudaMemcpyAsync(zd, b, nf * 8, cudaMemcpyDeviceToDevice, st));
+    if (!u) SAC_CUDA(cudaMemsetAsync(ud, 0, nf * 8, st));
+    const bool mixed = (P.prec == SAC_MIXED);
+    float *bf = nullptr, *zf = nullptr, *uf = nullptr;
+    if (mixed) {
+        bf = (float*)P.arr[0];
+        zf = (float*)P.arr[1];
+        uf = (float*)P.arr[2];
+        SAC_CUDA(launch_cast(nf, b, bf, st));
+        SAC_CUDA(launch_cast(nf, zd, zf, st));
+        SAC_CUDA(launch_cast(nf, ud, uf, st));
+        SAC_TRY(plan_upload(&P, p, I1, I2, bf, zf, uf, P.arr[3], P.arr[4], st));
+    } else {
+        SAC_TRY(plan_upload(&P, p, I1, I2, b, zd, ud, P.arr[3], P.arr[4], st));
+    }
+    const double sqn = sqrt((double)nf), rhd = p->rho * P.G.hd;
+    const int every = p->check_every > 0 ? p->check_every : 1;
+    int k = 0, conv = 0;
+    double rp = 0.0, rd = 0.0;
+    for (k = 0; k < p->max_iter;) {
+        SAC_TRY(bstep_dev(P, p, st));
+        SAC_TRY(zstep_passes(P, st));
+        ++k;
+        if (k % every == 0 || k == p->max_iter) {
+            double s[5];
+            SAC_TRY(read_back(s, P.d_out + 16, sizeof(s), st));
+            rp = sqrt(s[0]);
+            rd = rhd * sqrt(s[1]);
+            const double nb = sqrt(s[2]), nz = sqrt(s[3]), nu = sqrt(s[4]);
+            const double ep = sqn * p->eps_abs + p->eps_rel * (nb > nz ? nb : nz);
+            const double ed = sqn * p->eps_abs + p->eps_rel * rhd * nu;
+            if (hist) {
+                double* hk = hist + 6 * (k - 1);
+                hk[0] = rp; hk[1] = rd; hk[2] = ep; hk[3] = ed; hk[4] = p->rho; hk[5] = 0.0;
+            }
+            if (!(rp == rp) || !(rd == rd)) return SAC_ENAN;
+            if (rp <= ep && rd <= ed) { conv = 1; break; }
+        }
+    }
+    if (mixed) {
+        SAC_CUDA(launch_cast_back(nf, bf, b, st));
+        SAC_CUDA(launch_cast_back(nf, zf, zd, st));
+        SAC_CUDA(launch_cast_back(nf, uf, ud, st));
+    }
+    if (iters) *iters = k;
+    if (r_pri) *r_pri = rp;
+    if (r_dual) *r_dual = rd;
+    SAC_TRY(status_of(P, st, nullptr));
+    return conv ? SAC_OK : SAC_ENOTCONV;
+}
+
+int sac_hessvec(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
+                const double* v, double* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b || !v || !out) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, (void*)b, nullptr, nullptr, nullptr, nullptr, st));
+    SAC_TRY(linearize_dev(P, b, P.arr[0], P.arr[1], st));
+    SAC_CUDA(launch_hessvec(P.d_job, 1, P.d_pref_elem, P.elem_blocks, P.arr[0], P.arr[1], v, out, nullptr, st));
+    return status_of(P, st, nullptr);
+}
+
+int sac_precond_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
+                      const double* rhs, double* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b || !rhs || !out) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, (void*)b, nullptr, nullptr, nullptr, nullptr, st));
+    if (p->precond == 0) {
+        SAC_CUDA(cudaMemcpyAsync(out, rhs, P.G.nf * 8, cudaMemcpyDeviceToDevice, st));
+        return status_of(P, st, nullptr);
+    }
+    SAC_TRY(linearize_dev(P, b, P.arr[0], P.arr[1], st));
+    LineLaunch L = plan_line_launch(&P, 1, 0.0, st);
+    SAC_CUDA(launch_line_solve(L, p->precond, P.arr[0], P.arr[1], rhs, out));
+    return status_of(P, st, nullptr);
+}
+
+int sac_gnpcg_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, double* b, int* iters,
+                    double* J_out, double* gnorm, double* hist, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, b, nullptr, nullptr, nullptr, nullptr, st));
+    const long long nf = P.G.nf;
+    double* diag = P.arr[0];
+    double* off = P.arr[1];
+    double* grad = P.arr[2];
+    double* d = P.arr[3];
+    double* r = P.arr[4];
+    double* pv = P.arr[5];
+    double* q = P.arr[6];
+    double* zz = P.arr[7];
+    double* bt = P.arr[8];
+    double* zero = P.arr[9];
+    SAC_CUDA(cudaMemsetAsync(zero, 0, nf * 8, st));
+    double o4[4];
+    SAC_TRY(objective_dev(P, p, zero, o4, st));
+    const double J0 = o4[0];
+    SAC_TRY(objective_dev(P, p, b, o4, st));
+    double Jk = o4[0];
+    if (!isfinite(Jk)) return SAC_EINFEASIBLE;
+    SAC_TRY(gradient_dev(P, p, b, grad, st));
+    double gg;
+    SAC_TRY(dot_dev(P, grad, grad, &gg, st));
+    double gk = sqrt(gg);
+    const double g0 = gk;
+    LineLaunch L = plan_line_launch(&P, 1, 0.0, st);
+    int k = 0, conv = 0, status = SAC_OK;
+    for (k = 0; k < p->max_gn;) {
+        // PCG on H d = -grad (Eq. inexactGNsolve), d^0 = 0
+        SAC_TRY(linearize_dev(P, b, diag, off, st));
+        SAC_CUDA(cudaMemsetAsync(d, 0, nf * 8, st));
+        SAC_CUDA(launch_axpby(nf, -1.0, grad, 0.0, nullptr, r, st));
+        int pits = 0;
+        double rel = 1.0;
+        if (gk > 0) {
+            if (p->precond == 0) SAC_CUDA(cudaMemcpyAsync(zz, r, nf * 8, cudaMemcpyDeviceToDevice, st));
+            else SAC_CUDA(launch_line_solve(L, p->precond, diag, off, r, zz));
+            SAC_CUDA(cudaMemcpyAsync(pv, zz, nf * 8, cudaMemcpyDeviceToDevice, st));
+            double rz;
+            SAC_TRY(dot_dev(P, r, zz, &rz, st));
+            while (pits < p->max_pcg) {
+                SAC_CUDA(launch_hessvec(P.d_job, 1, P.d_pref_elem, P.elem_blocks, diag, off, pv, q, P.d_part, st));
+                SAC_CUDA(launch_reduce(P.d_part, (int)P.elem_blocks, 1, P.d_out + 24, st));
+                double pq;
+                SAC_TRY(read_back(&pq, P.d_out + 24, sizeof(double), st));
+                const double al = rz / pq;
+                SAC_CUDA(launch_axpby(nf, 1.0, d, al, pv, d, st));
+                SAC_CUDA(launch_axpby(nf, 1.0, r, -al, q, r, st));
+                ++pits;
+                double rr;
+                SAC_TRY(dot_dev(P, r, r, &rr, st));
+                rel = sqrt(rr) / gk;
+                if (rel <= p->eta) break;
+                if (p->precond == 0) SAC_CUDA(cudaMemcpyAsync(zz, r, nf * 8, cudaMemcpyDeviceToDevice, st));
+                else SAC_CUDA(launch_line_solve(L, p->precond, diag, off, r, zz));
+                double rz2;
+                SAC_TRY(dot_dev(P, r, zz, &rz2, st));
+                const double be = rz2 / rz;
+                rz = rz2;
+                SAC_CUDA(launch_axpby(nf, 1.0, zz, be, pv, pv, st));
+            }
+        } else {
+            rel = 0.0;
+        }
+        // Armijo backtracking
+        double slope;
+        SAC_TRY(dot_dev(P, grad, d, &slope, st));
+        double lam = 1.0, Jt = INFINITY;
+        int ok = 0;
+        for (int tr = 0; tr < 10; ++tr) {
+            SAC_CUDA(launch_axpby(nf, 1.0, b, lam, d, bt, st));
+            SAC_TRY(objective_dev(P, p, bt, o4, st));
+            Jt = o4[0];
+            if (isfinite(Jt) && Jt <= Jk + 1e-4 * lam * slope) { ok = 1; break; }
+            lam *= 0.5;
+        }
+        if (!ok) { status = SAC_ELSFAIL; break; }
+        // ||b_new - b|| = lam ||d||
+        double dd;
+        SAC_TRY(dot_dev(P, d, d, &dd, st));
+        double bb;
+        SAC_TRY(dot_dev(P, b, b, &bb, st));
+        const double dstep = lam * sqrt(dd), nbk = sqrt(bb);
+        SAC_CUDA(cudaMemcpyAsync(b, bt, nf * 8, cudaMemcpyDeviceToDevice, st));
+        const double Jprev = Jk;
+        Jk = Jt;
+        SAC_TRY(gradient_dev(P, p, b, grad, st));
+        SAC_TRY(dot_dev(P, grad, grad, &gg, st));
+        gk = sqrt(gg);
+        if (hist) {
+            double* hk = hist + 5 * k;
+            hk[0] = Jk; hk[1] = gk; hk[2] = pits; hk[3] = rel; hk[4] = lam;
+        }
+        ++k;
+        if (p->gn_rel_grad > 0) {
+            if (gk <= p->gn_rel_grad * g0) { conv = 1; break; }
+        } else {
+            const bool c1 = fabs(Jk - Jprev) <= p->eps_obj * (1.0 + fabs(J0));
+            const bool c2 = dstep <= p->eps_iter * (1.0 + nbk);
+            const bool c3 = gk <= p->eps_grad * (1.0 + fabs(J0));
+            if (c1 && c2 && c3) { conv = 1; break; }
+        }
+    }
+    if (iters) *iters = k;
+    if (J_out) *J_out = Jk;
+    if (gnorm) *gnorm = gk;
+    SAC_TRY(status_of(P, st, nullptr));
+    if (status < 0) return status;
+    return conv ? SAC_OK : SAC_ENOTCONV;
+}
+
+}  // extern "C"

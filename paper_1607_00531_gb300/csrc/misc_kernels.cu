@@ -1,0 +1,259 @@
+// misc_kernels.cu -- elementwise, stencil and reduction kernels (FP64):
+//   * k_cross_lap   s * (D2^T D2 + D3^T D3) v  and  ||D2 v||^2 + ||D3 v||^2
+//                   partial sums (Sec. 3, Eqs. S, d2d3): the cross-line part
+//                   of the regulariser, a Neumann Laplacian over the non-PE axes;
+//   * k_hessvec     H_JGN v from the line blocks of H (diagonal + coupling
+//                   along PE) plus alpha h^d (D2^T D2 + D3^T D3) v (Eq. dJGN),
+//                   with the partial sums of v^T H v for PCG;
+//   * reductions in a fixed order (deterministic), vector updates, casts.
+#include "sac_dev.cuh"
+#include "sac_launch.h"
+
+namespace sac {
+
+__device__ __forceinline__ void face_idx(const Job& J, long long f, int (&idx)[3]) {
+    idx[2] = (int)(f % J.F[2]);
+    long long q = f / J.F[2];
+    idx[1] = (int)(q % J.F[1]);
+    idx[0] = (int)(q / J.F[1]);
+}
+__device__ __forceinline__ long long face_stride(const Job& J, int a) {
+    return a == 0 ? (long long)J.F[1] * J.F[2] : (a == 1 ? (long long)J.F[2] : 1ll);
+}
+
+// cross-line Laplacian at face f (sum over the non-PE axes of length >= 2)
+__device__ __forceinline__ double cross_lap_at(const Job& J, const double* __restrict__ v, long long f,
+                                               const int (&idx)[3], double& sq) {
+    double acc = 0.0;
+    const double vf = v[f];
+    sq = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int a = q ? J.ax2 : J.ax1;
+        if (J.F[a] < 2) continue;
+        const double ih2 = 1.0 / (J.h[a] * J.h[a]);
+        const long long s = face_stride(J, a);
+        if (idx[a] > 0) acc += (vf - v[f - s]) * ih2;
+        if (idx[a] < J.F[a] - 1) {
+            const double vn = v[f + s];
+            acc += (vf - vn) * ih2;
+            const double d = (vn - vf) / J.h[a];
+            sq += d * d;
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) k_cross_lap(const Job* __restrict__ jobs, int njobs,
+                                                   const long long* __restrict__ prefix,
+                                                   const double* __restrict__ v, double* __restrict__ out,
+                                                   double scale, int accumulate, double* __restrict__ part) {
+    __shared__ double red[32];
+    const long long t = blockIdx.x;
+    if (t >= prefix[njobs]) return;
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    const long long f = (t - prefix[jid]) * 256 + threadIdx.x;
+    double sq = 0.0;
+    if (f < J.nf) {
+        int idx[3];
+        face_idx(J, f, idx);
+        const double lap = cross_lap_at(J, v, f, idx, sq);
+        if (out) out[f] = (accumulate ? out[f] : 0.0) + scale * lap;
+    }
+    if (part) {
+        double acc[1] = {sq};
+        block_sum<1>(acc, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_hessvec(const Job* __restrict__ jobs, int njobs,
+                                                 const long long* __restrict__ prefix,
+                                                 const double* __restrict__ diag, const double* __restrict__ off,
+                                                 const double* __restrict__ v, double* __restrict__ out,
+                                                 double* __restrict__ part) {
+    __shared__ double red[32];
+    const long long t = blockIdx.x;
+    if (t >= prefix[njobs]) return;
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    const long long f = (t - prefix[jid]) * 256 + threadIdx.x;
+    double vhv = 0.0;
+    if (f < J.nf) {
+        int idx[3];
+        face_idx(J, f, idx);
+        const long long s = face_stride(J, J.pe);
+        const int ip = idx[J.pe];
+        double y = diag[f] * v[f];
+        if (ip > 0) y += off[f - s] * v[f - s];
+        if (ip < J.mpe) y += off[f] * v[f + s];
+        double sq;
+        y += J.alpha * J.hd * cross_lap_at(J, v, f, idx, sq);
+        out[f] = y;
+        vhv = v[f] * y;
+    }
+    if (part) {
+        double acc[1] = {vhv};
+        block_sum<1>(acc, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+    }
+}
+
+// largest |D1 b| of the cells of a job (per-block maxima)
+__global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs, int njobs,
+                                                    const long long* __restrict__ prefix,
+                                                    const double* __restrict__ b, double* __restrict__ part) {
+    __shared__ double red[32];
+    const long long t = blockIdx.x;
+    if (t >= prefix[njobs]) return;
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    const long long f = (t - prefix[jid]) * 256 + threadIdx.x;
+    double mx = 0.0;
+    if (f < J.nf) {
+        int idx[3];
+        face_idx(J, f, idx);
+        if (idx[J.pe] < J.mpe) {
+            const long long s = face_stride(J, J.pe);
+            const double d = fabs(b[f + s] - b[f]) / J.hpe;
+            mx = (d == d) ? d : INFINITY;
+        }
+    }
+    mx = warp_max(mx);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    if (wid == 0) {
+        mx = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        mx = warp_max(mx);
+        if (lane == 0) part[blockIdx.x] = mx;
+    }
+}
+
+// out[c] = sum over p of part[p * ncomp + c] (ncomp <= 8), fixed order.
+// ncomp < 0: maximum of the |ncomp| = 1 component instead of the sum.
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part, int nparts, int ncomp,
+                                                double* __restrict__ out) {
+    __shared__ double red[32 * 8];
+    const bool is_max = ncomp < 0;
+    const int nc = is_max ? 1 : ncomp;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+        for (int c = 0; c < nc; ++c) {
+            const double v = part[(long long)p * nc + c];
+            acc[c] = is_max ? fmax(acc[c], v) : acc[c] + v;
+        }
+    if (is_max) {
+        double m = warp_max(acc[0]);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) red[wid] = m;
+        __syncthreads();
+        if (wid == 0) {
+            m = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+            m = warp_max(m);
+            if (lane == 0) out[0] = m;
+        }
+        return;
+    }
+    block_sum<8>(acc, red);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < nc; ++c) out[c] = acc[c];
+}
+
+// out may alias x or y (element-wise, same index)
+__global__ void k_axpby(long long n, double a, const double* x, double b, const double* y, double* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+// partial sums of x.y (and y.z when z != NULL) with a fixed grid
+__global__ void __launch_bounds__(256) k_dot2(long long n, const double* __restrict__ x,
+                                              const double* __restrict__ y, const double* __restrict__ z,
+                                              double* __restrict__ part) {
+    __shared__ double red[64];
+    double acc[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        acc[0] += x[i] * y[i];
+        if (z) acc[1] += y[i] * z[i];
+    }
+    block_sum<2>(acc, red);
+    if (threadIdx.x == 0) { part[blockIdx.x * 2] = acc[0]; part[blockIdx.x * 2 + 1] = acc[1]; }
+}
+
+__global__ void k_cast(long long n, const double* __restrict__ s, float* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = (float)s[i];
+}
+__global__ void k_cast_back(long long n, const float* __restrict__ s, double* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = (double)s[i];
+}
+__global__ void k_fill(long long n, double v, double* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = v;
+}
+
+static unsigned grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_cross_lap(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                             const double* v, double* out, double scale, int accumulate, double* part,
+                             cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    count_launch();
+    k_cross_lap<<<(unsigned)total_blocks, 256, 0, st>>>(jobs, njobs, prefix, v, out, scale, accumulate, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_hessvec(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                           const double* diag, const double* off, const double* v, double* out, double* part,
+                           cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    count_launch();
+    k_hessvec<<<(unsigned)total_blocks, 256, 0, st>>>(jobs, njobs, prefix, diag, off, v, out, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                              const double* b, double* part, cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    count_launch();
+    k_max_abs_d1<<<(unsigned)total_blocks, 256, 0, st>>>(jobs, njobs, prefix, b, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce(const double* part, int nparts, int ncomp, double* out, cudaStream_t st) {
+    count_launch();
+    k_reduce<<<1, 256, 0, st>>>(part, nparts, ncomp, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_axpby(long long n, double a, const double* x, double b, const double* y, double* out,
+                         cudaStream_t st) {
+    count_launch();
+    k_axpby<<<grid_for(n), 256, 0, st>>>(n, a, x, b, y, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_dot2(long long n, const double* x, const double* y, const double* z, double* part,
+                        int nblocks, cudaStream_t st) {
+    count_launch();
+    k_dot2<<<nblocks, 256, 0, st>>>(n, x, y, z, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_cast(long long n, const double* src, float* dst, cudaStream_t st) {
+    count_launch();
+    k_cast<<<grid_for(n), 256, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_cast_back(long long n, const float* src, double* dst, cudaStream_t st) {
+    count_launch();
+    k_cast_back<<<grid_for(n), 256, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill(long long n, double v, double* dst, cudaStream_t st) {
+    count_launch();
+    k_fill<<<grid_for(n), 256, 0, st>>>(n, v, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace sac

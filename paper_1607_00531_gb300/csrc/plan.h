@@ -1,0 +1,65 @@
+// plan.h -- host-side plan of one volume: validated grid, kernel launch
+// shapes, and the carving of the caller's workspace.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sac.h"
+#include "sac_dev.cuh"
+#include "sac_launch.h"
+
+namespace sac {
+
+struct Geometry {
+    int nd, pe;
+    int M[3], F[3];
+    int ax1, ax2;
+    long long nf, nc;
+    int n_outer, mpe, n_inner;
+    double h[3], hd, hpe;
+};
+
+// validate a grid; returns SAC_OK or SAC_EINVAL
+int make_geometry(const sac_grid* g, Geometry* out);
+int check_params(const sac_params* p);
+
+// DCT-II matrix (orthonormal) and the eigenvalues of the Neumann difference
+// operator it diagonalises (Sec. 4.2, Eq. dctdiag), computed on the host.
+void dct2_matrix(int L, double* C);
+void neumann_eigs(int L, double h, double* lam);
+
+// Device-side layout of a workspace for one volume.
+struct Plan {
+    Geometry G;
+    int prec;                 // SAC_F64 / SAC_MIXED
+    int W, K, RLf;            // line kernels: lines per CTA, faces per lane, smem row
+    long long line_tiles, pass_tiles[4], elem_blocks;
+    int rcap;
+    // device pointers inside ws
+    Job* d_job;
+    long long* d_pref_line;
+    long long* d_pref_pass[4];
+    long long* d_pref_elem;
+    int* d_status;
+    int* d_rcount;
+    unsigned long long* d_rlist;
+    double* d_out;            // 64 doubles of reduction results
+    double* d_part;
+    long long n_part;
+    double *d_C1, *d_C2, *d_lam1, *d_lam2;
+    float *d_C1f, *d_C2f;
+    double* arr[10];          // face-sized scratch arrays (8 bytes per face each)
+    size_t bytes;             // total workspace bytes used
+};
+
+// plan layout; with ws == NULL only computes plan->bytes
+int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* plan);
+// upload the job descriptor, prefixes and DCT tables (stream-ordered)
+int plan_upload(Plan* plan, const sac_params* p, const void* I1, const void* I2, void* b, void* z, void* u,
+                void* t1, void* t2, cudaStream_t st);
+// line-launch description for this plan
+LineLaunch plan_line_launch(const Plan* plan, int n_sqp, double near_bound, cudaStream_t st);
+
+}  // namespace sac

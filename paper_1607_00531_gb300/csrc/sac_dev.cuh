@@ -1,0 +1,307 @@
+// sac_dev.cuh -- device-side building blocks shared by the SAC kernels.
+//
+// Everything here is written for one warp per phase-encoding (PE) line:
+// lane L owns the K consecutive faces L*K .. L*K+K-1 of its line (and the
+// cells of the same indices), so that a line of up to 32*K faces lives in
+// registers.  K is odd so that lane-strided shared-memory accesses are
+// bank-conflict free.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sac {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Status bits written by kernels (atomicOr into a device word).
+enum : int { kStQpCap = 1, kStNaN = 2, kStInfeasible = 4, kStTimeout = 8 };
+
+// One volume (job) as the kernels see it.  All pointers are device pointers;
+// element types are fixed by the launching code (float or double).
+struct Job {
+    // grid
+    int nd, pe;
+    int M[3];          // cells per axis (1 on the unused third axis in 2D)
+    int F[3];          // faces per axis (M, plus one along pe)
+    int ax1, ax2;      // the two non-PE axes (ax2 may have length 1)
+    long long nf, nc;  // number of faces / cells
+    int n_outer, mpe, n_inner;   // line view (outer, PE, inner)
+    double h[3], hd, hpe;
+    // parameters
+    double alpha, rho, beta, gamma;
+    // data
+    const void* I1;
+    const void* I2;
+    void* b;
+    void* z;
+    void* u;
+    void* t1;          // z-step scratch (faces)
+    void* t2;          // z-step scratch (faces)
+    const void* C1;    // DCT-II matrix along ax1 (F[ax1]^2, storage type)
+    const void* C2;    // DCT-II matrix along ax2
+    const double* lam1;  // eigenvalues 4/h^2 sin^2(pi k / (2 m)) along ax1
+    const double* lam2;
+    double* part;      // per-block partial sums of this job
+    int active;        // 0: tiles of this job return at once
+    int pad_;
+};
+
+// ---------------------------------------------------------------- job lookup
+
+// prefix[j] = first tile of job j, prefix[njobs] = total tiles.
+__device__ __forceinline__ int find_job(const long long* __restrict__ prefix, int njobs, long long t) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- warp utilities
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, d));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, d));
+    return v;
+}
+// minimum value, ties broken by the lowest index
+template <typename T>
+__device__ __forceinline__ void warp_argmin(T& v, int& idx) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        T ov = __shfl_xor_sync(kFull, v, d);
+        int oi = __shfl_xor_sync(kFull, idx, d);
+        if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+}
+__device__ __forceinline__ int warp_incl_scan_int(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+// value of the previous lane (0 on lane 0) / next lane (0 on lane 31)
+template <typename T>
+__device__ __forceinline__ T from_prev(T v) {
+    T o = __shfl_up_sync(kFull, v, 1);
+    return (threadIdx.x & 31) ? o : T(0);
+}
+template <typename T>
+__device__ __forceinline__ T from_next(T v) {
+    T o = __shfl_down_sync(kFull, v, 1);
+    return ((threadIdx.x & 31) != 31) ? o : T(0);
+}
+
+// Segmented inclusive prefix sum over the warp's 32*K elements (lane-major,
+// K per lane); a set flag starts a new segment at that element.
+template <typename T, int K>
+__device__ __forceinline__ void seg_incl_scan(T (&v)[K], const bool (&flag)[K]) {
+    const int lane = threadIdx.x & 31;
+    bool any = false;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (flag[k]) { acc = v[k]; any = true; } else { acc += v[k]; }
+        v[k] = acc;
+    }
+    int f = any ? 1 : 0;
+    T s = acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int fo = __shfl_up_sync(kFull, f, d);
+        T so = __shfl_up_sync(kFull, s, d);
+        if (lane >= d) {
+            if (!f) s = so + s;
+            f |= fo;
+        }
+    }
+    T carry = from_prev(s);
+    bool open = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (flag[k]) open = false;
+        if (open) v[k] += carry;
+    }
+}
+
+// ---------------------------------------------------------------- tridiagonal solve
+//
+// Solves a_i x_{i-1} + d_i x_i + c_i x_{i+1} = r_i for the warp's 32*K rows
+// (row i = lane*K + k), solution returned in r.  Rows beyond the system are
+// identity rows (d = 1, a = c = r = 0) and the last real row has c = 0.
+//
+// Method (partitioned elimination + parallel cyclic reduction):
+//  1. each lane eliminates its interior rows so that every interior unknown
+//     is expressed through the lane's first and last unknowns;
+//  2. the 64 first/last unknowns form a tridiagonal system, solved by PCR
+//     across lanes with shuffles (6 steps);
+//  3. each lane back-substitutes its interior unknowns.
+// Without pivoting: the systems here are symmetric positive definite.
+template <typename T, int K>
+__device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[K], T (&r)[K]) {
+    static_assert(K >= 3, "need at least 3 rows per lane");
+    const int lane = threadIdx.x & 31;
+    // forward: rows 0 and 1 normalised; row i >= 2 rewritten as
+    // x_i + a_i x_0 + c_i x_{i+1} = r_i
+    {
+        T inv = T(1) / d[0];
+        a[0] *= inv; c[0] *= inv; r[0] *= inv;
+        inv = T(1) / d[1];
+        a[1] *= inv; c[1] *= inv; r[1] *= inv;
+    }
+#pragma unroll
+    for (int i = 2; i < K; ++i) {
+        T inv = T(1) / (d[i] - a[i] * c[i - 1]);
+        r[i] = (r[i] - a[i] * r[i - 1]) * inv;
+        c[i] = c[i] * inv;
+        a[i] = -a[i] * a[i - 1] * inv;
+    }
+    // backward: rows K-3 .. 1 rewritten as x_i + a_i x_0 + c_i x_{K-1} = r_i
+#pragma unroll
+    for (int i = K - 3; i >= 1; --i) {
+        r[i] -= c[i] * r[i + 1];
+        a[i] -= c[i] * a[i + 1];
+        c[i] = -c[i] * c[i + 1];
+    }
+    // row 0: x_0 + a_0 x_{prev last} + c_0 x_{K-1} = r_0
+    {
+        T inv = T(1) / (T(1) - c[0] * a[1]);
+        r[0] = (r[0] - c[0] * r[1]) * inv;
+        c[0] = -c[0] * c[1] * inv;
+        a[0] = a[0] * inv;
+    }
+    // reduced system: row 2L (x_0 of lane L), row 2L+1 (x_{K-1} of lane L)
+    T eA = a[0], eB = T(1), eC = c[0], eR = r[0];
+    T oA = a[K - 1], oB = T(1), oC = c[K - 1], oR = r[K - 1];
+    // PCR, stride 1 (neighbours of 2L: 2L-1 = prev lane odd, 2L+1 = own odd;
+    // of 2L+1: 2L = own even, 2L+2 = next lane even)
+    {
+        T pA = __shfl_up_sync(kFull, oA, 1), pB = __shfl_up_sync(kFull, oB, 1);
+        T pC = __shfl_up_sync(kFull, oC, 1), pR = __shfl_up_sync(kFull, oR, 1);
+        T nA = __shfl_down_sync(kFull, eA, 1), nB = __shfl_down_sync(kFull, eB, 1);
+        T nC = __shfl_down_sync(kFull, eC, 1), nR = __shfl_down_sync(kFull, eR, 1);
+        if (lane == 0) { pA = 0; pB = 1; pC = 0; pR = 0; }
+        if (lane == 31) { nA = 0; nB = 1; nC = 0; nR = 0; }
+        // even row
+        T k1 = eA / pB, k2 = eC / oB;
+        T neA = -k1 * pA, neC = -k2 * oC;
+        T neB = eB - k1 * pC - k2 * oA;
+        T neR = eR - k1 * pR - k2 * oR;
+        // odd row
+        T k3 = oA / eB, k4 = oC / nB;
+        T noA = -k3 * eA, noC = -k4 * nC;
+        T noB = oB - k3 * eC - k4 * nA;
+        T noR = oR - k3 * eR - k4 * nR;
+        eA = neA; eB = neB; eC = neC; eR = neR;
+        oA = noA; oB = noB; oC = noC; oR = noR;
+    }
+    // strides 2, 4, 8, 16, 32 rows = 1, 2, 4, 8, 16 lanes
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        T peA = __shfl_up_sync(kFull, eA, s), peB = __shfl_up_sync(kFull, eB, s);
+        T peC = __shfl_up_sync(kFull, eC, s), peR = __shfl_up_sync(kFull, eR, s);
+        T poA = __shfl_up_sync(kFull, oA, s), poB = __shfl_up_sync(kFull, oB, s);
+        T poC = __shfl_up_sync(kFull, oC, s), poR = __shfl_up_sync(kFull, oR, s);
+        T neA = __shfl_down_sync(kFull, eA, s), neB = __shfl_down_sync(kFull, eB, s);
+        T neC = __shfl_down_sync(kFull, eC, s), neR = __shfl_down_sync(kFull, eR, s);
+        T noA = __shfl_down_sync(kFull, oA, s), noB = __shfl_down_sync(kFull, oB, s);
+        T noC = __shfl_down_sync(kFull, oC, s), noR = __shfl_down_sync(kFull, oR, s);
+        if (lane < s) { peA = 0; peB = 1; peC = 0; peR = 0; poA = 0; poB = 1; poC = 0; poR = 0; }
+        if (lane + s > 31) { neA = 0; neB = 1; neC = 0; neR = 0; noA = 0; noB = 1; noC = 0; noR = 0; }
+        T k1 = eA / peB, k2 = eC / neB;
+        T xA = -k1 * peA, xC = -k2 * neC;
+        T xB = eB - k1 * peC - k2 * neA;
+        T xR = eR - k1 * peR - k2 * neR;
+        T k3 = oA / poB, k4 = oC / noB;
+        T yA = -k3 * poA, yC = -k4 * noC;
+        T yB = oB - k3 * poC - k4 * noA;
+        T yR = oR - k3 * poR - k4 * noR;
+        eA = xA; eB = xB; eC = xC; eR = xR;
+        oA = yA; oB = yB; oC = yC; oR = yR;
+    }
+    T x0 = eR / eB, xl = oR / oB;
+    r[0] = x0;
+    r[K - 1] = xl;
+#pragma unroll
+    for (int i = 1; i < K - 1; ++i) r[i] = r[i] - a[i] * x0 - c[i] * xl;
+}
+
+// ---------------------------------------------------------------- image model
+//
+// 1D linear interpolation of the m cell-centred samples of a PE line in index
+// units t = x/h - 1/2: through (k, I[k]) for k = 0..m-1 and through zero at
+// k = -1 and k = m, zero outside [-1, m]; slope of [floor(t), floor(t)+1].
+// Returns value and dI/dt.
+template <typename T, typename S>
+__device__ __forceinline__ void interp_line(const S* __restrict__ row, int m, T t, T& v, T& dv) {
+    T fl = floor(t);
+    if (!(fl >= T(-1)) || !(fl <= T(m - 1))) { v = T(0); dv = T(0); return; }
+    int k = (int)fl;
+    T f = t - fl;
+    T left = (k >= 0) ? T(row[k]) : T(0);
+    T right = (k + 1 <= m - 1) ? T(row[k + 1]) : T(0);
+    v = (T(1) - f) * left + f * right;
+    dv = right - left;
+}
+
+// ---------------------------------------------------------------- penalty phi (Eqs. P, dphi)
+template <typename T>
+__device__ __forceinline__ T phi_val(T x) {
+    T s = T(1) - x * x;
+    return x * x * x * x / s;
+}
+template <typename T>
+__device__ __forceinline__ T phi_d1(T x) {
+    T s = T(1) - x * x;
+    return (T(4) * x * x * x - T(2) * x * x * x * x * x) / (s * s);
+}
+template <typename T>
+__device__ __forceinline__ T phi_d2(T x) {
+    T s = T(1) - x * x;
+    T x2 = x * x;
+    return T(2) * x2 * (x2 * x2 - T(3) * x2 + T(6)) / (s * s * s);
+}
+
+// ---------------------------------------------------------------- block reduction of a few doubles
+// Sums v[0..N) over the block; thread 0 receives the totals in v.  Uses
+// `scratch` (>= 32*N doubles of shared memory).
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = warp_sum(v[c]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) scratch[wid * N + c] = v[c];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = (lane < nw) ? scratch[lane * N + c] : 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = warp_sum(v[c]);
+    }
+    __syncthreads();
+}
+
+}  // namespace sac

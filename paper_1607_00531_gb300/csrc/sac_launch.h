@@ -1,0 +1,105 @@
+// sac_launch.h -- host-side launch interface between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace sac {
+
+struct Job;
+
+// number of kernels launched by this library (instrumentation)
+void count_launch(long long n = 1);
+
+// Launch description of a line kernel (one warp per PE line, W lines per CTA).
+struct LineLaunch {
+    const Job* jobs;             // device array of jobs
+    int njobs;
+    const long long* prefix;     // device: first tile of each job, [njobs] = total
+    long long total_tiles;       // host copy of prefix[njobs]
+    int W, K, RLc, RLf;          // lines per CTA, faces per lane, smem row lengths
+    int n_sqp;
+    double near_bound;
+    int mode;                    // b-step: 0 tiles, 1 listed lines
+    const unsigned long long* rlist;
+    const int* rcount;
+    unsigned long long* rlist_out;
+    int* rcount_out;
+    int rcap;
+    long long list_blocks;       // grid size in mode 1
+    int* status;
+    cudaStream_t stream;
+};
+
+// faces per lane for a line of m cells (m + 1 faces); 0 if too long
+inline int faces_per_lane(int m) {
+    const int need = (m + 1 + 31) / 32;
+    if (need <= 3) return 3;
+    if (need <= 5) return 5;
+    if (need <= 9) return 9;
+    if (need <= 15) return 15;
+    return 0;
+}
+// shared-memory row length for `len` entries, padded so that the staging
+// writes of W lines are spread over the banks
+inline int smem_row(int len, int W, size_t elem) {
+    const int words = (elem == 8) ? 16 : 32;
+    int r = ((len + words - 1) / words) * words;
+    int pad = words / (W < words ? W : words);
+    return r + (pad > 0 ? pad : 1);
+}
+inline size_t line_smem_bstep(int W, int RLc, int RLf, size_t tsz, size_t ssz) {
+    return (size_t)W * 3 * RLf * tsz + (size_t)W * (2 * RLc + 3 * RLf) * ssz;
+}
+inline size_t line_smem_eval(int W, int RLc, int RLf, size_t ssz) {
+    return 128 * sizeof(double) + (size_t)W * 2 * RLc * ssz + 8 + (size_t)W * RLf * sizeof(double);
+}
+inline long long line_tiles(int n_outer, int n_inner, int W) {
+    if (n_inner > 1) return (long long)n_outer * ((n_inner + W - 1) / W);
+    return (n_outer + W - 1) / W;
+}
+
+// prec: 0 FP64, 1 FP32, 2 FP64 compute on FP32 storage
+cudaError_t launch_bstep(int prec, const LineLaunch& L);
+cudaError_t launch_bstep_f64(const LineLaunch& L);
+cudaError_t launch_bstep_f32(const LineLaunch& L);
+cudaError_t launch_bstep_mixed(const LineLaunch& L);
+cudaError_t launch_line_eval(int prec, const LineLaunch& L, int what, const double* bsrc, double* out0,
+                             double* out1, double* part);
+cudaError_t launch_line_solve(const LineLaunch& L, int precond, const double* diag, const double* off,
+                              const double* rhs, double* out);
+
+// ---- z-step (dense per-axis DCT passes)
+struct AxisLaunch {
+    const Job* jobs;
+    int njobs;
+    const long long* prefix;    // tiles per job for this pass
+    long long total_tiles;
+    int pass;                   // see zstep_kernels.cu
+    int prec;                   // 0 FP64, 1 FP32
+    double* part;               // pass 3: 5 partial sums per CTA
+    cudaStream_t stream;
+};
+cudaError_t launch_axis_pass(const AxisLaunch& A);
+// tiles of one pass for a job with face dims F, non-PE axes ax1/ax2
+long long axis_pass_tiles(const int F[3], int axis);
+
+// ---- elementwise / stencil kernels (FP64)
+cudaError_t launch_cross_lap(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                             const double* v, double* out, double scale, int accumulate, double* part,
+                             cudaStream_t st);
+cudaError_t launch_hessvec(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                           const double* diag, const double* off, const double* v, double* out, double* part,
+                           cudaStream_t st);
+cudaError_t launch_reduce(const double* part, int nparts, int ncomp, double* out, cudaStream_t st);
+cudaError_t launch_axpby(long long n, double a, const double* x, double b, const double* y, double* out,
+                         cudaStream_t st);
+cudaError_t launch_dot2(long long n, const double* x, const double* y, const double* z, double* part,
+                        int nblocks, cudaStream_t st);
+cudaError_t launch_cast(long long n, const double* src, float* dst, cudaStream_t st);
+cudaError_t launch_cast_back(long long n, const float* src, double* dst, cudaStream_t st);
+cudaError_t launch_fill(long long n, double v, double* dst, cudaStream_t st);
+cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                              const double* b, double* part, cudaStream_t st);
+
+}  // namespace sac

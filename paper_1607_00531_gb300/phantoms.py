@@ -69,7 +69,7 @@ WORKLOADS = {
     # 3D, 256 x 256 x 80 (5 263 360 faces), 20 ellipsoids, Rician 0.02, up to 8 px, 0.9.
     "3d_256x256x80": Workload("3d_256x256x80", (256, 256, 80), 1, 20, 8, 8.0, 0.9, sigma=0.02,
                               rician=True, unit_range=True, alpha=50.0, seed=3,
-                              bump_width=(0.03, 0.12)),
+                              bump_width=(0.012, 0.04)),
 }
 
 
@@ -164,12 +164,28 @@ class _Field:
         self.scale = 1.0
 
     def val_and_dpe(self, X):
-        v = np.zeros(X.shape[:-1])
-        dv = np.zeros(X.shape[:-1])
+        return self.along_pe(X[..., self.pe], self.cross_factors(X))
+
+    def cross_factors(self, X):
+        """Per bump, the factor of the Gaussian that does not depend on the PE
+        coordinate (fixed along a PE line)."""
+        out = []
         for c, w, s in zip(self.c, self.w, self.s):
-            e = s * np.exp(-0.5 * np.sum(((X - c) / w) ** 2, axis=-1))
+            q = np.zeros(X.shape[:-1])
+            for a in range(X.shape[-1]):
+                if a != self.pe:
+                    q += ((X[..., a] - c[a]) / w) ** 2
+            out.append(s * np.exp(-0.5 * q))
+        return out
+
+    def along_pe(self, xpe, fac):
+        v = np.zeros(xpe.shape)
+        dv = np.zeros(xpe.shape)
+        for c, w, f in zip(self.c, self.w, fac):
+            t = (xpe - c[self.pe]) / w
+            e = f * np.exp(-0.5 * t * t)
             v += e
-            dv += e * (-(X[..., self.pe] - c[self.pe]) / (w * w))
+            dv -= e * t / w
         return self.scale * v, self.scale * dv
 
 
@@ -193,19 +209,18 @@ def _invert(field: _Field, X, sign, bmax):
     lo, hi = y - bmax - 1e-12, y + bmax + 1e-12
     Z = X.copy()
     x = y.copy()
+    fac = field.cross_factors(X)
+    tol = 4e-16 * (1.0 + np.max(np.abs(y)))
     for _ in range(60):
-        Z[..., pe] = x
-        b, db = field.val_and_dpe(Z)
+        b, db = field.along_pe(x, fac)
         F = x + sign * b - y
+        if np.max(np.abs(F)) <= tol:
+            break
         lo = np.where(F < 0, x, lo)
         hi = np.where(F >= 0, x, hi)
         xn = x - F / (1.0 + sign * db)
-        bad = ~((xn > lo) & (xn < hi))
-        xn = np.where(bad, 0.5 * (lo + hi), xn)
-        if np.max(np.abs(xn - x)) < 1e-15:
-            x = xn
-            break
-        x = xn
+        bad = ~((xn >= lo) & (xn <= hi))
+        x = np.where(bad, 0.5 * (lo + hi), xn)
     Z[..., pe] = x
     return Z
 

@@ -1,0 +1,287 @@
+"""ctypes binding of ``libsac.so`` (include/sac.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays are torch CUDA tensors (device memory and streams come
+from PyTorch); results are written in place or returned as tensors.  There is
+no fallback: if the library is missing or the GPU is absent the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsac.so")
+HEADER = os.path.join(_HERE, "..", "include", "sac.h")
+
+SAC_OK, SAC_ENOTCONV = 0, 1
+SAC_EINVAL, SAC_ENOMEM, SAC_ECUDA, SAC_EINFEASIBLE = -1, -2, -3, -4
+SAC_ETIMEOUT, SAC_ENAN, SAC_ELSFAIL = -5, -6, -7
+SAC_F64, SAC_MIXED = 0, 1
+
+
+class SacGrid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("m", ctypes.c_int * 3), ("h", ctypes.c_double * 3),
+                ("pe_axis", ctypes.c_int)]
+
+
+class SacParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("alpha", "beta", "gamma", "rho", "eps_abs", "eps_rel", "eta", "eps_obj", "eps_iter",
+                 "eps_grad", "gn_rel_grad")] + \
+               [(n, ctypes.c_int) for n in ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "prec")] + \
+               [("near_bound", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+class SacError(RuntimeError):
+    def __init__(self, name, status):
+        super().__init__(f"{name} failed with status {status} ({status_string(status)})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libsac.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1607_00531_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_size_t
+        G, P = ctypes.POINTER(SacGrid), ctypes.POINTER(SacParams)
+        sig = {
+            "sac_params_default": (None, [P]),
+            "sac_version": (ctypes.c_int, []),
+            "sac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "sac_workspace_bytes": (sz, [G, P]),
+            "sac_objective": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp, sz, vp]),
+            "sac_gradient": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, sz, vp]),
+            "sac_bstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]),
+            "sac_zstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, dp, vp, sz, vp]),
+            "sac_admm_solve": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, ip, dp, dp, dp, vp, sz, vp]),
+            "sac_hessvec": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "sac_precond_solve": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "sac_gnpcg_solve": (ctypes.c_int, [G, P, vp, vp, vp, ip, dp, dp, dp, vp, sz, vp]),
+            "sac_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+            "sac_profile_read": (ctypes.c_int, [dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+            "sac_launch_count": (ctypes.c_longlong, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_symbols():
+    """Function names declared in include/sac.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sac_[a-z0-9_]+)\s*\(", txt)))
+
+
+def status_string(st):
+    return lib().sac_status_string(int(st)).decode()
+
+
+def grid(m, h, pe):
+    g = SacGrid()
+    g.ndim = len(m)
+    for a in range(3):
+        g.m[a] = int(m[a]) if a < len(m) else 1
+        g.h[a] = float(h[a]) if a < len(m) else 1.0
+    g.pe_axis = int(pe)
+    return g
+
+
+def params(**kw):
+    p = SacParams()
+    lib().sac_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = {"f64": SAC_F64, "mixed": SAC_MIXED}[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def face_shape(g):
+    return tuple(g.m[a] + (1 if a == g.pe_axis else 0) for a in range(g.ndim))
+
+
+def cell_shape(g):
+    return tuple(g.m[a] for a in range(g.ndim))
+
+
+def workspace_bytes(g, p):
+    return int(lib().sac_workspace_bytes(ctypes.byref(g), ctypes.byref(p)))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def workspace(g, p, device="cuda"):
+    torch = _torch()
+    n = workspace_bytes(g, p)
+    if n == 0:
+        raise SacError("sac_workspace_bytes", SAC_EINVAL)
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("arrays must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("arrays must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(name, st, allow_notconv=True):
+    if st < 0 or (st == SAC_ENOTCONV and not allow_notconv):
+        raise SacError(name, st)
+    return st
+
+
+def _img_dtype(p):
+    torch = _torch()
+    return torch.float32 if p.prec == SAC_MIXED else torch.float64
+
+
+def _check_inputs(g, p, I1, I2):
+    torch = _torch()
+    for I in (I1, I2):
+        if tuple(I.shape) != cell_shape(g) or I.dtype != _img_dtype(p):
+            raise ValueError(f"image must be {cell_shape(g)} {_img_dtype(p)}, got {tuple(I.shape)} {I.dtype}")
+
+
+def _ws(g, p, ws):
+    return ws if ws is not None else workspace(g, p)
+
+
+def objective(g, p, I1, I2, b, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    out = (ctypes.c_double * 4)()
+    _check("sac_objective", lib().sac_objective(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), out,
+                                                _ptr(ws), ws.numel(), _stream(stream)))
+    return dict(J=out[0], D=out[1], S=out[2], P=out[3])
+
+
+def gradient(g, p, I1, I2, b, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    out = _torch().empty_like(b)
+    _check("sac_gradient", lib().sac_gradient(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b),
+                                              _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def bstep(g, p, I1, I2, b, z, u, out=None, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    out = _torch().empty_like(b) if out is None else out
+    cap = ctypes.c_int(0)
+    _check("sac_bstep", lib().sac_bstep(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), _ptr(z),
+                                        _ptr(u), _ptr(out), ctypes.byref(cap), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+    return out, bool(cap.value)
+
+
+def zstep(g, p, b, u, z, u_out=None, ws=None, stream=None):
+    """z is updated in place (z^k -> z^{k+1}); returns (u_out, norms5)."""
+    ws = _ws(g, p, ws)
+    u_out = _torch().empty_like(u) if u_out is None else u_out
+    nr = (ctypes.c_double * 5)()
+    _check("sac_zstep", lib().sac_zstep(ctypes.byref(g), ctypes.byref(p), _ptr(b), _ptr(u), _ptr(z), _ptr(u_out),
+                                        nr, _ptr(ws), ws.numel(), _stream(stream)))
+    return u_out, np.array(nr[:])
+
+
+def admm_solve(g, p, I1, I2, b, z=None, u=None, want_hist=False, ws=None, stream=None):
+    """b (in: feasible b^0, out: result), z, u (in/out or None) in place."""
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    it = ctypes.c_int(0)
+    rp, rd = ctypes.c_double(0), ctypes.c_double(0)
+    hist = np.zeros((max(p.max_iter, 1), 6)) if want_hist else None
+    st = lib().sac_admm_solve(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), _ptr(z), _ptr(u),
+                              ctypes.byref(it), ctypes.byref(rp), ctypes.byref(rd),
+                              hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_hist else None, _ptr(ws), ws.numel(),
+                              _stream(stream))
+    _check("sac_admm_solve", st)
+    res = dict(iters=it.value, r_pri=rp.value, r_dual=rd.value, converged=(st == SAC_OK), status=st)
+    if want_hist:
+        res["hist"] = hist[:it.value]
+    return res
+
+
+def hessvec(g, p, I1, I2, b, v, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    out = _torch().empty_like(v)
+    _check("sac_hessvec", lib().sac_hessvec(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), _ptr(v),
+                                            _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def precond_solve(g, p, I1, I2, b, rhs, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    out = _torch().empty_like(rhs)
+    _check("sac_precond_solve", lib().sac_precond_solve(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2),
+                                                        _ptr(b), _ptr(rhs), _ptr(out), _ptr(ws), ws.numel(),
+                                                        _stream(stream)))
+    return out
+
+
+def gnpcg_solve(g, p, I1, I2, b, want_hist=False, ws=None, stream=None):
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    it = ctypes.c_int(0)
+    J, gn = ctypes.c_double(0), ctypes.c_double(0)
+    hist = np.zeros((max(p.max_gn, 1), 5)) if want_hist else None
+    st = lib().sac_gnpcg_solve(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), ctypes.byref(it),
+                               ctypes.byref(J), ctypes.byref(gn),
+                               hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_hist else None, _ptr(ws), ws.numel(),
+                               _stream(stream))
+    _check("sac_gnpcg_solve", st)
+    res = dict(iters=it.value, J=J.value, gnorm=gn.value, converged=(st == SAC_OK), status=st)
+    if want_hist:
+        res["hist"] = hist[:it.value]
+    return res
+
+
+PHASES = ["bstep", "bstep_refine", "zpass0", "zpass1", "zpass2", "zpass3"]
+
+
+def profile_enable(on=True):
+    lib().sac_profile_enable(1 if on else 0)
+
+
+def profile_read(reset=True):
+    ms = (ctypes.c_double * len(PHASES))()
+    n = (ctypes.c_longlong * len(PHASES))()
+    lib().sac_profile_read(ms, n, 1 if reset else 0)
+    return {name: (ms[i], n[i]) for i, name in enumerate(PHASES)}
+
+
+def launch_count():
+    return int(lib().sac_launch_count())

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Sizes span several line tiles with ragged tails (tiles hold 8 lines), every
+phase-encoding axis position (first, middle, last), every faces-per-lane
+class (K = 3, 5, 9, 15), and lines with active constraints.  The FP64 path
+must match to 1e-9 relative (Sec. 4.2 ADMM after a fixed number of
+iterations); the mixed path to 1e-3 voxel in b and 1e-6 relative objective.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00531_gb300 import phantoms as ph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((37, 50), 1),          # 2D, contiguous lines, 5 tiles (ragged), K = 3
+    ((9, 70, 21), 1),       # 3D, PE middle, inner tiles 8 + 8 + 5, K = 3
+    ((40, 7, 9), 0),        # PE first: one outer, 63 inner lines
+    ((6, 7, 100), 2),       # PE last: contiguous lines, K = 5
+    ((5, 256, 11), 1),      # K = 9
+    ((3, 300), 1),          # K = 15
+]
+
+
+@pytest.fixture(scope="module")
+def sac():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00531_gb300 import build, sac as S
+    build.build()
+    return S
+
+
+def cu(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def case_data(m, pe, seed=0, max_d=0.5):
+    h = tuple(1.0 / m[0] for _ in m)
+    I1 = ph.random_images(m, seed + 1)
+    I2 = ph.random_images(m, seed + 2)
+    b = ph.random_field(m, pe, h, seed + 3, max_d=max_d)
+    rng = np.random.default_rng(seed + 4)
+    z = b + 0.05 * h[pe] * rng.normal(size=b.shape)
+    u = 0.05 * h[pe] * rng.normal(size=b.shape)
+    return h, I1, I2, b, z, u
+
+
+@pytest.mark.parametrize("m,pe", CASES)
+def test_objective_and_gradient_f64(sac, m, pe):
+    h, I1, I2, b, _, _ = case_data(m, pe)
+    og = oracle.Grid(m, h, pe)
+    op = oracle.Params(alpha=0.7, beta=0.4)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=0.7, beta=0.4, prec="f64")
+    ws = sac.workspace(g, p)
+    o_ref = oracle.objective(og, op, I1, I2, b)
+    o = sac.objective(g, p, cu(I1), cu(I2), cu(b), ws=ws)
+    for k in ("J", "D", "S", "P"):
+        assert o[k] == pytest.approx(o_ref[k], rel=1e-12, abs=1e-300), k
+    gr = sac.gradient(g, p, cu(I1), cu(I2), cu(b), ws=ws).cpu().numpy()
+    assert rel(gr, oracle.gradient(og, op, I1, I2, b)) < 1e-11
+
+
+def test_objective_infinite_penalty_when_infeasible(sac):
+    m, pe = (10, 12), 1
+    h, I1, I2, b, _, _ = case_data(m, pe)
+    b[3, 5] += 2.0 * h[1]
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=1.0, beta=1.0, prec="f64")
+    o = sac.objective(g, p, cu(I1), cu(I2), cu(b))
+    assert np.isinf(o["P"]) and np.isinf(o["J"])
+
+
+@pytest.mark.parametrize("m,pe", CASES)
+def test_bstep_f64(sac, m, pe):
+    h, I1, I2, b, z, u = case_data(m, pe, seed=10)
+    og = oracle.Grid(m, h, pe)
+    op = oracle.Params(alpha=0.5, rho=100.0)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=0.5, rho=100.0, prec="f64")
+    b_ref, st = oracle.bstep(og, op, I1, I2, b, z, u)
+    out, capped = sac.bstep(g, p, cu(I1), cu(I2), cu(b), cu(z), cu(u))
+    assert not capped and st["capped"] == 0
+    assert rel(out.cpu().numpy(), b_ref) < 1e-10
+
+
+@pytest.mark.parametrize("m,pe", [((37, 50), 1), ((9, 70, 21), 1), ((6, 7, 100), 2), ((5, 256, 11), 1)])
+def test_bstep_f64_with_active_constraints(sac, m, pe):
+    # steep targets z and small alpha push many cells onto |D1 b| = 1
+    h, I1, I2, b, _, u = case_data(m, pe, seed=20, max_d=0.8)
+    rng = np.random.default_rng(5)
+    z = b + 3.0 * h[pe] * rng.normal(size=b.shape)
+    og = oracle.Grid(m, h, pe)
+    op = oracle.Params(alpha=1e-3, rho=1e5, n_sqp=2)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=1e-3, rho=1e5, n_sqp=2, prec="f64")
+    b_ref, st = oracle.bstep(og, op, I1, I2, b, z, u)
+    assert st["active"] > 0 and st["capped"] == 0
+    out, capped = sac.bstep(g, p, cu(I1), cu(I2), cu(b), cu(z), cu(u))
+    assert not capped
+    assert rel(out.cpu().numpy(), b_ref) < 1e-9
+    assert oracle.max_abs_d1(og, out.cpu().numpy()) <= 1 + 1e-9
+
+
+@pytest.mark.parametrize("m,pe", CASES)
+def test_zstep_f64(sac, m, pe):
+    h, _, _, b, z, u = case_data(m, pe, seed=30)
+    og = oracle.Grid(m, h, pe)
+    op = oracle.Params(alpha=2.0, rho=50.0)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=2.0, rho=50.0, prec="f64")
+    z_ref = oracle.zstep(og, op, b, u)
+    u_ref = u + b - z_ref
+    zt = cu(z)
+    u_out, nr = sac.zstep(g, p, cu(b), cu(u), zt)
+    assert rel(zt.cpu().numpy(), z_ref) < 1e-12
+    assert rel(u_out.cpu().numpy(), u_ref) < 1e-11
+    ref = [np.sum((b - z_ref) ** 2), np.sum((z_ref - z) ** 2), np.sum(b ** 2), np.sum(z_ref ** 2), np.sum(u_ref ** 2)]
+    np.testing.assert_allclose(nr, ref, rtol=1e-10)
+
+
+@pytest.mark.parametrize("m,pe,K", [((24, 40), 1, 20), ((8, 48, 13), 1, 12), ((12, 9, 50), 2, 10)])
+def test_admm_f64_fixed_iterations(sac, m, pe, K):
+    w = ph.small_workload(m, pe, seed=3, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    og = oracle.Grid(m, d["h"], pe)
+    op = oracle.Params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0)
+    ref = oracle.admm(og, op, d["I1"], d["I2"], np.zeros(og.face_shape), want_hist=True)
+    g = sac.grid(m, d["h"], pe)
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec="f64")
+    b = cu(np.zeros(og.face_shape))
+    z = cu(np.zeros(og.face_shape))
+    u = cu(np.zeros(og.face_shape))
+    res = sac.admm_solve(g, p, cu(d["I1"]), cu(d["I2"]), b, z, u, want_hist=True)
+    assert res["iters"] == K
+    bb = b.cpu().numpy()
+    assert np.linalg.norm(bb - ref["b"]) <= 1e-9 * np.linalg.norm(ref["b"])
+    assert rel(bb, ref["b"]) < 1e-9
+    assert rel(z.cpu().numpy(), ref["z"]) < 1e-9
+    np.testing.assert_allclose(res["hist"][:, :4], ref["hist"][:, :4], rtol=1e-7)
+
+
+def test_admm_rejects_infeasible_start(sac):
+    m, pe = (10, 12), 1
+    h, I1, I2, b, _, _ = case_data(m, pe)
+    b[2, 4] += 3.0 * h[1]
+    g = sac.grid(m, h, pe)
+    p = sac.params(prec="f64")
+    with pytest.raises(sac.SacError) as e:
+        sac.admm_solve(g, p, cu(I1), cu(I2), cu(b))
+    assert e.value.status == sac.SAC_EINFEASIBLE
+
+
+@pytest.mark.parametrize("m,pe", [((37, 50), 1), ((9, 70, 21), 1), ((40, 7, 9), 0), ((5, 256, 11), 1)])
+def test_hessvec_and_preconditioners_f64(sac, m, pe):
+    h, I1, I2, b, _, _ = case_data(m, pe, seed=40)
+    v = np.random.default_rng(1).normal(size=b.shape)
+    og = oracle.Grid(m, h, pe)
+    g = sac.grid(m, h, pe)
+    for prec in (0, 1, 2):
+        op = oracle.Params(alpha=0.8, beta=0.5, precond=prec)
+        p = sac.params(alpha=0.8, beta=0.5, precond=prec, prec="f64")
+        if prec == 2:
+            Hv = sac.hessvec(g, p, cu(I1), cu(I2), cu(b), cu(v)).cpu().numpy()
+            assert rel(Hv, oracle.apply(og, op, "HJGN", I1, I2, b, v)) < 1e-11
+        x = sac.precond_solve(g, p, cu(I1), cu(I2), cu(b), cu(v)).cpu().numpy()
+        assert rel(x, oracle.precond_solve(og, op, I1, I2, b, v)) < 1e-10
+
+
+@pytest.mark.parametrize("m,pe", [((24, 40), 1), ((8, 48, 13), 1)])
+def test_gnpcg_f64(sac, m, pe):
+    w = ph.small_workload(m, pe, seed=4, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    og = oracle.Grid(m, d["h"], pe)
+    op = oracle.Params(alpha=1.0, beta=10.0, max_gn=6, eta=0.1)
+    ref = oracle.gnpcg(og, op, d["I1"], d["I2"], np.zeros(og.face_shape), want_hist=True)
+    g = sac.grid(m, d["h"], pe)
+    p = sac.params(alpha=1.0, beta=10.0, max_gn=6, eta=0.1, prec="f64")
+    b = cu(np.zeros(og.face_shape))
+    res = sac.gnpcg_solve(g, p, cu(d["I1"]), cu(d["I2"]), b, want_hist=True)
+    assert res["iters"] == ref["iters"]
+    np.testing.assert_array_equal(res["hist"][:, 2], ref["hist"][:, 2])     # PCG iterations
+    assert rel(b.cpu().numpy(), ref["b"]) < 1e-8
+    assert res["J"] == pytest.approx(ref["J"], rel=1e-10)
+
+
+@pytest.mark.parametrize("m,pe,K", [((24, 40), 1, 20), ((8, 48, 13), 1, 12)])
+def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
+    w = ph.small_workload(m, pe, seed=3, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    og = oracle.Grid(m, d["h"], pe)
+    op = oracle.Params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0)
+    ref = oracle.admm(og, op, d["I1"], d["I2"], np.zeros(og.face_shape))
+    g = sac.grid(m, d["h"], pe)
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec="mixed")
+    b = cu(np.zeros(og.face_shape))
+    res = sac.admm_solve(g, p, cu(d["I1"], torch.float32), cu(d["I2"], torch.float32), b)
+    assert res["iters"] == K
+    bb = b.cpu().numpy()
+    assert np.max(np.abs(bb - ref["b"])) / d["h"][pe] <= 1e-3
+    J_ref = oracle.objective(og, op, d["I1"], d["I2"], ref["b"])["J"]
+    J_mix = oracle.objective(og, op, d["I1"], d["I2"], bb)["J"]
+    assert abs(J_mix - J_ref) <= 1e-6 * abs(J_ref)
