@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tts-cap", type=int, default=400)
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="only the warm-up and the timed mixed-precision iterations (profiling runs)")
     return ap.parse_args()
 
 
@@ -228,6 +230,12 @@ def main():
     assert res["iters"] == args.steps
     value = world * nf * args.steps / (t_ms / 1e3)
     clocks = clk.summary()
+    if args.only_mixed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": args.steps,
+                              "ms_per_step": t_ms / args.steps, "gpu_launches": launches,
+                              "kernels": {k: v for k, v in prof.items()}}), flush=True)
+        return
 
     # plain FP64 GPU path on the same workload (fewer iterations: FP64 is slow on GB300)
     kf = max(2, min(args.steps, 5))

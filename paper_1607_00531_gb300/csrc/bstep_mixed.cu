@@ -5,9 +5,11 @@
 namespace sac {
 cudaError_t launch_bstep_mixed(const LineLaunch& L) { return launch_bstep_t<double, float>(L); }
 
+// prec 0: FP64 (both kernels); prec 1: FP32 tiles (mode 0) / FP64-on-FP32
+// list (mode 1); prec 2: FP64 compute on FP32 storage (both kernels)
 cudaError_t launch_bstep(int prec, const LineLaunch& L) {
     if (prec == 0) return launch_bstep_f64(L);
-    if (prec == 1) return launch_bstep_f32(L);
+    if (prec == 1) return L.mode == 0 ? launch_bstep_f32(L) : launch_bstep_mixed(L);
     return launch_bstep_mixed(L);
 }
 }  // namespace sac

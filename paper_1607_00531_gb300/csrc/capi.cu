@@ -165,7 +165,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
     P->elem_blocks = (G.nf + 255) / 256;
     const long long nlines = (long long)G.n_outer * G.n_inner;
-    P->rcap = (int)(nlines < (1 << 20) ? nlines : (1 << 20));
+    P->rcap = (int)nlines;
     long long np = 4 * P->line_tiles;
     if (5 * P->pass_tiles[3] > np) np = 5 * P->pass_tiles[3];
     if (P->elem_blocks > np) np = P->elem_blocks;
@@ -274,6 +274,7 @@ LineLaunch plan_line_launch(const Plan* P, int n_sqp, double near_bound, cudaStr
     L.rcount_out = P->d_rcount;
     L.rcap = P->rcap;
     L.list_blocks = (P->rcap + P->W - 1) / P->W;
+    if (L.list_blocks > 4 * 152) L.list_blocks = 4 * 152;
     L.status = P->d_status;
     L.stream = st;
     return L;
@@ -380,25 +381,21 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
     return SAC_OK;
 }
 
-// b-step on the plan's job; mixed: FP32 pass then FP64 re-solve of near-bound lines
+// b-step on the plan's job: the fast kernel over all tiles, then the full
+// active-set method on the lines it queued (FP64 compute in the mixed path,
+// which also queues the lines that end within near_bound of the bound).
 static int bstep_dev(Plan& P, const sac_params* p, cudaStream_t st) {
-    if (P.prec == SAC_MIXED) {
-        SAC_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int), st));
-        LineLaunch L = plan_line_launch(&P, p->n_sqp, p->near_bound, st);
-        {
-            PhaseScope ps(0, st);
-            SAC_CUDA(launch_bstep(1, L));
-        }
-        if (p->near_bound > 0) {
-            PhaseScope ps(1, st);
-            L.mode = 1;
-            L.near_bound = 0.0;
-            SAC_CUDA(launch_bstep(2, L));
-        }
-    } else {
+    const bool mixed = (P.prec == SAC_MIXED);
+    SAC_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int), st));
+    LineLaunch L = plan_line_launch(&P, p->n_sqp, mixed ? p->near_bound : 0.0, st);
+    {
         PhaseScope ps(0, st);
-        LineLaunch L = plan_line_launch(&P, p->n_sqp, 0.0, st);
-        SAC_CUDA(launch_bstep(0, L));
+        SAC_CUDA(launch_bstep(mixed ? 1 : 0, L));
+    }
+    {
+        PhaseScope ps(1, st);
+        L.mode = 1;
+        SAC_CUDA(launch_bstep(mixed ? 1 : 0, L));
     }
     return SAC_OK;
 }

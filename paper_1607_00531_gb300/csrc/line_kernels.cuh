@@ -390,84 +390,180 @@ __device__ bool bstep_line(const Job& J, int n_sqp, double near_bound, const S* 
     return false;
 }
 
-// The b-step over lines.  Storage type S (images and b, z, u), compute type T.
-// mode 0: all tiles of all active jobs (one CTA per tile of W lines).  With
-//         near_bound > 0, a line whose new b has 1 - max|D1 b| < near_bound
-//         keeps b^k and is appended to rlist_out (job << 40 | line) for a
-//         re-solve in FP64 (while the list has room).
-// mode 1: the lines listed in rlist[0 .. *rcount), one per warp.
+// Fast path of the b-step for the warp's line: each SQP pass takes the
+// unconstrained Gauss-Newton step (the first pass of the active-set method
+// with an empty working set).  If that step would cross |D1 b| = 1 somewhere
+// (a blocking constraint: the active-set method has more passes to make) or,
+// when near_bound > 0, if the result ends within near_bound of the bound, the
+// line is left unchanged and the function returns true so that the caller
+// queues it for the full method.  The decision uses the same ratio test as
+// line_qp, so the queued line's QP retraces this pass exactly.
 template <typename T, typename S, int K>
-__global__ void __launch_bounds__(256) k_bstep(const Job* __restrict__ jobs, int njobs,
-                                               const long long* __restrict__ prefix, int W, int RLc, int RLf,
-                                               int n_sqp, double near_bound, int mode,
-                                               const unsigned long long* __restrict__ rlist,
-                                               const int* __restrict__ rcount,
-                                               unsigned long long* __restrict__ rlist_out,
-                                               int* __restrict__ rcount_out, int rcap,
-                                               int* __restrict__ status) {
+__device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double near_bound,
+                                                const S* __restrict__ rowI1, const S* __restrict__ rowI2,
+                                                S* __restrict__ rowB, const S* __restrict__ rowZ,
+                                                const S* __restrict__ rowU, int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int m = J.mpe;
+    const T inv_h = T(1.0 / J.hpe), ih2 = inv_h * inv_h;
+    const T alpha = T(J.alpha), rho = T(J.rho);
+    T bv[K], zu[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = lane * K + k;
+        if (i <= m) {
+            bv[k] = T(rowB[i]);
+            zu[k] = T(rowU[i]) - T(rowZ[i]);
+        } else {
+            bv[k] = T(0); zu[k] = T(0);
+        }
+    }
+    for (int it = 0; it < n_sqp; ++it) {
+        T r[K], Jd[K], Ju[K], dc[K];
+        T bnext = from_next(bv[0]);
+        lane_cells<T, S, K>(rowI1, rowI2, m, inv_h, bv, bnext, r, Jd, Ju, dc);
+        T Ju_p = from_prev(Ju[K - 1]), r_p = from_prev(r[K - 1]), d_p = from_prev(dc[K - 1]);
+        T aa[K], dd[K], cc[K], xh[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = lane * K + k;
+            if (i <= m) {
+                T Jup = k ? Ju[k - 1] : Ju_p, rup = k ? r[k - 1] : r_p, dup = k ? dc[k - 1] : d_p;
+                if (i == 0) { Jup = T(0); rup = T(0); dup = T(0); }
+                T nadj = T((i > 0) + (i < m));
+                dd[k] = Jup * Jup + Jd[k] * Jd[k] + alpha * nadj * ih2 + rho;
+                cc[k] = (i < m) ? (Jd[k] * Ju[k] - alpha * ih2) : T(0);
+                xh[k] = -(Jup * rup + Jd[k] * r[k] + alpha * (dup - dc[k]) * inv_h + rho * (bv[k] + zu[k]));
+            } else {
+                dd[k] = T(1); cc[k] = T(0); xh[k] = T(0);
+            }
+        }
+        T cprev = from_prev(cc[K - 1]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) aa[k] = k ? cc[k - 1] : cprev;
+        warp_tridiag_solve<T, K>(aa, dd, cc, xh);
+        // ratio test of the full step from x = 0 (line_qp's first pass)
+        T sn = from_next(xh[0]);
+        bool blocked = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = lane * K + k;
+            if (j < m) {
+                T sp1 = (k + 1 < K) ? xh[k + 1] : sn;
+                T dp = (sp1 - xh[k]) * inv_h;
+                T tl = T(INFINITY);
+                if (dp < T(0)) tl = (T(-1) - dc[k]) / dp;
+                else if (dp > T(0)) tl = (T(1) - dc[k]) / dp;
+                blocked |= (tl < T(1)) || !(tl == tl);
+            }
+        }
+        if (__any_sync(kFull, blocked)) return true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) bv[k] += xh[k];
+    }
+    T bnext = from_next(bv[0]);
+    T dmax = T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = lane * K + k;
+        if (j < m) {
+            T b1 = (k + 1 < K) ? bv[k + 1] : bnext;
+            T d = fabs((b1 - bv[k]) * inv_h);
+            if (!(d == d)) bad = true;
+            dmax = fmax(dmax, d);
+        }
+    }
+    dmax = warp_max(dmax);
+    if (__any_sync(kFull, bad)) {
+        if (lane == 0) atomicOr(status, kStNaN);
+    }
+    if (near_bound > 0.0 && (double)(T(1) - dmax) < near_bound) return true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = lane * K + k;
+        if (i <= m) rowB[i] = S(bv[k]);
+    }
+    return false;
+}
+
+// The b-step over all tiles of all active jobs (one CTA per tile of W lines).
+// Lines that need the active-set method (or, near_bound > 0, an FP64 re-solve
+// near the bound) keep b^k and are appended to rlist (job << 40 | line); the
+// list must have room for every line of the launch.
+template <typename T, typename S, int K>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_bstep(const Job* __restrict__ jobs, int njobs,
+                                                  const long long* __restrict__ prefix, int W, int RLc, int RLf,
+                                                  int n_sqp, double near_bound,
+                                                  unsigned long long* __restrict__ rlist,
+                                                  int* __restrict__ rcount, int rcap,
+                                                  int* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // shared layout: QP scratch (T) first, then I1, I2 (cells), b, z, u (faces)
+    S* sI1 = reinterpret_cast<S*>(smem_raw);
+    S* sI2 = sI1 + (size_t)W * RLc;
+    S* sB = sI2 + (size_t)W * RLc;
+    S* sZ = sB + (size_t)W * RLf;
+    S* sU = sZ + (size_t)W * RLf;
+    const long long t = blockIdx.x;
+    if (t >= prefix[njobs]) return;
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    if (!J.active) return;
+    const TileInfo ti = tile_info(J, t - prefix[jid], W);
+    stage_rows<S>(sI1, RLc, (const S*)J.I1, ti.c0, ti, W, J.mpe, J.n_inner);
+    stage_rows<S>(sI2, RLc, (const S*)J.I2, ti.c0, ti, W, J.mpe, J.n_inner);
+    stage_rows<S>(sB, RLf, (const S*)J.b, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    stage_rows<S>(sZ, RLf, (const S*)J.z, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    stage_rows<S>(sU, RLf, (const S*)J.u, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    __syncthreads();
+    if (w < ti.nl) {
+        const bool queue = bstep_line_fast<T, S, K>(J, n_sqp, near_bound, sI1 + w * RLc, sI2 + w * RLc,
+                                                    sB + w * RLf, sZ + w * RLf, sU + w * RLf, status);
+        if (queue && lane == 0) {
+            const int slot = atomicAdd(rcount, 1);
+            const long long tl = t - prefix[jid];
+            long long o, n;
+            if (ti.inner_fast) {
+                const long long tpo = (J.n_inner + W - 1) / W;
+                o = tl / tpo; n = (tl % tpo) * W + w;
+            } else {
+                o = tl * W + w; n = 0;
+            }
+            if (slot < rcap) rlist[slot] = ((unsigned long long)jid << 40) | (unsigned long long)(o * J.n_inner + n);
+            else atomicOr(status, kStTimeout);
+        }
+    }
+    __syncthreads();
+    unstage_rows<S>(sB, RLf, (S*)J.b, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+}
+
+// The full b-step (active-set QP, Eqs. qp and schurasqp) for the listed lines,
+// one warp per line, grid-stride over the list.  Compute type T (FP64 for the
+// mixed path), storage type S.
+template <typename T, typename S, int K>
+__global__ void __launch_bounds__(256) k_bstep_list(const Job* __restrict__ jobs, int W, int RLc, int RLf,
+                                                    int n_sqp, const unsigned long long* __restrict__ rlist,
+                                                    const int* __restrict__ rcount, int rcap,
+                                                    int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T* scr = reinterpret_cast<T*>(smem_raw);
     S* sI1 = reinterpret_cast<S*>(scr + (size_t)W * 3 * RLf);
     S* sI2 = sI1 + (size_t)W * RLc;
     S* sB = sI2 + (size_t)W * RLc;
     S* sZ = sB + (size_t)W * RLf;
     S* sU = sZ + (size_t)W * RLf;
-    if (mode == 0) {
-        const long long t = blockIdx.x;
-        if (t >= prefix[njobs]) return;
-        const int jid = find_job(prefix, njobs, t);
-        const Job& J = jobs[jid];
-        if (!J.active) return;
-        const TileInfo ti = tile_info(J, t - prefix[jid], W);
-        stage_rows<S>(sI1, RLc, (const S*)J.I1, ti.c0, ti, W, J.mpe, J.n_inner);
-        stage_rows<S>(sI2, RLc, (const S*)J.I2, ti.c0, ti, W, J.mpe, J.n_inner);
-        stage_rows<S>(sB, RLf, (const S*)J.b, ti.f0, ti, W, J.mpe + 1, J.n_inner);
-        stage_rows<S>(sZ, RLf, (const S*)J.z, ti.f0, ti, W, J.mpe + 1, J.n_inner);
-        stage_rows<S>(sU, RLf, (const S*)J.u, ti.f0, ti, W, J.mpe + 1, J.n_inner);
-        __syncthreads();
-        if (w < ti.nl) {
-            const bool near = bstep_line<T, S, K>(J, n_sqp, near_bound, sI1 + w * RLc, sI2 + w * RLc,
-                                                  sB + w * RLf, sZ + w * RLf, sU + w * RLf,
-                                                  scr + (size_t)w * 3 * RLf, RLf, status, true);
-            if (near) {
-                // queue for the FP64 re-solve; if the list is full keep this result
-                int slot = 0;
-                if (lane == 0) {
-                    slot = atomicAdd(rcount_out, 1);
-                    if (slot < rcap) {
-                        const long long tl = t - prefix[jid];
-                        long long o, n;
-                        if (ti.inner_fast) {
-                            const long long tpo = (J.n_inner + W - 1) / W;
-                            o = tl / tpo; n = (tl % tpo) * W + w;
-                        } else {
-                            o = tl * W + w; n = 0;
-                        }
-                        rlist_out[slot] = ((unsigned long long)jid << 40) | (unsigned long long)(o * J.n_inner + n);
-                    }
-                }
-                slot = __shfl_sync(kFull, slot, 0);
-                if (slot >= rcap)
-                    bstep_line<T, S, K>(J, n_sqp, 0.0, sI1 + w * RLc, sI2 + w * RLc, sB + w * RLf,
-                                        sZ + w * RLf, sU + w * RLf, scr + (size_t)w * 3 * RLf, RLf, status,
-                                        false);
-            }
-        }
-        __syncthreads();
-        unstage_rows<S>(sB, RLf, (S*)J.b, ti.f0, ti, W, J.mpe + 1, J.n_inner);
-    } else {
-        // one listed line per warp; no block-wide barriers in this mode
-        const long long e = (long long)blockIdx.x * W + w;
-        if (e >= (long long)min(*rcount, rcap)) return;
+    const long long n = min(*rcount, rcap);
+    for (long long e = (long long)blockIdx.x * W + w; e < n; e += (long long)gridDim.x * W) {
         const unsigned long long key = rlist[e];
         const int jid = (int)(key >> 40);
         const long long line_id = (long long)(key & ((1ull << 40) - 1));
         const Job& J = jobs[jid];
-        const long long o = line_id / J.n_inner, n = line_id % J.n_inner;
-        const long long f0 = o * (long long)(J.mpe + 1) * J.n_inner + n;
-        const long long c0 = o * (long long)J.mpe * J.n_inner + n;
+        const long long o = line_id / J.n_inner, nn = line_id % J.n_inner;
+        const long long f0 = o * (long long)(J.mpe + 1) * J.n_inner + nn;
+        const long long c0 = o * (long long)J.mpe * J.n_inner + nn;
+        __syncwarp();
         warp_load_line<S>(sI1 + w * RLc, (const S*)J.I1, c0, J.mpe, J.n_inner);
         warp_load_line<S>(sI2 + w * RLc, (const S*)J.I2, c0, J.mpe, J.n_inner);
         warp_load_line<S>(sB + w * RLf, (const S*)J.b, f0, J.mpe + 1, J.n_inner);
@@ -677,16 +773,26 @@ __global__ void __launch_bounds__(256) k_line_solve(const Job* __restrict__ jobs
 
 template <typename T, typename S, int K>
 cudaError_t launch_bstep_k(const LineLaunch& L) {
-    auto kern = k_bstep<T, S, K>;
+    if (L.mode == 0) {
+        auto kern = k_bstep<T, S, K>;
+        size_t sm = (size_t)L.W * (2 * L.RLc + 3 * L.RLf) * sizeof(S);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        if (L.total_tiles <= 0) return cudaSuccess;
+        count_launch();
+        kern<<<(unsigned)L.total_tiles, 32 * L.W, sm, L.stream>>>(L.jobs, L.njobs, L.prefix, L.W, L.RLc, L.RLf,
+                                                                 L.n_sqp, L.near_bound, L.rlist_out, L.rcount_out,
+                                                                 L.rcap, L.status);
+        return cudaGetLastError();
+    }
+    auto kern = k_bstep_list<T, S, K>;
     size_t sm = line_smem_bstep(L.W, L.RLc, L.RLf, sizeof(T), sizeof(S));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    long long grid = L.mode == 0 ? L.total_tiles : L.list_blocks;
-    if (grid <= 0) return cudaSuccess;
+    if (L.list_blocks <= 0) return cudaSuccess;
     count_launch();
-    kern<<<(unsigned)grid, 32 * L.W, sm, L.stream>>>(L.jobs, L.njobs, L.prefix, L.W, L.RLc, L.RLf, L.n_sqp,
-                                                    L.near_bound, L.mode, L.rlist, L.rcount, L.rlist_out,
-                                                    L.rcount_out, L.rcap, L.status);
+    kern<<<(unsigned)L.list_blocks, 32 * L.W, sm, L.stream>>>(L.jobs, L.W, L.RLc, L.RLf, L.n_sqp, L.rlist,
+                                                             L.rcount, L.rcap, L.status);
     return cudaGetLastError();
 }
 

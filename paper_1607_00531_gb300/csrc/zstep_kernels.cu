@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(256) k_axis(const Job* __restrict__ jobs, int 
             __syncthreads();
         }
     }
-    // epilogue
-    double nrm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    // epilogue; residual-norm partials: per thread in T (at most 16 terms),
+    // across threads and blocks in FP64
+    T tn[5] = {T(0), T(0), T(0), T(0), T(0)};
     const bool scale_here = (pass == 1) || (pass == 0 && J.F[J.ax2] < 2);
     long long s_between = 1;   // stride of the ax1 index inside `pre` (pass 1)
     for (int a = J.ax1 + 1; a < J.ax2; ++a) s_between *= J.F[a];
@@ -163,12 +164,12 @@ __global__ void __launch_bounds__(256) k_axis(const Job* __restrict__ jobs, int 
                     const T un = uu + bb - v;
                     Z[a] = v;
                     U[a] = un;
-                    const double dbz = double(bb) - double(v), dzz = double(v) - double(zo);
-                    nrm[0] += dbz * dbz;
-                    nrm[1] += dzz * dzz;
-                    nrm[2] += double(bb) * double(bb);
-                    nrm[3] += double(v) * double(v);
-                    nrm[4] += double(un) * double(un);
+                    const T dbz = bb - v, dzz = v - zo;
+                    tn[0] += dbz * dbz;
+                    tn[1] += dzz * dzz;
+                    tn[2] += bb * bb;
+                    tn[3] += v * v;
+                    tn[4] += un * un;
                 } else {
                     Y[a] = v;
                 }
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) k_axis(const Job* __restrict__ jobs, int 
         }
     }
     if (pass == 3) {
+        double nrm[5] = {double(tn[0]), double(tn[1]), double(tn[2]), double(tn[3]), double(tn[4])};
         block_sum<5>(nrm, red);
         if (threadIdx.x == 0) {
             double* p = part + blockIdx.x * 5;
