@@ -122,6 +122,60 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def roofline(prof, w, g, nf, sac):
+    """Per phase: algorithmic HBM bytes and algorithmic flops per launch over
+    the measured average launch time; the binding roof (larger fraction) of
+    the dominant phase is reported."""
+    hbm, smmax, src = peaks()
+    bf16 = 1955.6
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            bf16 = json.load(fh).get("bf16_tflops", bf16)
+    tf32_peak = bf16 * (1.1 / 2.25)          # measured BF16 x nominal TF32/BF16 ratio (dense)
+    fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+    cells = int(np.prod(w.m))
+    F = sac.face_shape(g)
+    axes = [a for a in range(3) if a != w.pe]
+    L1 = F[axes[0]] if axes[0] < len(F) else 1
+    L2 = F[axes[1]] if axes[1] < len(F) else 1
+    per_face_bytes = {"zpass0": 12, "zpass1": 8, "zpass2": 8, "zpass3": 24}
+    flops = {"zpass0": 2 * L1 * nf, "zpass3": 2 * L1 * nf, "zpass1": 2 * L2 * nf, "zpass2": 2 * L2 * nf}
+    nphase = {k: v for k, v in prof.items() if v[1] > 0}
+    tot_ms = sum(v[0] for v in nphase.values())
+    kernels = {}
+    for k, (ms, n) in nphase.items():
+        avg = ms / n / 1e3
+        if k in ("bstep", "bstep_refine"):
+            byts = 2 * 4 * cells + 4 * 4 * nf if k == "bstep" else None
+            ent = {"ms_total": ms, "launches": n, "share": ms / tot_ms}
+            if byts:
+                ent.update(bound="hbm", bytes=byts, achieved_gbs=byts / avg / 1e9, frac_hbm=byts / avg / 1e9 / hbm)
+        else:
+            byts = per_face_bytes[k] * nf
+            ach_b = byts / avg / 1e9
+            ach_f = flops[k] / avg / 1e12
+            ent = {"ms_total": ms, "launches": n, "share": ms / tot_ms, "bytes": byts, "flops": flops[k],
+                   "achieved_gbs": ach_b, "frac_hbm": ach_b / hbm, "achieved_tflops": ach_f,
+                   "frac_tensor_tf32": ach_f / tf32_peak}
+            ent["bound"] = "hbm" if ent["frac_hbm"] >= ent["frac_tensor_tf32"] else "tensor"
+        kernels[k] = ent
+    dom = max(nphase, key=lambda k: nphase[k][0])
+    e = kernels[dom]
+    if e.get("bound") == "tensor":
+        roof = {"kernel": f"k_axis_tc {dom}", "bound": "tensor", "achieved": e["achieved_tflops"],
+                "peak": tf32_peak, "unit": "TFLOP/s", "frac": e["frac_tensor_tf32"], "traffic": None,
+                "algorithmic_flops_per_launch": e["flops"],
+                "peak_source": f"{src}: bf16 {bf16:.1f} TFLOP/s x nominal TF32/BF16 1.1/2.25 (split TF32 runs 3 MMAs per product)"}
+    else:
+        name = "k_bstep<float,float,9>" if dom == "bstep" else f"k_axis_tc {dom}"
+        roof = {"kernel": name, "bound": "hbm", "achieved": e["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": e["frac_hbm"], "traffic": None, "algorithmic_bytes_per_launch": e["bytes"],
+                "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    roof["fp32_simt_peak_tflops"] = fp32_peak
+    return roof, kernels
+
+
 def oracle_cpu_baseline(d, w, iters=1, nthreads=0):
     """The FP64 oracle as it stands, on the host cores: `iters` ADMM
     iterations over the full volume."""
@@ -296,30 +350,7 @@ def main():
             del wst
 
     # roofline of the dominant kernel (largest summed device time in the timed region)
-    hbm, smmax, src = peaks()
-    cells = int(np.prod(w.m))
-    nphase = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(nphase, key=lambda k: nphase[k][0])
-    tot_ms = sum(v[0] for v in nphase.values())
-    F = sac.face_shape(g)
-    L1 = F[0] if w.pe != 0 else F[1]
-    L2 = F[2] if w.pe != 2 else F[1]
-    flops = {"zpass0": 2 * L1 * nf, "zpass3": 2 * L1 * nf, "zpass1": 2 * L2 * nf, "zpass2": 2 * L2 * nf}
-    fp32_peak = 152 * 128 * 2 * smmax * 1e6 / 1e12   # TFLOP/s, SIMT FP32 at the max SM clock
-    avg_ms = nphase[dom][0] / nphase[dom][1]
-    if dom in ("bstep", "bstep_refine"):
-        bytes_per = 2 * 4 * cells + 3 * 4 * nf + 4 * nf
-        ach = bytes_per / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": "k_bstep<float>", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "algorithmic_bytes_per_launch": bytes_per}
-    else:
-        ach = flops[dom] / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": f"k_axis<float> {dom}", "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
-                "algorithmic_flops_per_launch": flops[dom]}
-    roof["peak_source"] = f"{src} (HBM copy) / SIMT FP32 = 152 SM x 128 lanes x 2 x {smmax:.0f} MHz"
-    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / tot_ms} for k, v in nphase.items()}
-
+    roof, kernels = roofline(prof, w, g, nf, sac)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         nfc, ts, cores = oracle_cpu_baseline(d, w, iters=1)

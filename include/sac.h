@@ -96,7 +96,11 @@ typedef struct {
     double near_bound;   /* SAC_MIXED: lines with 1 - max|D1 b| < near_bound are
                             re-solved in FP64 after the FP32 b-step */
     int check_every;     /* ADMM: test the stopping rule every k iterations */
-    int reserved[3];
+    int zstep_kernel;    /* SAC_MIXED z-step DCTs: 0 tensor cores (tcgen05, split TF32)
+                            where the grid allows (else SIMT), 1 SIMT FP32 */
+    int autotune;        /* batched runs: 1 = pick the b-step tile width on the
+                            first live iterations (results do not depend on it) */
+    int reserved[1];
 } sac_params;
 
 void sac_params_default(sac_params* p);
@@ -164,6 +168,61 @@ int sac_precond_solve(const sac_grid* g, const sac_params* p, const void* I1, co
 int sac_gnpcg_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
                     double* b, int* iters, double* J_out, double* gnorm, double* hist,
                     void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- batching
+ * Many volumes solved together by ADMM (Sec. 4.2, each volume independently):
+ * every phase of an iteration is one kernel launch over the lines (b-step)
+ * or slabs (z-step) of all volumes of the batch; each volume stops on its own
+ * residuals (Eq. admmStop, checked on the device) and its tiles then return
+ * at once.  Iterations are replayed from a CUDA graph of `chunk` iterations,
+ * with one host synchronisation per chunk.  A volume's arithmetic does not
+ * depend on the other volumes of the batch.
+ *
+ * Grids may differ between volumes; all share `p`.  I1[j], I2[j] are device
+ * images (float for SAC_MIXED, double for SAC_F64); b[j] is a device FP64
+ * face array holding b^0 on entry (feasible; z^0 = b^0, u^0 = 0) and the
+ * result after sac_batch_finish.  `ws` must hold sac_batch_workspace_bytes;
+ * the handle (host memory) is released by sac_batch_destroy. */
+typedef struct sac_batch_s* sac_batch;
+size_t sac_batch_workspace_bytes(int njobs, const sac_grid* grids, const sac_params* p);
+int sac_batch_create(int njobs, const sac_grid* grids, const sac_params* p, const void* const* I1,
+                     const void* const* I2, double* const* b, void* ws, size_t ws_bytes, void* stream,
+                     sac_batch* out);
+/* runs at most max_iter more iterations (p->max_iter caps each volume) */
+int sac_batch_run(sac_batch bt, int max_iter, int chunk);
+/* host arrays of njobs entries (any may be NULL) */
+int sac_batch_stats(sac_batch bt, int* iters, int* converged, double* r_pri, double* r_dual);
+int sac_batch_finish(sac_batch bt);
+void sac_batch_destroy(sac_batch bt);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of SAC requests.  The caller gives the server a device
+ * memory pool (`pool`, 256-byte aligned, `pool_bytes` long: the admission
+ * budget) and a stream.  sac_server_submit copies the request's images from
+ * host memory (float for SAC_MIXED, double for SAC_F64; the grid must suit
+ * the tensor-core z-step when it is selected) and queues it; it returns a
+ * ticket.  Each sac_server_step admits queued requests while the pool has
+ * room (first fit in arrival order), runs up to `iters` batched ADMM
+ * iterations (sac_batch semantics, b^0 = 0) on every admitted job, and
+ * retires the jobs that stopped (Eq. admmStop or p->max_iter), whose memory
+ * returns to the pool.  Running jobs keep their state between steps, and a
+ * job's result does not depend on which other jobs ran with it.
+ * sac_server_poll: state 0 queued, 1 running, 2 done; times3 = host seconds
+ * {submitted, admitted, finished}.  sac_server_fetch copies a finished field
+ * (FP64 faces) into host memory and forgets the request.  sac_server_totals:
+ * {ADMM iterations, faces x iterations, pool bytes in use}. */
+typedef struct sac_server_s* sac_server;
+/* device bytes one request of grid g takes from the pool while it runs */
+size_t sac_server_request_bytes(const sac_params* p, const sac_grid* g);
+int sac_server_create(const sac_params* p, void* pool, size_t pool_bytes, int max_jobs, void* stream,
+                      sac_server* out);
+int sac_server_submit(sac_server s, const sac_grid* g, const void* I1_host, const void* I2_host,
+                      long long* ticket);
+int sac_server_step(sac_server s, int iters, int chunk, int* n_running, int* n_queued);
+int sac_server_poll(sac_server s, long long ticket, int* state, int* iters, int* converged, double* times3);
+int sac_server_fetch(sac_server s, long long ticket, double* b_host);
+int sac_server_totals(sac_server s, long long* out3);
+void sac_server_destroy(sac_server s);
 
 /* ---------------------------------------------------------------- tracing
  * Instrumentation (not part of the method).  With profiling enabled, the ADMM

@@ -3,4 +3,5 @@
 
 namespace sac {
 cudaError_t launch_bstep_f64(const LineLaunch& L) { return launch_bstep_t<double, double>(L); }
+cudaError_t prepare_bstep_f64() { return prepare_bstep_t<double, double>(); }
 }  // namespace sac

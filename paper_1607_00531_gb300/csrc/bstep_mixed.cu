@@ -4,6 +4,7 @@
 
 namespace sac {
 cudaError_t launch_bstep_mixed(const LineLaunch& L) { return launch_bstep_t<double, float>(L); }
+cudaError_t prepare_bstep_mixed() { return prepare_bstep_t<double, float>(); }
 
 // prec 0: FP64 (both kernels); prec 1: FP32 tiles (mode 0) / FP64-on-FP32
 // list (mode 1); prec 2: FP64 compute on FP32 storage (both kernels)

@@ -18,6 +18,23 @@ namespace sac {
 static std::atomic<long long> g_launches{0};
 void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static std::mutex g_prep_mu;
+static int g_prep_device = -1;
+int prepare_kernels() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SAC_ECUDA;
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (g_prep_device == dev) return SAC_OK;
+    if (prepare_bstep_f64() != cudaSuccess || prepare_bstep_f32() != cudaSuccess ||
+        prepare_bstep_mixed() != cudaSuccess || prepare_line_eval() != cudaSuccess ||
+        prepare_axis_tc() != cudaSuccess) {
+        cudaGetLastError();
+        return SAC_ECUDA;
+    }
+    g_prep_device = dev;
+    return SAC_OK;
+}
+
 // Per-phase device timers: CUDA events recorded on the launching stream
 // around each phase of the ADMM iteration.
 struct Profiler {
@@ -72,7 +89,10 @@ struct PhaseScope {
 #define SAC_CUDA(x)                                  \
     do {                                             \
         cudaError_t e_ = (x);                        \
-        if (e_ != cudaSuccess) return SAC_ECUDA;     \
+        if (e_ != cudaSuccess) {                     \
+            cudaGetLastError();                      \
+            return SAC_ECUDA;                        \
+        }                                            \
     } while (0)
 #define SAC_TRY(x)                                   \
     do {                                             \
@@ -119,6 +139,7 @@ int check_params(const sac_params* p) {
     if (p->precond < 0 || p->precond > 2) return SAC_EINVAL;
     if (p->prec != SAC_F64 && p->prec != SAC_MIXED) return SAC_EINVAL;
     if (!(p->near_bound >= 0)) return SAC_EINVAL;
+    if (p->zstep_kernel < 0 || p->zstep_kernel > 1) return SAC_EINVAL;
     return SAC_OK;
 }
 
@@ -164,10 +185,18 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     const int axes[4] = {G.ax1, G.ax2, G.ax2, G.ax1};
     for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
     P->elem_blocks = (G.nf + 255) / 256;
+    P->use_tc = (p->prec == SAC_MIXED && p->zstep_kernel == 0);
+    for (int q = 0; q < 4; ++q) {
+        if (!tc_pass_supported(G.F, G.ax1, G.ax2, q)) P->use_tc = 0;
+        P->tc_tiles[q] = tc_pass_tiles(G.F, G.ax1, G.ax2, q);
+        P->tc_floats[q] = tc_matrix_floats(G.F, G.ax1, G.ax2, q);
+        P->tc_smem[q] = tc_smem_bytes(G.F, G.ax1, G.ax2, q);
+    }
     const long long nlines = (long long)G.n_outer * G.n_inner;
     P->rcap = (int)nlines;
     long long np = 4 * P->line_tiles;
     if (5 * P->pass_tiles[3] > np) np = 5 * P->pass_tiles[3];
+    if (5 * P->tc_tiles[3] > np) np = 5 * P->tc_tiles[3];
     if (P->elem_blocks > np) np = P->elem_blocks;
     if (2 * 1216 > np) np = 2 * 1216;
     P->n_part = np;
@@ -176,7 +205,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     size_t o_job = take(sizeof(Job));
-    size_t o_pref = take(sizeof(long long) * 2 * 6);
+    size_t o_pref = take(sizeof(long long) * 2 * 10);
     size_t o_stat = take(256);
     size_t o_out = take(sizeof(double) * 64);
     size_t o_rlist = take(sizeof(unsigned long long) * (size_t)P->rcap);
@@ -187,6 +216,9 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t o_C2f = take(sizeof(float) * (size_t)L2 * L2);
     size_t o_l1 = take(sizeof(double) * (size_t)L1);
     size_t o_l2 = take(sizeof(double) * (size_t)L2);
+    size_t o_scale = take(sizeof(float) * (size_t)L1 * L2);
+    size_t o_tc[4];
+    for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
     size_t o_arr[10];
     for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
     P->bytes = off;
@@ -198,6 +230,9 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->d_pref_line = pref;
     for (int q = 0; q < 4; ++q) P->d_pref_pass[q] = pref + 2 * (1 + q);
     P->d_pref_elem = pref + 10;
+    for (int q = 0; q < 4; ++q) P->d_pref_tc[q] = pref + 12 + 2 * q;
+    for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
+    P->d_scale = (float*)(base + o_scale);
     P->d_status = (int*)(base + o_stat);
     P->d_rcount = P->d_status + 1;
     P->d_out = (double*)(base + o_out);
@@ -215,6 +250,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
 
 int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, void* b, void* z, void* u, void* t1,
                 void* t2, cudaStream_t st) {
+    SAC_TRY(prepare_kernels());
     const Geometry& G = P->G;
     Job J;
     memset(&J, 0, sizeof(J));
@@ -231,9 +267,12 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     J.C2 = f32 ? (const void*)P->d_C2f : (const void*)P->d_C2;
     J.lam1 = P->d_lam1; J.lam2 = P->d_lam2;
     J.part = P->d_part;
+    for (int q = 0; q < 4; ++q) J.Ctc[q] = P->d_Ctc[q];
+    J.scale = P->d_scale;
     J.active = 1;
-    long long pref[12] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
-                          0, P->pass_tiles[3], 0, P->elem_blocks};
+    long long pref[20] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
+                          0, P->pass_tiles[3], 0, P->elem_blocks, 0, P->tc_tiles[0], 0, P->tc_tiles[1],
+                          0, P->tc_tiles[2], 0, P->tc_tiles[3]};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -243,6 +282,29 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     neumann_eigs(L1, G.h[G.ax1], l1.data());
     neumann_eigs(L2, G.h[G.ax2], l2.data());
     std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end());
+    {
+        // spectral scaling of the z-step, rho / (alpha (lam1 + lam2) + rho), in FP64 then FP32
+        std::vector<float> sc((size_t)L1 * L2);
+        for (int i = 0; i < L1; ++i)
+            for (int j = 0; j < L2; ++j)
+                sc[(size_t)i * L2 + j] = (float)(p->rho / (p->alpha * (l1[i] + l2[j]) + p->rho));
+        SAC_CUDA(cudaMemcpyAsync(P->d_scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice, st));
+    }
+    if (P->use_tc) {
+        // pass 0: C1, pass 1: C2, pass 2: C2^T, pass 3: C1^T, split TF32 and pre-arranged
+        std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
+        for (int i = 0; i < L1; ++i)
+            for (int j = 0; j < L1; ++j) C1t[(size_t)i * L1 + j] = C1[(size_t)j * L1 + i];
+        for (int i = 0; i < L2; ++i)
+            for (int j = 0; j < L2; ++j) C2t[(size_t)i * L2 + j] = C2[(size_t)j * L2 + i];
+        const double* Ms[4] = {C1.data(), C2.data(), C2t.data(), C1t.data()};
+        for (int q = 0; q < 4; ++q) {
+            if (P->tc_floats[q] == 0) continue;
+            std::vector<float> arr((size_t)P->tc_floats[q], 0.f);
+            tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
+            SAC_CUDA(cudaMemcpyAsync(P->d_Ctc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
+        }
+    }
     SAC_CUDA(cudaMemcpyAsync(P->d_C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_C1f, C1f.data(), C1f.size() * 4, cudaMemcpyHostToDevice, st));
@@ -293,6 +355,7 @@ static int status_of(const Plan& P, cudaStream_t st, int* qp_capped) {
     SAC_TRY(read_back(s, P.d_status, sizeof(s), st));
     if (qp_capped) *qp_capped = (s[0] & kStQpCap) ? 1 : 0;
     if (s[0] & kStNaN) return SAC_ENAN;
+    if (s[0] & kStTimeout) return SAC_ETIMEOUT;
     return SAC_OK;
 }
 
@@ -369,14 +432,22 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
         AxisLaunch A;
         A.jobs = P.d_job;
         A.njobs = 1;
-        A.prefix = P.d_pref_pass[q];
-        A.total_tiles = P.pass_tiles[q];
         A.pass = q;
         A.prec = prec;
         A.part = P.d_part;
+        A.status = P.d_status;
         A.stream = st;
-        SAC_CUDA(launch_axis_pass(A));
-        if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
+        if (P.use_tc) {
+            A.prefix = P.d_pref_tc[q];
+            A.total_tiles = P.tc_tiles[q];
+            SAC_CUDA(launch_axis_pass_tc(A, P.tc_smem[q]));
+            if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.tc_tiles[3], 5, P.d_out + 16, st));
+        } else {
+            A.prefix = P.d_pref_pass[q];
+            A.total_tiles = P.pass_tiles[q];
+            SAC_CUDA(launch_axis_pass(A));
+            if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
+        }
     }
     return SAC_OK;
 }
@@ -428,6 +499,7 @@ void sac_params_default(sac_params* p) {
     p->prec = SAC_F64;
     p->near_bound = 1e-3;
     p->check_every = 1;
+    p->zstep_kernel = 0;
 }
 
 int sac_version(void) { return SAC_VERSION; }

@@ -1,0 +1,554 @@
+// engine.cu -- batched ADMM over many volumes (Sec. 4.2 per volume):
+//   * jobs are grouped by faces-per-lane class K; each class is one b-step
+//     launch over all its lines (and one list launch), so that every job's
+//     arithmetic is the same as when it runs alone;
+//   * each z-step pass is one launch over the slabs of all jobs;
+//   * a stopping kernel reduces each job's residual norms in a fixed order and
+//     retires it (Job::active = 0) when Eq. admmStop holds or at the cap;
+//     retired jobs' tiles return at once, so the launch sequence stays fixed
+//     and is captured once into a CUDA graph of `chunk` iterations;
+//   * the lines-per-CTA width of each class is tuned on live iterations (the
+//     tiling does not change any result).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "engine.h"
+
+namespace sac {
+
+#define ENG_CUDA(x)                                  \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) {                     \
+            cudaGetLastError();                      \
+            return SAC_ECUDA;                        \
+        }                                            \
+    } while (0)
+#define ENG_TRY(x)                                   \
+    do {                                             \
+        int s_ = (x);                                \
+        if (s_ < 0) return s_;                       \
+    } while (0)
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------- autotuner cache
+static std::mutex g_tune_mu;
+static std::map<long long, int> g_tune;
+static long long tune_key(int K, int prec, int inner_fast) { return ((long long)K << 8) | (prec << 1) | inner_fast; }
+int tuned_lines_per_cta(int K, int prec, int inner_fast, int fallback) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(K, prec, inner_fast));
+    return it == g_tune.end() ? fallback : it->second;
+}
+void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(K, prec, inner_fast)] = W;
+}
+
+// ---------------------------------------------------------------- per-job state block
+struct StateLayout {
+    size_t b32, z, u, t1, t2;          // face arrays
+    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4];
+    size_t bytes;
+};
+
+static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
+    StateLayout s;
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o = off; off = a256(off + n); return o; };
+    const size_t es = (prec == SAC_MIXED) ? 4 : 8;
+    s.b32 = (prec == SAC_MIXED) ? take(es * G.nf) : 0;
+    s.z = take(es * G.nf);
+    s.u = take(es * G.nf);
+    s.t1 = take(es * G.nf);
+    s.t2 = take(es * G.nf);
+    const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+    s.C1 = take(8 * (size_t)L1 * L1);
+    s.C2 = take(8 * (size_t)L2 * L2);
+    s.C1f = take(4 * (size_t)L1 * L1);
+    s.C2f = take(4 * (size_t)L2 * L2);
+    s.l1 = take(8 * (size_t)L1);
+    s.l2 = take(8 * (size_t)L2);
+    s.scale = take(4 * (size_t)L1 * L2);
+    for (int q = 0; q < 4; ++q)
+        s.tc[q] = take(use_tc ? 4 * (size_t)tc_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
+    s.bytes = off;
+    return s;
+}
+
+size_t job_state_bytes(const Geometry& G, int prec, int use_tc) { return state_layout(G, prec, use_tc).bytes; }
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_admm_check(Job* __restrict__ jobs, int njobs, const long long* __restrict__ pref3,
+                             const double* __restrict__ part, double eps_abs, double eps_rel, int max_iter,
+                             double* __restrict__ stats, int* __restrict__ nactive) {
+    __shared__ double red[32 * 5];
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    Job& J = jobs[j];
+    if (!J.active) return;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long t = pref3[j] + threadIdx.x; t < pref3[j + 1]; t += blockDim.x)
+        for (int c = 0; c < 5; ++c) acc[c] += part[t * 5 + c];
+    block_sum<5>(acc, red);
+    if (threadIdx.x == 0) {
+        double* st = stats + (size_t)j * 8;
+        const int it = (int)st[4] + 1;
+        const double rhd = J.rho * J.hd, sqn = sqrt((double)J.nf);
+        const double rp = sqrt(acc[0]), rd = rhd * sqrt(acc[1]);
+        const double nb = sqrt(acc[2]), nz = sqrt(acc[3]), nu = sqrt(acc[4]);
+        const double ep = sqn * eps_abs + eps_rel * fmax(nb, nz);
+        const double ed = sqn * eps_abs + eps_rel * rhd * nu;
+        const bool conv = (rp <= ep) && (rd <= ed);
+        st[0] = rp; st[1] = rd; st[2] = ep; st[3] = ed; st[4] = it; st[5] = conv ? 1.0 : 0.0;
+        if (!(rp == rp) || !(rd == rd)) st[6] = 1.0;   // non-finite
+        if (conv || it >= max_iter || st[6] != 0.0) {
+            J.active = 0;
+        } else {
+            atomicAdd(nactive, 1);
+        }
+    }
+}
+
+// state initialisation: z = b, u = 0 (FP32 state: b32 = z = float(b))
+__global__ void k_init_state(long long n, const double* __restrict__ b, void* b32, void* z, void* u, int f32) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (f32) {
+            const float v = (float)b[i];
+            ((float*)b32)[i] = v;
+            ((float*)z)[i] = v;
+            ((float*)u)[i] = 0.f;
+        } else {
+            ((double*)z)[i] = b[i];
+            ((double*)u)[i] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Engine
+
+size_t Engine::table_bytes(const std::vector<EngineJob>& jobs, const sac_params& p) {
+    (void)p;
+    const size_t nj = jobs.size();
+    long long lines = 0, tiles3 = 0, tiles_ax3 = 0;
+    for (auto& j : jobs) {
+        lines += (long long)j.G.n_outer * j.G.n_inner;
+        tiles3 += tc_pass_tiles(j.G.F, j.G.ax1, j.G.ax2, 3);
+        tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
+    }
+    long long np = 5 * std::max(tiles3, tiles_ax3) + 8;
+    size_t off = 0;
+    off += a256(sizeof(Job) * nj);
+    off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 4 classes) + 8 pass prefixes
+    off += a256(sizeof(unsigned long long) * (size_t)lines);
+    off += a256(sizeof(int) * 16);
+    off += a256(sizeof(double) * (size_t)np);
+    off += a256(sizeof(double) * 8 * nj);
+    return off;
+}
+
+int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* ws, size_t ws_bytes,
+                  cudaStream_t st) {
+    release();
+    p_ = p;
+    caller_ = st;
+    if (in.empty()) return SAC_EINVAL;
+    ENG_TRY(prepare_kernels());
+    if (!st_) ENG_CUDA(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+    if (!ev_in_) ENG_CUDA(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming));
+    if (!ev_out_) ENG_CUDA(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming));
+    // work already queued on the caller's stream (inputs) comes first
+    ENG_CUDA(cudaEventRecord(ev_in_, caller_));
+    ENG_CUDA(cudaStreamWaitEvent(st_, ev_in_, 0));
+    st = st_;
+    if (!ws || ((uintptr_t)ws & 255)) return SAC_EINVAL;
+    if (ws_bytes < table_bytes(in, p)) return SAC_ENOMEM;
+    const int prec = p.prec;
+    // group by K class, stable in the caller's order
+    order_.resize(in.size());
+    for (size_t i = 0; i < in.size(); ++i) order_[i] = (int)i;
+    std::stable_sort(order_.begin(), order_.end(), [&](int a, int b) { return in[a].K < in[b].K; });
+    jobs_.clear();
+    for (int i : order_) jobs_.push_back(in[i]);
+    use_tc_ = (prec == SAC_MIXED && p.zstep_kernel == 0);
+    for (auto& j : jobs_)
+        for (int q = 0; q < 4; ++q)
+            if (!tc_pass_supported(j.G.F, j.G.ax1, j.G.ax2, q)) use_tc_ = 0;
+    // carve the engine tables
+    const size_t nj = jobs_.size();
+    char* base = (char*)ws;
+    size_t off = 0;
+    auto take = [&](size_t n) { char* ptr = base + off; off += a256(n); return ptr; };
+    d_jobs_ = (Job*)take(sizeof(Job) * nj);
+    long long* pref = (long long*)take(sizeof(long long) * (nj + 1) * (4 + 8 + 8));
+    long long lines = 0;
+    for (auto& j : jobs_) { j.nlines = (long long)j.G.n_outer * j.G.n_inner; lines += j.nlines; }
+    d_rlist_ = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)lines);
+    d_rcount_ = (int*)take(sizeof(int) * 16);
+    d_status_ = d_rcount_ + 4;
+    d_nactive_ = d_rcount_ + 5;
+    long long tiles3 = 0, tiles_ax3 = 0;
+    for (auto& j : jobs_) {
+        tiles3 += tc_pass_tiles(j.G.F, j.G.ax1, j.G.ax2, 3);
+        tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
+    }
+    d_part_ = (double*)take(sizeof(double) * (size_t)(5 * std::max(tiles3, tiles_ax3) + 8));
+    d_stats_ = (double*)take(sizeof(double) * 8 * nj);
+    // classes
+    std::vector<long long> hpref((nj + 1) * (4 + 8 + 8), 0);
+    cls_.clear();
+    long long line_off = 0;
+    for (size_t i = 0; i < nj;) {
+        Cls c;
+        c.K = jobs_[i].K;
+        c.first = (int)i;
+        size_t k = i;
+        int maxm = 0, inner_fast = 0;
+        while (k < nj && jobs_[k].K == c.K) {
+            maxm = std::max(maxm, jobs_[k].G.mpe);
+            inner_fast |= (jobs_[k].G.n_inner > 1);
+            ++k;
+        }
+        c.count = (int)(k - i);
+        // lines per CTA: tuned value if known, else 8 (halved until the tile fits)
+        int W = tuned_lines_per_cta(c.K, prec, inner_fast, 8);
+        const size_t ssz = (prec == SAC_MIXED) ? 4 : 8;
+        for (;;) {
+            const int RL = smem_row(maxm + 1, W, 8);
+            if (line_smem_bstep(W, RL, RL, 8, ssz) <= 200 * 1024 || W == 1) break;
+            W >>= 1;
+        }
+        c.W = W;
+        c.RLf = smem_row(maxm + 1, W, 8);
+        if ((int)cls_.size() >= 4) return SAC_EINVAL;
+        c.d_pref = pref + cls_.size() * (nj + 1);
+        long long* hp = hpref.data() + cls_.size() * (nj + 1);
+        hp[0] = 0;
+        c.lines = 0;
+        for (int q = 0; q < c.count; ++q) {
+            const Geometry& G = jobs_[c.first + q].G;
+            hp[q + 1] = hp[q] + line_tiles(G.n_outer, G.n_inner, W);
+            c.lines += jobs_[c.first + q].nlines;
+        }
+        c.tiles = hp[c.count];
+        c.line_off = line_off;
+        line_off += c.lines;
+        cls_.push_back(c);
+        i = k;
+    }
+    for (int q = 0; q < 4; ++q) {
+        d_pref_tc_[q] = pref + (4 + q) * (nj + 1);
+        d_pref_ax_[q] = pref + (8 + q) * (nj + 1);
+        long long* ht = hpref.data() + (4 + q) * (nj + 1);
+        long long* ha = hpref.data() + (8 + q) * (nj + 1);
+        ht[0] = ha[0] = 0;
+        tc_smem_[q] = 0;
+        for (size_t i = 0; i < nj; ++i) {
+            const Geometry& G = jobs_[i].G;
+            ht[i + 1] = ht[i] + tc_pass_tiles(G.F, G.ax1, G.ax2, q);
+            const int axis = (q == 0 || q == 3) ? G.ax1 : G.ax2;
+            ha[i + 1] = ha[i] + axis_pass_tiles(G.F, axis);
+            tc_smem_[q] = std::max(tc_smem_[q], tc_smem_bytes(G.F, G.ax1, G.ax2, q));
+        }
+        tc_tiles_[q] = ht[nj];
+        ax_tiles_[q] = ha[nj];
+    }
+    ENG_CUDA(cudaMemcpyAsync(pref, hpref.data(), hpref.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    // jobs: state layout, tables, initial state
+    std::vector<Job> hj(nj);
+    for (size_t i = 0; i < nj; ++i) {
+        const EngineJob& E = jobs_[i];
+        const Geometry& G = E.G;
+        const StateLayout L = state_layout(G, prec, use_tc_);
+        Job& J = hj[i];
+        memset(&J, 0, sizeof(J));
+        J.nd = G.nd; J.pe = G.pe;
+        for (int a = 0; a < 3; ++a) { J.M[a] = G.M[a]; J.F[a] = G.F[a]; J.h[a] = G.h[a]; }
+        J.ax1 = G.ax1; J.ax2 = G.ax2;
+        J.nf = G.nf; J.nc = G.nc;
+        J.n_outer = G.n_outer; J.mpe = G.mpe; J.n_inner = G.n_inner;
+        J.hd = G.hd; J.hpe = G.hpe;
+        J.alpha = p.alpha; J.rho = p.rho; J.beta = p.beta; J.gamma = p.gamma;
+        J.I1 = E.I1; J.I2 = E.I2;
+        char* s = E.state;
+        J.b = (prec == SAC_MIXED) ? (void*)(s + L.b32) : (void*)E.b;
+        J.z = s + L.z; J.u = s + L.u; J.t1 = s + L.t1; J.t2 = s + L.t2;
+        J.C1 = (prec == SAC_MIXED) ? (const void*)(s + L.C1f) : (const void*)(s + L.C1);
+        J.C2 = (prec == SAC_MIXED) ? (const void*)(s + L.C2f) : (const void*)(s + L.C2);
+        J.lam1 = (const double*)(s + L.l1);
+        J.lam2 = (const double*)(s + L.l2);
+        J.scale = (const float*)(s + L.scale);
+        for (int q = 0; q < 4; ++q) J.Ctc[q] = use_tc_ ? (const void*)(s + L.tc[q]) : nullptr;
+        J.part = d_part_;
+        J.active = 1;
+        if (E.fresh) {
+            // tables (host-computed, FP64 then FP32 / split TF32 copies)
+            const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+            std::vector<double> C1((size_t)L1 * L1), C2((size_t)L2 * L2), l1(L1), l2(L2);
+            dct2_matrix(L1, C1.data());
+            dct2_matrix(L2, C2.data());
+            neumann_eigs(L1, G.h[G.ax1], l1.data());
+            neumann_eigs(L2, G.h[G.ax2], l2.data());
+            std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end()), sc((size_t)L1 * L2);
+            for (int a = 0; a < L1; ++a)
+                for (int c = 0; c < L2; ++c) sc[(size_t)a * L2 + c] = (float)(p.rho / (p.alpha * (l1[a] + l2[c]) + p.rho));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C1f, C1f.data(), C1f.size() * 4, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C2f, C2f.data(), C2f.size() * 4, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.l1, l1.data(), l1.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.l2, l2.data(), l2.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice, st));
+            if (use_tc_) {
+                std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
+                for (int a = 0; a < L1; ++a)
+                    for (int c = 0; c < L1; ++c) C1t[(size_t)a * L1 + c] = C1[(size_t)c * L1 + a];
+                for (int a = 0; a < L2; ++a)
+                    for (int c = 0; c < L2; ++c) C2t[(size_t)a * L2 + c] = C2[(size_t)c * L2 + a];
+                const double* Ms[4] = {C1.data(), C2.data(), C2t.data(), C1t.data()};
+                for (int q = 0; q < 4; ++q) {
+                    const long long nfl = tc_matrix_floats(G.F, G.ax1, G.ax2, q);
+                    if (!nfl) continue;
+                    std::vector<float> arr((size_t)nfl, 0.f);
+                    tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
+                    ENG_CUDA(cudaMemcpyAsync(s + L.tc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
+                }
+            }
+            count_launch();
+            k_init_state<<<256, 256, 0, st>>>(G.nf, E.b, s + L.b32, s + L.z, s + L.u, prec == SAC_MIXED);
+            ENG_CUDA(cudaGetLastError());
+
+        }
+    }
+    ENG_CUDA(cudaMemcpyAsync(d_jobs_, hj.data(), sizeof(Job) * nj, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<double> hs(8 * nj, 0.0);
+        for (size_t i = 0; i < nj; ++i) hs[8 * i + 4] = jobs_[i].iters0;
+        ENG_CUDA(cudaMemcpyAsync(d_stats_, hs.data(), hs.size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * 16, st));
+    ENG_CUDA(cudaStreamSynchronize(st));
+    iters_done_ = 0;
+    return SAC_OK;
+}
+
+int Engine::enqueue_iteration() {
+    const bool mixed = (p_.prec == SAC_MIXED);
+    ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * 4, st_));
+    for (size_t c = 0; c < cls_.size(); ++c) {
+        const Cls& C = cls_[c];
+        LineLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.jobs = d_jobs_ + C.first;
+        L.njobs = C.count;
+        L.prefix = C.d_pref;
+        L.total_tiles = C.tiles;
+        L.W = C.W;
+        L.K = C.K;
+        L.RLc = C.RLf;
+        L.RLf = C.RLf;
+        L.n_sqp = p_.n_sqp;
+        L.near_bound = mixed ? p_.near_bound : 0.0;
+        L.rlist = d_rlist_ + C.line_off;
+        L.rcount = d_rcount_ + c;
+        L.rlist_out = d_rlist_ + C.line_off;
+        L.rcount_out = d_rcount_ + c;
+        L.rcap = (int)C.lines;
+        L.list_blocks = std::min<long long>((C.lines + C.W - 1) / C.W, 4 * 152);
+        L.status = d_status_;
+        L.stream = st_;
+        L.mode = 0;
+        ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
+        L.mode = 1;
+        ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
+    }
+    const int nj = (int)jobs_.size();
+    for (int q = 0; q < 4; ++q) {
+        AxisLaunch A;
+        A.jobs = d_jobs_;
+        A.njobs = nj;
+        A.pass = q;
+        A.prec = mixed ? 1 : 0;
+        A.part = d_part_;
+        A.status = d_status_;
+        A.stream = st_;
+        if (use_tc_) {
+            A.prefix = d_pref_tc_[q];
+            A.total_tiles = tc_tiles_[q];
+            ENG_CUDA(launch_axis_pass_tc(A, tc_smem_[q]));
+        } else {
+            A.prefix = d_pref_ax_[q];
+            A.total_tiles = ax_tiles_[q];
+            ENG_CUDA(launch_axis_pass(A));
+        }
+    }
+    ENG_CUDA(cudaMemsetAsync(d_nactive_, 0, sizeof(int), st_));
+    count_launch();
+    k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, use_tc_ ? d_pref_tc_[3] : d_pref_ax_[3], d_part_, p_.eps_abs,
+                                      p_.eps_rel, p_.max_iter, d_stats_, d_nactive_);
+    ENG_CUDA(cudaGetLastError());
+    return SAC_OK;
+}
+
+int Engine::capture(int chunk) {
+    if (exec_ && graph_chunk_ == chunk) return SAC_OK;
+    if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
+    if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+    ENG_CUDA(cudaStreamBeginCapture(st_, cudaStreamCaptureModeRelaxed));
+    int s = SAC_OK;
+    const long long n0 = sac_launch_count();
+    for (int i = 0; i < chunk && s == SAC_OK; ++i) s = enqueue_iteration();
+    graph_launches_ = sac_launch_count() - n0;
+    count_launch(-graph_launches_);     // captured, not launched
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st_, &g);
+    if (s != SAC_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return SAC_ECUDA;
+    graph_ = g;
+    ENG_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+    graph_chunk_ = chunk;
+    return SAC_OK;
+}
+
+// Autotuner: time one live iteration per candidate lines-per-CTA width of
+// every class (the b-step result does not depend on the width) and keep the
+// fastest for the rest of the run and for later engines of the same class.
+int Engine::tune() {
+    const bool mixed = (p_.prec == SAC_MIXED);
+    const int cands[3] = {2, 4, 8};
+    cudaEvent_t a, b;
+    ENG_CUDA(cudaEventCreate(&a));
+    ENG_CUDA(cudaEventCreate(&b));
+    for (size_t c = 0; c < cls_.size(); ++c) {
+        Cls& C = cls_[c];
+        int inner_fast = 0, maxm = 0;
+        for (int q = 0; q < C.count; ++q) {
+            inner_fast |= (jobs_[C.first + q].G.n_inner > 1);
+            maxm = std::max(maxm, jobs_[C.first + q].G.mpe);
+        }
+        float best = 1e30f;
+        int bestW = C.W;
+        std::vector<long long> hp(C.count + 1);
+        for (int W : cands) {
+            const size_t ssz = mixed ? 4 : 8;
+            const int RL = smem_row(maxm + 1, W, 8);
+            if (line_smem_bstep(W, RL, RL, 8, ssz) > 200 * 1024) continue;
+            hp[0] = 0;
+            for (int q = 0; q < C.count; ++q) {
+                const Geometry& G = jobs_[C.first + q].G;
+                hp[q + 1] = hp[q] + line_tiles(G.n_outer, G.n_inner, W);
+            }
+            ENG_CUDA(cudaMemcpyAsync(C.d_pref, hp.data(), hp.size() * sizeof(long long), cudaMemcpyHostToDevice, st_));
+            C.W = W;
+            C.RLf = RL;
+            C.tiles = hp[C.count];
+            ENG_CUDA(cudaEventRecord(a, st_));
+            ENG_TRY(enqueue_iteration());
+            ENG_CUDA(cudaEventRecord(b, st_));
+            ENG_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            ENG_CUDA(cudaEventElapsedTime(&ms, a, b));
+            ++iters_done_;
+            if (ms < best) { best = ms; bestW = W; }
+        }
+        hp[0] = 0;
+        for (int q = 0; q < C.count; ++q) {
+            const Geometry& G = jobs_[C.first + q].G;
+            hp[q + 1] = hp[q] + line_tiles(G.n_outer, G.n_inner, bestW);
+        }
+        ENG_CUDA(cudaMemcpyAsync(C.d_pref, hp.data(), hp.size() * sizeof(long long), cudaMemcpyHostToDevice, st_));
+        C.W = bestW;
+        C.RLf = smem_row(maxm + 1, bestW, 8);
+        C.tiles = hp[C.count];
+        set_tuned_lines_per_cta(C.K, p_.prec, inner_fast, bestW);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return SAC_OK;
+}
+
+int Engine::run(int max_iter, int chunk) {
+    if (jobs_.empty()) return SAC_EINVAL;
+    if (chunk < 1) chunk = 1;
+    ENG_CUDA(cudaEventRecord(ev_in_, caller_));
+    ENG_CUDA(cudaStreamWaitEvent(st_, ev_in_, 0));
+    int remaining = max_iter;
+    if (p_.autotune && !tuned_) {       // autotune on the first live iterations
+        tuned_ = true;
+        const int before = iters_done_;
+        ENG_TRY(tune());
+        remaining -= (iters_done_ - before);
+        if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; cudaGraphDestroy(graph_); graph_ = nullptr; }
+    }
+    ENG_TRY(capture(chunk));
+    int nact = 1;
+    while (remaining > 0 && nact > 0) {
+        ENG_CUDA(cudaGraphLaunch(exec_, st_));
+        count_launch(graph_launches_);
+        remaining -= chunk;
+        iters_done_ += chunk;
+        ENG_CUDA(cudaMemcpyAsync(&nact, d_nactive_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+        ENG_CUDA(cudaStreamSynchronize(st_));
+    }
+    int s = 0;
+    ENG_CUDA(cudaMemcpyAsync(&s, d_status_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    ENG_CUDA(cudaStreamSynchronize(st_));
+    if (s & kStNaN) return SAC_ENAN;
+    if (s & kStTimeout) return SAC_ETIMEOUT;
+    return SAC_OK;
+}
+
+int Engine::stats(std::vector<EngineStats>* out) {
+    const size_t nj = jobs_.size();
+    std::vector<double> h(8 * nj);
+    ENG_CUDA(cudaMemcpyAsync(h.data(), d_stats_, h.size() * 8, cudaMemcpyDeviceToHost, st_));
+    std::vector<Job> hj(nj);
+    ENG_CUDA(cudaMemcpyAsync(hj.data(), d_jobs_, sizeof(Job) * nj, cudaMemcpyDeviceToHost, st_));
+    ENG_CUDA(cudaStreamSynchronize(st_));
+    out->assign(nj, EngineStats{});
+    for (size_t i = 0; i < nj; ++i) {
+        EngineStats& S = (*out)[order_[i]];
+        const double* r = h.data() + 8 * i;
+        S.r_pri = r[0]; S.r_dual = r[1]; S.eps_pri = r[2]; S.eps_dual = r[3];
+        S.iters = (int)r[4];
+        S.converged = r[5] != 0.0;
+        S.done = !hj[i].active;
+    }
+    return SAC_OK;
+}
+
+int Engine::finish() {
+    if (p_.prec == SAC_MIXED) {
+        for (auto& E : jobs_) {
+            const StateLayout L = state_layout(E.G, p_.prec, use_tc_);
+            ENG_CUDA(launch_cast_back(E.G.nf, (const float*)(E.state + L.b32), E.b, st_));
+        }
+    }
+    // later work on the caller's stream sees the results
+    ENG_CUDA(cudaEventRecord(ev_out_, st_));
+    ENG_CUDA(cudaStreamWaitEvent(caller_, ev_out_, 0));
+    ENG_CUDA(cudaStreamSynchronize(st_));
+    return SAC_OK;
+}
+
+void Engine::destroy_stream() {
+    if (ev_in_) { cudaEventDestroy(ev_in_); ev_in_ = nullptr; }
+    if (ev_out_) { cudaEventDestroy(ev_out_); ev_out_ = nullptr; }
+    if (st_) { cudaStreamSynchronize(st_); cudaStreamDestroy(st_); st_ = nullptr; }
+}
+
+void Engine::release() {
+    if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
+    if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+    graph_chunk_ = 0;
+    tuned_ = false;
+    jobs_.clear();
+    cls_.clear();
+}
+
+}  // namespace sac

@@ -1,0 +1,102 @@
+// engine.h -- batched ADMM engine: many volumes (jobs), one launch per phase
+// over all their lines / slabs, device-side per-job stopping, CUDA graphs.
+// Used by the sac_batch_* entry points and by the serving runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <map>
+#include <vector>
+
+#include "plan.h"
+
+extern "C" long long sac_launch_count(void);
+
+namespace sac {
+
+// Device memory of one job's solver state (caller- or pool-provided block).
+size_t job_state_bytes(const Geometry& G, int prec, int use_tc);
+
+struct EngineJob {
+    Geometry G;
+    const void* I1;      // device images (float for SAC_MIXED, double for SAC_F64)
+    const void* I2;
+    double* b;           // device FP64 field: in b^0, out result
+    char* state;         // device block of job_state_bytes(G, prec, use_tc) bytes
+    int K;               // faces per lane class
+    int fresh = 1;       // 1: initialise the state (z = b, u = 0) and the tables
+    int iters0 = 0;      // iterations already done (continuing jobs)
+    // filled by the engine
+    long long nlines;
+};
+
+struct EngineStats {     // per job, host copy
+    int iters;
+    int converged;
+    int done;
+    double r_pri, r_dual, eps_pri, eps_dual;
+};
+
+class Engine {
+public:
+    // bytes of the engine tables (job table, prefixes, lists, partial sums)
+    static size_t table_bytes(const std::vector<EngineJob>& jobs, const sac_params& p);
+    // lay the engine out in `ws` (>= table_bytes) and upload the job states
+    // (z = b, u = 0, DCT tables); returns a sac_status
+    int build(const std::vector<EngineJob>& jobs, const sac_params& p, void* ws, size_t ws_bytes,
+              cudaStream_t st);
+    // run ADMM iterations until every job stopped or max_iter more iterations;
+    // replays a CUDA graph of `chunk` iterations, one host sync per chunk
+    int run(int max_iter, int chunk);
+    // copy per-job stats to the host
+    int stats(std::vector<EngineStats>* out);
+    // write the FP64 results of the finished jobs (mixed: FP32 state -> b)
+    int finish();
+    int njobs() const { return (int)jobs_.size(); }
+    void release();
+    void destroy_stream();
+    ~Engine() { release(); destroy_stream(); }
+
+private:
+    int enqueue_iteration();
+    int capture(int chunk);
+    int tune();
+    std::vector<EngineJob> jobs_;   // grouped by K class
+    std::vector<int> order_;        // engine index -> caller index
+    sac_params p_{};
+    cudaStream_t st_ = nullptr;      // the engine's own stream (captures need a non-legacy stream)
+    cudaStream_t caller_ = nullptr;  // the caller's stream, joined by events
+    cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
+    int use_tc_ = 1;
+    // classes
+    struct Cls {
+        int K, W, RLf, first, count;
+        long long tiles, lines, line_off;
+        long long* d_pref;
+    };
+    std::vector<Cls> cls_;
+    Job* d_jobs_ = nullptr;
+    long long* d_pref_tc_[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long* d_pref_ax_[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long tc_tiles_[4] = {0, 0, 0, 0}, ax_tiles_[4] = {0, 0, 0, 0};
+    size_t tc_smem_[4] = {0, 0, 0, 0};
+    unsigned long long* d_rlist_ = nullptr;
+    int* d_rcount_ = nullptr;      // one counter per class
+    int* d_status_ = nullptr;
+    int* d_nactive_ = nullptr;
+    double* d_part_ = nullptr;
+    double* d_stats_ = nullptr;    // [njobs][8]
+    cudaGraphExec_t exec_ = nullptr;
+    cudaGraph_t graph_ = nullptr;
+    int graph_chunk_ = 0;
+    long long graph_launches_ = 0;
+    int iters_done_ = 0;
+    bool tuned_ = false;
+};
+
+// process-wide choice of lines per CTA for a line class (autotuned)
+int tuned_lines_per_cta(int K, int prec, int inner_fast, int fallback);
+void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W);
+
+}  // namespace sac

@@ -9,8 +9,6 @@ static cudaError_t launch_eval_k(const LineLaunch& L, int what, const double* bs
                                  double* part) {
     auto kern = k_line_eval<T, S, K>;
     size_t sm = line_smem_eval(L.W, L.RLc, L.RLf, sizeof(S));
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     if (L.total_tiles <= 0) return cudaSuccess;
     count_launch();
     kern<<<(unsigned)L.total_tiles, 32 * L.W, sm, L.stream>>>(L.jobs, L.njobs, L.prefix, L.W, L.RLc, L.RLf, what,
@@ -39,8 +37,6 @@ static cudaError_t launch_solve_k(const LineLaunch& L, int precond, const double
                                   const double* rhs, double* out) {
     auto kern = k_line_solve<K>;
     size_t sm = (size_t)3 * L.W * L.RLf * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     if (L.total_tiles <= 0) return cudaSuccess;
     count_launch();
     kern<<<(unsigned)L.total_tiles, 32 * L.W, sm, L.stream>>>(L.jobs, L.njobs, L.prefix, L.W, L.RLf, precond, diag,
@@ -59,4 +55,21 @@ cudaError_t launch_line_solve(const LineLaunch& L, int precond, const double* di
     }
 }
 
+}  // namespace sac
+
+namespace sac {
+cudaError_t prepare_line_eval() {
+    const void* ks[] = {
+        (const void*)k_line_eval<double, double, 3>, (const void*)k_line_eval<double, double, 5>,
+        (const void*)k_line_eval<double, double, 9>, (const void*)k_line_eval<double, double, 15>,
+        (const void*)k_line_eval<float, float, 3>, (const void*)k_line_eval<float, float, 5>,
+        (const void*)k_line_eval<float, float, 9>, (const void*)k_line_eval<float, float, 15>,
+        (const void*)k_line_solve<3>, (const void*)k_line_solve<5>, (const void*)k_line_solve<9>,
+        (const void*)k_line_solve<15>};
+    for (const void* k : ks) {
+        cudaError_t e = allow_max_dyn_smem(k);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 }  // namespace sac

@@ -49,29 +49,51 @@ __device__ __forceinline__ TileInfo tile_info(const Job& J, long long t, int W) 
     return ti;
 }
 
+// asynchronous global -> shared copy of one 4- or 8-byte element (cp.async:
+// no register round trip, so a thread keeps many copies in flight)
+template <typename S>
+__device__ __forceinline__ void cp_async_elem(S* sdst, const S* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    if (sizeof(S) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // coalesced cooperative load of `len` entries of each of the tile's lines
+// (W is a power of two); completes with cp_async_wait_all + __syncthreads
 template <typename S>
 __device__ __forceinline__ void stage_rows(S* __restrict__ s, int RL, const S* __restrict__ g, long long base,
                                            const TileInfo& ti, int W, int len, int n_inner) {
-    const int total = W * len;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int w, p;
-        long long ga;
-        if (ti.inner_fast) { w = e % W; p = e / W; ga = base + (long long)p * n_inner + w; }
-        else { w = e / len; p = e - w * len; ga = base + (long long)w * len + p; }
-        if (w < ti.nl) s[w * RL + p] = g[ga];
+    if (ti.inner_fast) {
+        // W consecutive elements of every PE row: thread -> (row p, line w)
+        const int lw = __ffs(W) - 1;
+        const int w = threadIdx.x & (W - 1);
+        const int pstep = blockDim.x >> lw;
+        if (w < ti.nl)
+            for (int p = threadIdx.x >> lw; p < len; p += pstep)
+                cp_async_elem(s + w * RL + p, g + base + (long long)p * n_inner + w);
+    } else {
+        // contiguous lines: warp -> line, lanes along the line
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int w = threadIdx.x >> 5; w < ti.nl; w += nw)
+            for (int p = lane; p < len; p += 32) cp_async_elem(s + w * RL + p, g + base + (long long)w * len + p);
     }
 }
 template <typename S>
 __device__ __forceinline__ void unstage_rows(const S* __restrict__ s, int RL, S* __restrict__ g, long long base,
                                              const TileInfo& ti, int W, int len, int n_inner) {
-    const int total = W * len;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int w, p;
-        long long ga;
-        if (ti.inner_fast) { w = e % W; p = e / W; ga = base + (long long)p * n_inner + w; }
-        else { w = e / len; p = e - w * len; ga = base + (long long)w * len + p; }
-        if (w < ti.nl) g[ga] = s[w * RL + p];
+    if (ti.inner_fast) {
+        const int lw = __ffs(W) - 1;
+        const int w = threadIdx.x & (W - 1);
+        const int pstep = blockDim.x >> lw;
+        if (w < ti.nl)
+            for (int p = threadIdx.x >> lw; p < len; p += pstep) g[base + (long long)p * n_inner + w] = s[w * RL + p];
+    } else {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int w = threadIdx.x >> 5; w < ti.nl; w += nw)
+            for (int p = lane; p < len; p += 32) g[base + (long long)w * len + p] = s[w * RL + p];
     }
 }
 // per-warp load of one line (strided by `stride`)
@@ -452,8 +474,8 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
                 T sp1 = (k + 1 < K) ? xh[k + 1] : sn;
                 T dp = (sp1 - xh[k]) * inv_h;
                 T tl = T(INFINITY);
-                if (dp < T(0)) tl = (T(-1) - dc[k]) / dp;
-                else if (dp > T(0)) tl = (T(1) - dc[k]) / dp;
+                if (dp < T(0)) tl = fdiv(T(-1) - dc[k], dp);
+                else if (dp > T(0)) tl = fdiv(T(1) - dc[k], dp);
                 blocked |= (tl < T(1)) || !(tl == tl);
             }
         }
@@ -516,6 +538,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_bstep(const Job
     stage_rows<S>(sB, RLf, (const S*)J.b, ti.f0, ti, W, J.mpe + 1, J.n_inner);
     stage_rows<S>(sZ, RLf, (const S*)J.z, ti.f0, ti, W, J.mpe + 1, J.n_inner);
     stage_rows<S>(sU, RLf, (const S*)J.u, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    cp_async_wait_all();
     __syncthreads();
     if (w < ti.nl) {
         const bool queue = bstep_line_fast<T, S, K>(J, n_sqp, near_bound, sI1 + w * RLc, sI2 + w * RLc,
@@ -607,6 +630,7 @@ __global__ void __launch_bounds__(256) k_line_eval(const Job* __restrict__ jobs,
     stage_rows<S>(sI1, RLc, (const S*)J.I1, ti.c0, ti, W, J.mpe, J.n_inner);
     stage_rows<S>(sI2, RLc, (const S*)J.I2, ti.c0, ti, W, J.mpe, J.n_inner);
     stage_rows<double>(sB, RLf, bsrc, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    cp_async_wait_all();
     __syncthreads();
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     double* sG = sB;      // reuse the b rows for the gradient / diagonal output
@@ -711,6 +735,7 @@ __global__ void __launch_bounds__(256) k_line_solve(const Job* __restrict__ jobs
     stage_rows<double>(sD, RLf, diag, ti.f0, ti, W, J.mpe + 1, J.n_inner);
     stage_rows<double>(sO, RLf, off, ti.f0, ti, W, J.mpe + 1, J.n_inner);
     stage_rows<double>(sR, RLf, rhs, ti.f0, ti, W, J.mpe + 1, J.n_inner);
+    cp_async_wait_all();
     __syncthreads();
     if (w < ti.nl) {
         const int m = J.mpe;
@@ -771,13 +796,29 @@ __global__ void __launch_bounds__(256) k_line_solve(const Job* __restrict__ jobs
 
 // ------------------------------------------------------------------------ launchers
 
+// kernel attributes (largest dynamic shared memory) are set once per
+// kernel, outside any stream capture (prepare_* functions)
+
+template <typename T, typename S, int K>
+cudaError_t prepare_bstep_k() {
+    cudaError_t e = allow_max_dyn_smem((const void*)k_bstep<T, S, K>);
+    if (e != cudaSuccess) return e;
+    return allow_max_dyn_smem((const void*)k_bstep_list<T, S, K>);
+}
+template <typename T, typename S>
+cudaError_t prepare_bstep_t() {
+    cudaError_t e;
+    if ((e = prepare_bstep_k<T, S, 3>()) != cudaSuccess) return e;
+    if ((e = prepare_bstep_k<T, S, 5>()) != cudaSuccess) return e;
+    if ((e = prepare_bstep_k<T, S, 9>()) != cudaSuccess) return e;
+    return prepare_bstep_k<T, S, 15>();
+}
+
 template <typename T, typename S, int K>
 cudaError_t launch_bstep_k(const LineLaunch& L) {
     if (L.mode == 0) {
         auto kern = k_bstep<T, S, K>;
         size_t sm = (size_t)L.W * (2 * L.RLc + 3 * L.RLf) * sizeof(S);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
         if (L.total_tiles <= 0) return cudaSuccess;
         count_launch();
         kern<<<(unsigned)L.total_tiles, 32 * L.W, sm, L.stream>>>(L.jobs, L.njobs, L.prefix, L.W, L.RLc, L.RLf,
@@ -787,8 +828,6 @@ cudaError_t launch_bstep_k(const LineLaunch& L) {
     }
     auto kern = k_bstep_list<T, S, K>;
     size_t sm = line_smem_bstep(L.W, L.RLc, L.RLf, sizeof(T), sizeof(S));
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     if (L.list_blocks <= 0) return cudaSuccess;
     count_launch();
     kern<<<(unsigned)L.list_blocks, 32 * L.W, sm, L.stream>>>(L.jobs, L.W, L.RLc, L.RLf, L.n_sqp, L.rlist,

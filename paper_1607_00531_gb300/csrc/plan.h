@@ -36,12 +36,19 @@ struct Plan {
     int prec;                 // SAC_F64 / SAC_MIXED
     int W, K, RLf;            // line kernels: lines per CTA, faces per lane, smem row
     long long line_tiles, pass_tiles[4], elem_blocks;
+    int use_tc;                // tensor-core z-step passes
+    long long tc_tiles[4];
+    long long tc_floats[4];
+    size_t tc_smem[4];
     int rcap;
     // device pointers inside ws
     Job* d_job;
     long long* d_pref_line;
     long long* d_pref_pass[4];
     long long* d_pref_elem;
+    long long* d_pref_tc[4];
+    float* d_Ctc[4];
+    float* d_scale;
     int* d_status;
     int* d_rcount;
     unsigned long long* d_rlist;

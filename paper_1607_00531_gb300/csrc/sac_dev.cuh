@@ -42,6 +42,8 @@ struct Job {
     const void* C2;    // DCT-II matrix along ax2
     const double* lam1;  // eigenvalues 4/h^2 sin^2(pi k / (2 m)) along ax1
     const double* lam2;
+    const void* Ctc[4];  // tensor-core z-step: split TF32 DCT matrices per pass
+    const float* scale;  // [k1][k2] = rho / (alpha (lam1[k1] + lam2[k2]) + rho), FP32
     double* part;      // per-block partial sums of this job
     int active;        // 0: tiles of this job return at once
     int pad_;
@@ -143,6 +145,11 @@ __device__ __forceinline__ void seg_incl_scan(T (&v)[K], const bool (&flag)[K]) 
     }
 }
 
+// ---------------------------------------------------------------- division
+// FP32: the hardware reciprocal (about 1 ulp); FP64: IEEE division.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 // ---------------------------------------------------------------- tridiagonal solve
 //
 // Solves a_i x_{i-1} + d_i x_i + c_i x_{i+1} = r_i for the warp's 32*K rows
@@ -163,14 +170,14 @@ __device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[
     // forward: rows 0 and 1 normalised; row i >= 2 rewritten as
     // x_i + a_i x_0 + c_i x_{i+1} = r_i
     {
-        T inv = T(1) / d[0];
+        T inv = fdiv(T(1), d[0]);
         a[0] *= inv; c[0] *= inv; r[0] *= inv;
-        inv = T(1) / d[1];
+        inv = fdiv(T(1), d[1]);
         a[1] *= inv; c[1] *= inv; r[1] *= inv;
     }
 #pragma unroll
     for (int i = 2; i < K; ++i) {
-        T inv = T(1) / (d[i] - a[i] * c[i - 1]);
+        T inv = fdiv(T(1), d[i] - a[i] * c[i - 1]);
         r[i] = (r[i] - a[i] * r[i - 1]) * inv;
         c[i] = c[i] * inv;
         a[i] = -a[i] * a[i - 1] * inv;
@@ -184,7 +191,7 @@ __device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[
     }
     // row 0: x_0 + a_0 x_{prev last} + c_0 x_{K-1} = r_0
     {
-        T inv = T(1) / (T(1) - c[0] * a[1]);
+        T inv = fdiv(T(1), T(1) - c[0] * a[1]);
         r[0] = (r[0] - c[0] * r[1]) * inv;
         c[0] = -c[0] * c[1] * inv;
         a[0] = a[0] * inv;
@@ -202,12 +209,12 @@ __device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[
         if (lane == 0) { pA = 0; pB = 1; pC = 0; pR = 0; }
         if (lane == 31) { nA = 0; nB = 1; nC = 0; nR = 0; }
         // even row
-        T k1 = eA / pB, k2 = eC / oB;
+        T k1 = fdiv(eA, pB), k2 = fdiv(eC, oB);
         T neA = -k1 * pA, neC = -k2 * oC;
         T neB = eB - k1 * pC - k2 * oA;
         T neR = eR - k1 * pR - k2 * oR;
         // odd row
-        T k3 = oA / eB, k4 = oC / nB;
+        T k3 = fdiv(oA, eB), k4 = fdiv(oC, nB);
         T noA = -k3 * eA, noC = -k4 * nC;
         T noB = oB - k3 * eC - k4 * nA;
         T noR = oR - k3 * eR - k4 * nR;
@@ -227,18 +234,18 @@ __device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[
         T noC = __shfl_down_sync(kFull, oC, s), noR = __shfl_down_sync(kFull, oR, s);
         if (lane < s) { peA = 0; peB = 1; peC = 0; peR = 0; poA = 0; poB = 1; poC = 0; poR = 0; }
         if (lane + s > 31) { neA = 0; neB = 1; neC = 0; neR = 0; noA = 0; noB = 1; noC = 0; noR = 0; }
-        T k1 = eA / peB, k2 = eC / neB;
+        T k1 = fdiv(eA, peB), k2 = fdiv(eC, neB);
         T xA = -k1 * peA, xC = -k2 * neC;
         T xB = eB - k1 * peC - k2 * neA;
         T xR = eR - k1 * peR - k2 * neR;
-        T k3 = oA / poB, k4 = oC / noB;
+        T k3 = fdiv(oA, poB), k4 = fdiv(oC, noB);
         T yA = -k3 * poA, yC = -k4 * noC;
         T yB = oB - k3 * poC - k4 * noA;
         T yR = oR - k3 * poR - k4 * noR;
         eA = xA; eB = xB; eC = xC; eR = xR;
         oA = yA; oB = yB; oC = yC; oR = yR;
     }
-    T x0 = eR / eB, xl = oR / oB;
+    T x0 = fdiv(eR, eB), xl = fdiv(oR, oB);
     r[0] = x0;
     r[K - 1] = xl;
 #pragma unroll

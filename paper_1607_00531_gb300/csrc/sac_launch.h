@@ -11,6 +11,25 @@ struct Job;
 // number of kernels launched by this library (instrumentation)
 void count_launch(long long n = 1);
 
+// set the kernels' launch attributes once per process, before any launch or
+// stream capture (capi.cu); returns a sac_status
+int prepare_kernels();
+// allow a kernel the device's opt-in shared memory minus its static part
+inline cudaError_t allow_max_dyn_smem(const void* k) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+cudaError_t prepare_bstep_f64();
+cudaError_t prepare_bstep_f32();
+cudaError_t prepare_bstep_mixed();
+cudaError_t prepare_line_eval();
+cudaError_t prepare_axis_tc();
+
 // Launch description of a line kernel (one warp per PE line, W lines per CTA).
 struct LineLaunch {
     const Job* jobs;             // device array of jobs
@@ -78,9 +97,17 @@ struct AxisLaunch {
     int pass;                   // see zstep_kernels.cu
     int prec;                   // 0 FP64, 1 FP32
     double* part;               // pass 3: 5 partial sums per CTA
+    int* status;
     cudaStream_t stream;
 };
 cudaError_t launch_axis_pass(const AxisLaunch& A);
+// tensor-core (tcgen05) passes, FP32 storage, split-TF32 arithmetic
+cudaError_t launch_axis_pass_tc(const AxisLaunch& A, size_t smem);
+long long tc_pass_tiles(const int F[3], int ax1, int ax2, int pass);
+bool tc_pass_supported(const int F[3], int ax1, int ax2, int pass);
+long long tc_matrix_floats(const int F[3], int ax1, int ax2, int pass);
+void tc_arrange_matrix(const int F[3], int ax1, int ax2, int pass, const double* M, float* out);
+size_t tc_smem_bytes(const int F[3], int ax1, int ax2, int pass);
 // tiles of one pass for a job with face dims F, non-PE axes ax1/ax2
 long long axis_pass_tiles(const int F[3], int axis);
 

@@ -34,7 +34,7 @@ class SacParams(ctypes.Structure):
                  "eps_grad", "gn_rel_grad")] + \
                [(n, ctypes.c_int) for n in ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "prec")] + \
                [("near_bound", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("zstep_kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class SacError(RuntimeError):
@@ -68,6 +68,21 @@ def lib():
             "sac_hessvec": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sac_precond_solve": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, sz, vp]),
             "sac_gnpcg_solve": (ctypes.c_int, [G, P, vp, vp, vp, ip, dp, dp, dp, vp, sz, vp]),
+            "sac_batch_workspace_bytes": (sz, [ctypes.c_int, G, P]),
+            "sac_batch_create": (ctypes.c_int, [ctypes.c_int, G, P, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                ctypes.POINTER(vp), vp, sz, vp, ctypes.POINTER(vp)]),
+            "sac_batch_run": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+            "sac_batch_stats": (ctypes.c_int, [vp, ip, ip, dp, dp]),
+            "sac_batch_finish": (ctypes.c_int, [vp]),
+            "sac_batch_destroy": (None, [vp]),
+            "sac_server_request_bytes": (sz, [P, G]),
+            "sac_server_create": (ctypes.c_int, [P, vp, sz, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+            "sac_server_submit": (ctypes.c_int, [vp, G, vp, vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "sac_server_step": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip]),
+            "sac_server_poll": (ctypes.c_int, [vp, ctypes.c_longlong, ip, ip, ip, dp]),
+            "sac_server_fetch": (ctypes.c_int, [vp, ctypes.c_longlong, dp]),
+            "sac_server_totals": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "sac_server_destroy": (None, [vp]),
             "sac_profile_enable": (ctypes.c_int, [ctypes.c_int]),
             "sac_profile_read": (ctypes.c_int, [dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
             "sac_launch_count": (ctypes.c_longlong, []),
@@ -285,3 +300,128 @@ def profile_read(reset=True):
 
 def launch_count():
     return int(lib().sac_launch_count())
+
+
+def _grid_array(grids):
+    arr = (SacGrid * len(grids))()
+    for i, g in enumerate(grids):
+        arr[i] = g
+    return arr
+
+
+def batch_workspace_bytes(grids, p):
+    return int(lib().sac_batch_workspace_bytes(len(grids), _grid_array(grids), ctypes.byref(p)))
+
+
+class Batch:
+    """Many volumes solved by ADMM together (one launch per phase over all of
+    them, device-side per-volume stopping, CUDA-graph replay).  bs[j] holds
+    b^0 and receives the result after finish()."""
+
+    def __init__(self, grids, p, I1s, I2s, bs, ws=None, stream=None):
+        n = len(grids)
+        for g, I1, I2 in zip(grids, I1s, I2s):
+            _check_inputs(g, p, I1, I2)
+        self.n, self.p = n, p
+        self._keep = (list(I1s), list(I2s), list(bs))
+        nbytes = batch_workspace_bytes(grids, p)
+        if nbytes == 0:
+            raise SacError("sac_batch_workspace_bytes", SAC_EINVAL)
+        self.ws = ws if ws is not None else _torch().empty(nbytes, dtype=_torch().uint8, device="cuda")
+        V = ctypes.c_void_p * n
+        h = ctypes.c_void_p()
+        _check("sac_batch_create", lib().sac_batch_create(
+            n, _grid_array(grids), ctypes.byref(p), V(*[_ptr(x) for x in I1s]), V(*[_ptr(x) for x in I2s]),
+            V(*[_ptr(x) for x in bs]), _ptr(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def run(self, max_iter, chunk=10):
+        return _check("sac_batch_run", lib().sac_batch_run(self.h, int(max_iter), int(chunk)))
+
+    def stats(self):
+        n = self.n
+        it, cv = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        rp, rd = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        _check("sac_batch_stats", lib().sac_batch_stats(self.h, it, cv, rp, rd))
+        return dict(iters=np.array(it[:]), converged=np.array(cv[:], dtype=bool), r_pri=np.array(rp[:]),
+                    r_dual=np.array(rd[:]))
+
+    def finish(self):
+        return _check("sac_batch_finish", lib().sac_batch_finish(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sac_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching SAC server over a device-memory pool (the
+    admission budget).  submit() takes host (numpy) images; step() admits,
+    iterates and retires; fetch() returns a finished field as numpy."""
+
+    def __init__(self, p, pool_bytes, max_jobs=64, stream=None):
+        torch = _torch()
+        self.p = p
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        _check("sac_server_create", lib().sac_server_create(ctypes.byref(p), _ptr(self.pool), self.pool.numel(),
+                                                            int(max_jobs), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.grids = {}
+
+    def submit(self, g, I1, I2):
+        dt = np.float32 if self.p.prec == SAC_MIXED else np.float64
+        a1 = np.ascontiguousarray(I1, dtype=dt)
+        a2 = np.ascontiguousarray(I2, dtype=dt)
+        t = ctypes.c_longlong(0)
+        _check("sac_server_submit", lib().sac_server_submit(self.h, ctypes.byref(g), a1.ctypes.data_as(ctypes.c_void_p),
+                                                            a2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+        self.grids[t.value] = g
+        return t.value
+
+    def step(self, iters, chunk=10):
+        nr, nq = ctypes.c_int(0), ctypes.c_int(0)
+        _check("sac_server_step", lib().sac_server_step(self.h, int(iters), int(chunk), ctypes.byref(nr),
+                                                        ctypes.byref(nq)))
+        return nr.value, nq.value
+
+    def poll(self, ticket):
+        st, it, cv = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        tm = (ctypes.c_double * 3)()
+        _check("sac_server_poll", lib().sac_server_poll(self.h, ticket, ctypes.byref(st), ctypes.byref(it),
+                                                        ctypes.byref(cv), tm))
+        return dict(state=st.value, iters=it.value, converged=bool(cv.value), t_submit=tm[0], t_admit=tm[1],
+                    t_done=tm[2])
+
+    def fetch(self, ticket):
+        g = self.grids.pop(ticket)
+        out = np.zeros(face_shape(g))
+        _check("sac_server_fetch", lib().sac_server_fetch(self.h, ticket,
+                                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def request_bytes(self, g):
+        return int(lib().sac_server_request_bytes(ctypes.byref(self.p), ctypes.byref(g)))
+
+    def totals(self):
+        t = (ctypes.c_longlong * 3)()
+        _check("sac_server_totals", lib().sac_server_totals(self.h, t))
+        return dict(iters=t[0], faces_iters=t[1], pool_used=t[2])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sac_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""Batched ADMM (one launch per phase over many volumes): each volume's
+result must equal its solo result, for mixed grid sizes in one batch, and
+the FP64 batch must match the CPU oracle (Sec. 4.2 per volume)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00531_gb300 import phantoms as ph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sac():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00531_gb300 import build, sac as S
+    build.build()
+    return S
+
+
+def volumes():
+    # different classes of line length (faces per lane 3, 5, 9), 2D and 3D, PE axes
+    specs = [((24, 40), 1, 1), ((10, 70, 9), 1, 2), ((12, 150), 1, 3), ((8, 9, 30), 2, 4),
+             ((6, 260, 5), 1, 5), ((30, 33), 1, 6)]
+    out = []
+    for m, pe, seed in specs:
+        w = ph.small_workload(m, pe, seed=seed, peak_px=2.0, max_d=0.5)
+        out.append(ph.make_pair(w))
+    return out
+
+
+def cu(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+def test_batch_equals_solo(sac, prec):
+    K = 12
+    vols = volumes()
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, check_every=K)
+    grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
+    I1s = [cu(d["I1"], dt) for d in vols]
+    I2s = [cu(d["I2"], dt) for d in vols]
+    bs = [torch.zeros(sac.face_shape(g), dtype=torch.float64, device="cuda") for g in grids]
+    bt = sac.Batch(grids, p, I1s, I2s, bs)
+    bt.run(K + 5, chunk=5)
+    st = bt.stats()
+    bt.finish()
+    bt.close()
+    assert np.all(st["iters"] == K)
+    for g, I1, I2, bb in zip(grids, I1s, I2s, bs):
+        b = torch.zeros_like(bb)
+        sac.admm_solve(g, p, I1, I2, b)
+        diff = (b - bb).abs().max().item()
+        assert diff <= 1e-12 * max(b.abs().max().item(), 1e-30), diff
+
+
+def test_batch_f64_matches_oracle(sac):
+    K = 10
+    vols = volumes()[:3]
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec="f64")
+    grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
+    bs = [torch.zeros(sac.face_shape(g), dtype=torch.float64, device="cuda") for g in grids]
+    bt = sac.Batch(grids, p, [cu(d["I1"], torch.float64) for d in vols], [cu(d["I2"], torch.float64) for d in vols], bs)
+    bt.run(K)
+    bt.finish()
+    for d, bb in zip(vols, bs):
+        og = oracle.Grid(d["m"], d["h"], d["pe"])
+        ref = oracle.admm(og, oracle.Params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0),
+                          d["I1"], d["I2"], np.zeros(og.face_shape))
+        assert np.linalg.norm(bb.cpu().numpy() - ref["b"]) <= 1e-9 * np.linalg.norm(ref["b"])
+
+
+def test_batch_stops_each_volume_on_its_own_residuals(sac):
+    vols = volumes()[:4]
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=300, eps_abs=0.0, eps_rel=1e-3, prec="mixed", autotune=1)
+    grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
+    bs = [torch.zeros(sac.face_shape(g), dtype=torch.float64, device="cuda") for g in grids]
+    bt = sac.Batch(grids, p, [cu(d["I1"], torch.float32) for d in vols], [cu(d["I2"], torch.float32) for d in vols], bs)
+    bt.run(300, chunk=10)
+    st = bt.stats()
+    bt.finish()
+    assert np.all((st["converged"]) | (st["iters"] == 300))
+    assert len(set(st["iters"].tolist())) > 1        # volumes stop at different iterations
+    # a converged volume's final residuals satisfy the stopping rule it was retired by
+    for g, bb, it, cv in zip(grids, bs, st["iters"], st["converged"]):
+        b = torch.zeros_like(bb)
+        q = sac.params(alpha=1.0, rho=100.0, max_iter=int(it), eps_abs=0.0, eps_rel=0.0, prec="mixed")
+        d = vols[grids.index(g)]
+        sac.admm_solve(g, q, cu(d["I1"], torch.float32), cu(d["I2"], torch.float32), b)
+        assert (b - bb).abs().max().item() <= 1e-12 * max(b.abs().max().item(), 1e-30)

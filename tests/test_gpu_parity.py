@@ -210,3 +210,48 @@ def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
     J_ref = oracle.objective(og, op, d["I1"], d["I2"], ref["b"])["J"]
     J_mix = oracle.objective(og, op, d["I1"], d["I2"], bb)["J"]
     assert abs(J_mix - J_ref) <= 1e-6 * abs(J_ref)
+
+
+# ---------------------------------------------------------------- tensor-core z-step (mixed path)
+
+TC_CASES = [
+    ((37, 50), 1),          # 2D: contracted axis 0 has post > 1 (case A)
+    ((50, 37), 0),          # 2D, PE first: contracted axis 1 is the last one (case B)
+    ((9, 70, 21), 1),       # 3D PE middle: axis 0 case A, axis 2 case B
+    ((40, 7, 9), 0),        # PE first: axis 1 case A (post = 9), axis 2 case B
+    ((6, 7, 100), 2),       # PE last: axis 0 case A, axis 1 case A (post = 101)
+    ((200, 20, 33), 1),     # two 128-row blocks (L = 200) and N = 48 (case B)
+    ((300, 9, 5), 1),       # L = 300 > 256: falls back to the SIMT passes
+]
+
+
+# Split TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation): each product carries
+# a relative error of about 3 * 2^-22 (truncated lo terms and the dropped lo*lo);
+# over a length-L DCT and 4 passes this stays below 1e-5 of the largest output
+# for L <= 256, far inside the mixed path's 1e-3-voxel budget.
+TC_TOL = 1e-5
+
+
+@pytest.mark.parametrize("m,pe", TC_CASES)
+def test_zstep_mixed_tensor_cores(sac, m, pe):
+    h, _, _, b, z, u = case_data(m, pe, seed=50)
+    og = oracle.Grid(m, h, pe)
+    op = oracle.Params(alpha=2.0, rho=50.0)
+    g = sac.grid(m, h, pe)
+    z_ref = oracle.zstep(og, op, b, u)
+    # FP32 storage: compare against the oracle run on the FP32-rounded inputs
+    b32 = b.astype(np.float32).astype(np.float64)
+    u32 = u.astype(np.float32).astype(np.float64)
+    z_ref32 = oracle.zstep(og, op, b32, u32)
+    outs = {}
+    for kern in (0, 1):
+        p = sac.params(alpha=2.0, rho=50.0, prec="mixed", zstep_kernel=kern)
+        zt = cu(z)
+        u_out, nr = sac.zstep(g, p, cu(b), cu(u), zt)
+        outs[kern] = zt.cpu().numpy()
+        assert rel(outs[kern], z_ref32) < TC_TOL, (kern, rel(outs[kern], z_ref32))
+        assert rel(u_out.cpu().numpy(), u32 + b32 - z_ref32) < 2e-5
+        ref = [np.sum((b32 - z_ref32) ** 2), np.sum((z_ref32 - z) ** 2), np.sum(b32 ** 2)]
+        np.testing.assert_allclose(nr[:3], ref, rtol=1e-4)
+    assert rel(outs[0], outs[1]) < TC_TOL
+    assert rel(outs[0], z_ref) < 2 * TC_TOL
