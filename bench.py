@@ -34,8 +34,8 @@ UNIT = "voxel-iters/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_256x256x80")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
@@ -68,7 +68,7 @@ def load_workload(name):
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -76,15 +76,22 @@ class Clocks:
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.marks = []
 
     def __enter__(self):
+        # started ahead of the timed region so that it samples during it
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
         except OSError:
             self.p = None
         return self
+
+    def mark(self):
+        """Call at the start and at the end of the timed region."""
+        self.marks.append(time.time())
 
     def __exit__(self, *a):
         if self.p:
@@ -103,6 +110,18 @@ class Clocks:
                 if len(parts) >= 9:
                     rows.append(parts)
         os.unlink(self.f.name)
+        if len(self.marks) >= 2:
+            import datetime
+            t0, t1 = self.marks[0], self.marks[-1]
+            sel = []
+            for r in rows:
+                try:
+                    ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if t0 - 0.02 <= ts <= t1 + 0.02:
+                    sel.append(r)
+            rows = sel
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -248,11 +267,12 @@ def main():
         return sac.params(alpha=w.alpha, rho=w.rho, prec=prec, max_iter=iters, eps_abs=0.0, eps_rel=eps_rel,
                           check_every=every or max(iters, 1), near_bound=1e-3)
 
-    pm = params("mixed", args.steps)
-    ws = sac.workspace(g, pm, device=dev)
-    b = torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
-    z = torch.zeros_like(b)
-    u = torch.zeros_like(b)
+    def batch(prec, I1x, I2x, max_iter, eps_rel=0.0, autotune=1):
+        p = sac.params(alpha=w.alpha, rho=w.rho, prec=prec, max_iter=max_iter, eps_abs=0.0, eps_rel=eps_rel,
+                       near_bound=1e-3, autotune=autotune)
+        bb = torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
+        return sac.Batch([g], p, [I1x], [I2x], [bb]), bb
+
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -260,28 +280,32 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up: W iterations (one solve)
-    sac.admm_solve(g, params("mixed", args.warmup), I1, I2, b, z, u, ws=ws)
-    # timed region: exactly K iterations, inputs resident in HBM
+    # headline: the batched engine on this volume (tables built once, CUDA-graph
+    # replay, device-side stopping); warm-up W iterations (autotuning the
+    # b-step tile width on live iterations), then exactly K timed iterations
+    big = 1 << 30
+    bt, bmix = batch("mixed", I1, I2, big)
+    bt.run(args.warmup, chunk=args.warmup)
     barrier()
     sac.profile_enable(True)
     sac.profile_read(reset=True)
     n0 = sac.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
-        e0.record(stream)
-        res = sac.admm_solve(g, pm, I1, I2, b, z, u, ws=ws)
-        e1.record(stream)
+        clk.mark()
+        bt.run(args.steps, chunk=args.steps)
         barrier()
+        clk.mark()
     launches = sac.launch_count() - n0
     prof = sac.profile_read(reset=True)
     sac.profile_enable(False)
-    t_ms = e0.elapsed_time(e1)
+    t_ms = bt.last_run_ms()
+    assert int(bt.stats()["iters"][0]) == args.warmup + args.steps
+    bt.finish()
+    bt.close()
     if dist:
         tt = torch.tensor([t_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
-    assert res["iters"] == args.steps
     value = world * nf * args.steps / (t_ms / 1e3)
     clocks = clk.summary()
     if args.only_mixed:
@@ -291,26 +315,29 @@ def main():
                               "kernels": {k: v for k, v in prof.items()}}), flush=True)
         return
 
-    # plain FP64 GPU path on the same workload (fewer iterations: FP64 is slow on GB300)
-    kf = max(2, min(args.steps, 5))
-    pf = params("f64", kf)
-    wsf = sac.workspace(g, pf, device=dev)
-    bf, zf, uf = torch.zeros_like(b), torch.zeros_like(b), torch.zeros_like(b)
-    sac.admm_solve(g, params("f64", 1), I1d, I2d, bf, zf, uf, ws=wsf)
-    barrier()
-    e0.record(stream)
-    sac.admm_solve(g, pf, I1d, I2d, bf, zf, uf, ws=wsf)
-    e1.record(stream)
-    barrier()
-    f64_val = nf * kf / (e0.elapsed_time(e1) / 1e3)
-    del wsf
+    # plain FP64 GPU path, same engine (FP64 is slow on GB300: fewer iterations)
+    kf = max(3, min(args.steps, 10))
+    btf, _ = batch("f64", I1d, I2d, big, autotune=0)
+    btf.run(2, chunk=2)
+    btf.run(kf, chunk=kf)
+    f64_ms = btf.last_run_ms()
+    btf.close()
+    f64_val = nf * kf / (f64_ms / 1e3)
 
-    # end to end through the C ABI with host buffers: H2D inputs, K iterations, D2H result
+    # end to end through the single-volume public call (sac_admm_solve) with
+    # host buffers: H2D inputs, K iterations (set-up of the DCT tables
+    # included), D2H result
+    pm = sac.params(alpha=w.alpha, rho=w.rho, prec="mixed", max_iter=args.steps, eps_abs=0.0, eps_rel=0.0,
+                    check_every=args.steps, near_bound=1e-3)
+    ws = sac.workspace(g, pm, device=dev)
     hI1 = torch.empty(I1.shape, dtype=torch.float32, pin_memory=True).copy_(I1.cpu())
     hI2 = torch.empty(I2.shape, dtype=torch.float32, pin_memory=True).copy_(I2.cpu())
-    hb = torch.zeros(b.shape, dtype=torch.float64, pin_memory=True)
-    hout = torch.empty(b.shape, dtype=torch.float64, pin_memory=True)
-    dI1, dI2, db = torch.empty_like(I1), torch.empty_like(I2), torch.empty_like(b)
+    hb = torch.zeros(sac.face_shape(g), dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(sac.face_shape(g), dtype=torch.float64, pin_memory=True)
+    dI1, dI2, db = torch.empty_like(I1), torch.empty_like(I2), torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
+    sac.admm_solve(g, sac.params(alpha=w.alpha, rho=w.rho, prec="mixed", max_iter=2, eps_abs=0.0, eps_rel=0.0),
+                   I1, I2, torch.zeros_like(db), ws=ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     dI1.copy_(hI1, non_blocking=True)
@@ -321,33 +348,43 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
+    del ws
     h2d = hI1.numel() * 4 + hI2.numel() * 4 + hb.numel() * 8
     d2h = hout.numel() * 8
     e2e = {"value": world * nf * args.steps / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "per_solve": {"iterations": args.steps, "h2d_bytes": h2d, "d2h_bytes": d2h}}
+           "per_solve": {"call": "sac_admm_solve", "iterations": args.steps, "h2d_bytes": h2d, "d2h_bytes": d2h}}
 
-    # time to solution at relative residual 1e-4 (Eq. admmStop with eps_abs = 0, eps_rel = 1e-4)
+    # time to solution at relative residual 1e-4 (Eq. admmStop with eps_abs = 0,
+    # eps_rel = 1e-4), device-side stopping, mixed and plain FP64
     tts = None
     if not args.no_tts:
         tts = {}
+        b_by = {}
         for prec, A1, A2 in (("mixed", I1, I2), ("f64", I1d, I2d)):
             cap = args.tts_cap if prec == "mixed" else min(args.tts_cap, 200)
-            pt = params(prec, cap, eps_rel=1e-4, every=5)
-            wst = ws if prec == "mixed" else sac.workspace(g, pt, device=dev)
-            bt = torch.zeros_like(b)
             barrier()
             t0 = time.perf_counter()
-            r = sac.admm_solve(g, pt, A1, A2, bt, ws=wst)
+            btt, bres = batch(prec, A1, A2, cap, eps_rel=1e-4, autotune=0)
+            btt.run(cap, chunk=10)
+            st = btt.stats()
+            btt.finish()
             torch.cuda.synchronize()
-            tts[prec] = {"seconds": time.perf_counter() - t0, "iterations": r["iters"],
-                         "converged": r["converged"], "r_pri": r["r_pri"], "r_dual": r["r_dual"], "cap": cap}
-            if prec == "mixed":
-                b_mixed = bt.cpu().numpy()
-            else:
-                tts["max_abs_db_voxels_mixed_vs_f64"] = float(
-                    np.max(np.abs(bt.cpu().numpy() - b_mixed)) / w.h[w.pe])
-            del wst
+            sec = time.perf_counter() - t0
+            btt.close()
+            b_by[prec] = (int(st["iters"][0]), bres.cpu().numpy())
+            tts[prec] = {"seconds": sec, "device_ms": None, "iterations": int(st["iters"][0]),
+                         "converged": bool(st["converged"][0]), "r_pri": float(st["r_pri"][0]),
+                         "r_dual": float(st["r_dual"][0]), "cap": cap}
+        # accuracy of the mixed path against the plain FP64 path after the same
+        # number of iterations
+        kk = min(b_by["mixed"][0], b_by["f64"][0])
+        btm, bm = batch("mixed", I1, I2, kk, autotune=0)
+        btm.run(kk, chunk=10); btm.finish(); btm.close()
+        bt6, b6 = batch("f64", I1d, I2d, kk, autotune=0)
+        bt6.run(kk, chunk=10); bt6.finish(); bt6.close()
+        tts["mixed_vs_f64_same_iterations"] = {
+            "iterations": kk, "max_abs_db_voxels": float((bm - b6).abs().max().item() / w.h[w.pe])}
 
     # roofline of the dominant kernel (largest summed device time in the timed region)
     roof, kernels = roofline(prof, w, g, nf, sac)
@@ -363,6 +400,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": w.name, "faces": nf, "grid": list(w.m), "pe_axis": w.pe,
                            "alpha": w.alpha, "rho": w.rho, "prec": "mixed", "parallelism": f"replicas{world}",
+                           "timed": "sac_batch_run (one volume): CUDA-graph replay of K iterations, device time",
                            "l2": "working set > 129 MB L2 (images, b, z, u, two scratch arrays)"},
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,

@@ -193,6 +193,8 @@ int sac_batch_run(sac_batch bt, int max_iter, int chunk);
 /* host arrays of njobs entries (any may be NULL) */
 int sac_batch_stats(sac_batch bt, int* iters, int* converged, double* r_pri, double* r_dual);
 int sac_batch_finish(sac_batch bt);
+/* device time (ms, CUDA events on the batch's stream) of the last sac_batch_run */
+double sac_batch_last_run_ms(sac_batch bt);
 void sac_batch_destroy(sac_batch bt);
 
 /* ---------------------------------------------------------------- serving

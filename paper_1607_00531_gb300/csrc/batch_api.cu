@@ -101,6 +101,8 @@ int sac_batch_finish(sac_batch bt) {
     return bt->eng.finish();
 }
 
+double sac_batch_last_run_ms(sac_batch bt) { return bt ? (double)bt->eng.last_run_ms() : -1.0; }
+
 void sac_batch_destroy(sac_batch bt) { delete bt; }
 
 }  // extern "C"

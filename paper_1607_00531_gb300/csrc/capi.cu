@@ -66,6 +66,17 @@ struct Profiler {
 };
 static Profiler g_prof;
 
+bool profiling_on() {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    return g_prof.on;
+}
+void profile_add(int phase, double ms, long long launches) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (phase < 0 || phase >= SAC_NPHASES) return;
+    g_prof.ms[phase] += ms;
+    g_prof.n[phase] += launches;
+}
+
 struct PhaseScope {
     cudaEvent_t a = nullptr;
     cudaStream_t st;

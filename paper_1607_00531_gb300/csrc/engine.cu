@@ -337,9 +337,19 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     return SAC_OK;
 }
 
-int Engine::enqueue_iteration() {
+// phase marks: events [slot][phase][start|end], 6 phases as in sac_profile_read
+void Engine::prof_mark(int slot, int phase, int end) {
+    if (slot < 0) return;
+    // an event record node of the captured graph (a plain record would only
+    // add a dependency edge during capture)
+    cudaEventRecordWithFlags(prof_ev_[((size_t)slot * SAC_NPHASES + phase) * 2 + end], st_, cudaEventRecordExternal);
+}
+
+int Engine::enqueue_iteration(int slot) {
     const bool mixed = (p_.prec == SAC_MIXED);
     ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * 4, st_));
+    for (int pass = 0; pass < 2; ++pass) {
+    prof_mark(slot, pass, 0);
     for (size_t c = 0; c < cls_.size(); ++c) {
         const Cls& C = cls_[c];
         LineLaunch L;
@@ -362,13 +372,14 @@ int Engine::enqueue_iteration() {
         L.list_blocks = std::min<long long>((C.lines + C.W - 1) / C.W, 4 * 152);
         L.status = d_status_;
         L.stream = st_;
-        L.mode = 0;
+        L.mode = pass;
         ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
-        L.mode = 1;
-        ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
+    }
+    prof_mark(slot, pass, 1);
     }
     const int nj = (int)jobs_.size();
     for (int q = 0; q < 4; ++q) {
+        prof_mark(slot, 2 + q, 0);
         AxisLaunch A;
         A.jobs = d_jobs_;
         A.njobs = nj;
@@ -386,23 +397,35 @@ int Engine::enqueue_iteration() {
             A.total_tiles = ax_tiles_[q];
             ENG_CUDA(launch_axis_pass(A));
         }
+        if (q < 3) prof_mark(slot, 2 + q, 1);
     }
     ENG_CUDA(cudaMemsetAsync(d_nactive_, 0, sizeof(int), st_));
     count_launch();
     k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, use_tc_ ? d_pref_tc_[3] : d_pref_ax_[3], d_part_, p_.eps_abs,
                                       p_.eps_rel, p_.max_iter, d_stats_, d_nactive_);
     ENG_CUDA(cudaGetLastError());
+    prof_mark(slot, 5, 1);
     return SAC_OK;
 }
 
 int Engine::capture(int chunk) {
-    if (exec_ && graph_chunk_ == chunk) return SAC_OK;
+    const bool prof = profiling_on();
+    if (exec_ && graph_chunk_ == chunk && (prof == (prof_slots_ > 0))) return SAC_OK;
     if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
     if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+    prof_slots_ = prof ? chunk : 0;
+    if (prof && (int)prof_ev_.size() < prof_slots_ * SAC_NPHASES * 2) {
+        const size_t want = (size_t)prof_slots_ * SAC_NPHASES * 2;
+        while (prof_ev_.size() < want) {
+            cudaEvent_t e;
+            ENG_CUDA(cudaEventCreate(&e));
+            prof_ev_.push_back(e);
+        }
+    }
     ENG_CUDA(cudaStreamBeginCapture(st_, cudaStreamCaptureModeRelaxed));
     int s = SAC_OK;
     const long long n0 = sac_launch_count();
-    for (int i = 0; i < chunk && s == SAC_OK; ++i) s = enqueue_iteration();
+    for (int i = 0; i < chunk && s == SAC_OK; ++i) s = enqueue_iteration(prof ? i : -1);
     graph_launches_ = sac_launch_count() - n0;
     count_launch(-graph_launches_);     // captured, not launched
     cudaGraph_t g = nullptr;
@@ -485,16 +508,33 @@ int Engine::run(int max_iter, int chunk) {
         remaining -= (iters_done_ - before);
         if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; cudaGraphDestroy(graph_); graph_ = nullptr; }
     }
-    ENG_TRY(capture(chunk));
+    if (!run_a_) ENG_CUDA(cudaEventCreate(&run_a_));
+    if (!run_b_) ENG_CUDA(cudaEventCreate(&run_b_));
     int nact = 1;
+    bool started = false;
     while (remaining > 0 && nact > 0) {
+        const int n = remaining < chunk ? remaining : chunk;   // the last replay covers exactly the rest
+        ENG_TRY(capture(n));
+        if (!started) { ENG_CUDA(cudaEventRecord(run_a_, st_)); started = true; }
         ENG_CUDA(cudaGraphLaunch(exec_, st_));
         count_launch(graph_launches_);
-        remaining -= chunk;
-        iters_done_ += chunk;
+        remaining -= n;
+        iters_done_ += n;
         ENG_CUDA(cudaMemcpyAsync(&nact, d_nactive_, sizeof(int), cudaMemcpyDeviceToHost, st_));
         ENG_CUDA(cudaStreamSynchronize(st_));
+        // per-phase device times of this replay (graph event nodes)
+        for (int i = 0; i < prof_slots_; ++i)
+            for (int ph = 0; ph < SAC_NPHASES; ++ph) {
+                float ms = 0.f;
+                const size_t k = ((size_t)i * SAC_NPHASES + ph) * 2;
+                if (cudaEventElapsedTime(&ms, prof_ev_[k], prof_ev_[k + 1]) == cudaSuccess) profile_add(ph, ms, 1);
+                else cudaGetLastError();
+            }
     }
+    if (!started) ENG_CUDA(cudaEventRecord(run_a_, st_));
+    ENG_CUDA(cudaEventRecord(run_b_, st_));
+    ENG_CUDA(cudaEventSynchronize(run_b_));
+    ENG_CUDA(cudaEventElapsedTime(&last_ms_, run_a_, run_b_));
     int s = 0;
     ENG_CUDA(cudaMemcpyAsync(&s, d_status_, sizeof(int), cudaMemcpyDeviceToHost, st_));
     ENG_CUDA(cudaStreamSynchronize(st_));
@@ -537,6 +577,10 @@ int Engine::finish() {
 }
 
 void Engine::destroy_stream() {
+    for (cudaEvent_t e : prof_ev_) cudaEventDestroy(e);
+    prof_ev_.clear();
+    if (run_a_) { cudaEventDestroy(run_a_); run_a_ = nullptr; }
+    if (run_b_) { cudaEventDestroy(run_b_); run_b_ = nullptr; }
     if (ev_in_) { cudaEventDestroy(ev_in_); ev_in_ = nullptr; }
     if (ev_out_) { cudaEventDestroy(ev_out_); ev_out_ = nullptr; }
     if (st_) { cudaStreamSynchronize(st_); cudaStreamDestroy(st_); st_ = nullptr; }

@@ -49,6 +49,8 @@ public:
     // run ADMM iterations until every job stopped or max_iter more iterations;
     // replays a CUDA graph of `chunk` iterations, one host sync per chunk
     int run(int max_iter, int chunk);
+    // device time of the last run() in milliseconds (events on the engine stream)
+    float last_run_ms() const { return last_ms_; }
     // copy per-job stats to the host
     int stats(std::vector<EngineStats>* out);
     // write the FP64 results of the finished jobs (mixed: FP32 state -> b)
@@ -59,7 +61,7 @@ public:
     ~Engine() { release(); destroy_stream(); }
 
 private:
-    int enqueue_iteration();
+    int enqueue_iteration(int prof_slot = -1);
     int capture(int chunk);
     int tune();
     std::vector<EngineJob> jobs_;   // grouped by K class
@@ -93,6 +95,12 @@ private:
     long long graph_launches_ = 0;
     int iters_done_ = 0;
     bool tuned_ = false;
+    float last_ms_ = 0.f;
+    cudaEvent_t run_a_ = nullptr, run_b_ = nullptr;
+    // per-phase timing events captured into the graph (profiling on)
+    std::vector<cudaEvent_t> prof_ev_;
+    int prof_slots_ = 0;
+    void prof_mark(int slot, int phase, int end);
 };
 
 // process-wide choice of lines per CTA for a line class (autotuned)

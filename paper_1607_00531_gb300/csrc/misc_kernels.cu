@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_hessvec(const Job* __restrict__ jobs, i
     }
 }
 
-// largest |D1 b| of the cells of a job (per-block maxima)
+// largest |b_{i+1} - b_i| / h along PE over the faces of a job (per-block
+// maxima); thread -> (outer index o, PE row i, inner index n) with n fastest
 __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs, int njobs,
                                                     const long long* __restrict__ prefix,
                                                     const double* __restrict__ b, double* __restrict__ part) {
@@ -111,14 +112,13 @@ __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs
     const Job& J = jobs[jid];
     const long long f = (t - prefix[jid]) * 256 + threadIdx.x;
     double mx = 0.0;
-    if (f < J.nf) {
-        int idx[3];
-        face_idx(J, f, idx);
-        if (idx[J.pe] < J.mpe) {
-            const long long s = face_stride(J, J.pe);
-            const double d = fabs(b[f + s] - b[f]) / J.hpe;
-            mx = (d == d) ? d : INFINITY;
-        }
+    const long long ncell_rows = (long long)J.n_outer * J.mpe * J.n_inner;   // one entry per cell
+    if (f < ncell_rows) {
+        const long long per_outer = (long long)J.mpe * J.n_inner;
+        const long long o = f / per_outer, rem = f - o * per_outer;          // one 64-bit division per thread
+        const long long a = o * (J.mpe + 1) * (long long)J.n_inner + rem;   // face (o, i, n)
+        const double d = fabs(b[a + J.n_inner] - b[a]);
+        mx = (d == d) ? d : INFINITY;
     }
     mx = warp_max(mx);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs
     if (wid == 0) {
         mx = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
         mx = warp_max(mx);
-        if (lane == 0) part[blockIdx.x] = mx;
+        if (lane == 0) part[blockIdx.x] = mx / J.hpe;
     }
 }
 

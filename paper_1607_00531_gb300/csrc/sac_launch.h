@@ -10,6 +10,9 @@ struct Job;
 
 // number of kernels launched by this library (instrumentation)
 void count_launch(long long n = 1);
+// profiling: is it on; add a measured phase duration (capi.cu)
+bool profiling_on();
+void profile_add(int phase, double ms, long long launches);
 
 // set the kernels' launch attributes once per process, before any launch or
 // stream capture (capi.cu); returns a sac_status

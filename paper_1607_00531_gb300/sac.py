@@ -75,6 +75,7 @@ def lib():
             "sac_batch_stats": (ctypes.c_int, [vp, ip, ip, dp, dp]),
             "sac_batch_finish": (ctypes.c_int, [vp]),
             "sac_batch_destroy": (None, [vp]),
+            "sac_batch_last_run_ms": (ctypes.c_double, [vp]),
             "sac_server_request_bytes": (sz, [P, G]),
             "sac_server_create": (ctypes.c_int, [P, vp, sz, ctypes.c_int, vp, ctypes.POINTER(vp)]),
             "sac_server_submit": (ctypes.c_int, [vp, G, vp, vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -348,6 +349,9 @@ class Batch:
 
     def finish(self):
         return _check("sac_batch_finish", lib().sac_batch_finish(self.h))
+
+    def last_run_ms(self):
+        return float(lib().sac_batch_last_run_ms(self.h))
 
     def close(self):
         if getattr(self, "h", None):
