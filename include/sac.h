@@ -116,6 +116,28 @@ size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p);
 int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
                   const double* b, double* out4, void* ws, size_t ws_bytes, void* stream);
 
+/* The objective of sac_objective (same kernels, same results) without a
+   workspace: for callers that cannot allocate device memory, such as
+   reconstruction services that reserve all GPU memory at start-up and forbid
+   allocations afterwards, code running inside another framework's memory
+   manager, or callers that cannot size a workspace ahead of time.  The paper
+   has no counterpart: this is an interface convenience, not part of the
+   method.  The scratch (job descriptor, status words and partial sums) is a
+   fixed array of sac_objective_noalloc_max_bytes() = 1 MiB inside the
+   library, which every GPU that loads the library holds until the process
+   exits.  Grids whose scratch would not fit (about 4 doubles per 8 PE lines
+   plus 1 double per 256 faces) are rejected with SAC_ENOMEM before any GPU
+   work.  The first call on a device looks up the array's device address and
+   caches it: make that first call before any stream capture.  All calls
+   share the array and it keeps the last call's contents; the status words
+   are cleared at the start of every call, and calls that overlap on the GPU
+   (on different streams or from several threads) race on the array.  No
+   cudaMalloc, cudaFree or other allocating call is made.  Arguments as in
+   sac_objective; synchronises `stream` before returning. */
+int sac_objective_noalloc(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                          const double* b, double* out4, void* stream);
+size_t sac_objective_noalloc_max_bytes(void);
+
 /* Gradient of J_GN (Sec. 3: grad D = h^d J_r^T r, grad S = h^d sum_a D_a^T D_a b,
    grad P = beta h^d D1^T phi'(D1 b)) into grad (face array, double). */
 int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,

@@ -62,6 +62,8 @@ def lib():
             "sac_workspace_bytes": (sz, [G, P]),
             "sac_objective": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp, sz, vp]),
             "sac_gradient": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, sz, vp]),
+            "sac_objective_noalloc": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp]),
+            "sac_objective_noalloc_max_bytes": (sz, []),
             "sac_bstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]),
             "sac_zstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, dp, vp, sz, vp]),
             "sac_admm_solve": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, ip, dp, dp, dp, vp, sz, vp]),
@@ -198,6 +200,16 @@ def objective(g, p, I1, I2, b, ws=None, stream=None):
     out = (ctypes.c_double * 4)()
     _check("sac_objective", lib().sac_objective(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), out,
                                                 _ptr(ws), ws.numel(), _stream(stream)))
+    return dict(J=out[0], D=out[1], S=out[2], P=out[3])
+
+
+def objective_noalloc(g, p, I1, I2, b, stream=None):
+    """sac_objective without a workspace: its scratch is a fixed array inside
+    the library (see include/sac.h), for callers that cannot allocate."""
+    _check_inputs(g, p, I1, I2)
+    out = (ctypes.c_double * 4)()
+    _check("sac_objective_noalloc", lib().sac_objective_noalloc(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2),
+                                                                _ptr(b), out, _stream(stream)))
     return dict(J=out[0], D=out[1], S=out[2], P=out[3])
 
 
