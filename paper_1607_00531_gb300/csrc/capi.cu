@@ -201,13 +201,16 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
         if (!tc_pass_supported(G.F, G.ax1, G.ax2, q)) P->use_tc = 0;
         P->tc_tiles[q] = tc_pass_tiles(G.F, G.ax1, G.ax2, q);
         P->tc_floats[q] = tc_matrix_floats(G.F, G.ax1, G.ax2, q);
-        P->tc_smem[q] = tc_smem_bytes(G.F, G.ax1, G.ax2, q);
+        P->tc_cfg[q] = TcCfg();
+        tc_cfg_add(&P->tc_cfg[q], G.F, G.ax1, G.ax2, q);
+        if (!tc_cfg_finish(&P->tc_cfg[q])) P->use_tc = 0;
     }
     const long long nlines = (long long)G.n_outer * G.n_inner;
     P->rcap = (int)nlines;
     long long np = 4 * P->line_tiles;
     if (5 * P->pass_tiles[3] > np) np = 5 * P->pass_tiles[3];
-    if (5 * P->tc_tiles[3] > np) np = 5 * P->tc_tiles[3];
+    P->admm_blocks = admm_update_blocks(G.nf);
+    if (5 * P->admm_blocks > np) np = 5 * P->admm_blocks;
     if (P->elem_blocks > np) np = P->elem_blocks;
     if (2 * 1216 > np) np = 2 * 1216;
     P->n_part = np;
@@ -216,7 +219,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     size_t o_job = take(sizeof(Job));
-    size_t o_pref = take(sizeof(long long) * 2 * 10);
+    size_t o_pref = take(sizeof(long long) * 2 * 11);
     size_t o_stat = take(256);
     size_t o_out = take(sizeof(double) * 64);
     size_t o_rlist = take(sizeof(unsigned long long) * (size_t)P->rcap);
@@ -230,6 +233,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t o_scale = take(sizeof(float) * (size_t)L1 * L2);
     size_t o_tc[4];
     for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
+    size_t o_tmap = take(P->use_tc ? tc_map_bytes() : 0);
     size_t o_arr[10];
     for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
     P->bytes = off;
@@ -242,8 +246,10 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) P->d_pref_pass[q] = pref + 2 * (1 + q);
     P->d_pref_elem = pref + 10;
     for (int q = 0; q < 4; ++q) P->d_pref_tc[q] = pref + 12 + 2 * q;
+    P->d_pref_admm = pref + 20;
     for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
     P->d_scale = (float*)(base + o_scale);
+    P->d_tmaps = P->use_tc ? (void*)(base + o_tmap) : nullptr;
     P->d_status = (int*)(base + o_stat);
     P->d_rcount = P->d_status + 1;
     P->d_out = (double*)(base + o_out);
@@ -279,11 +285,20 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     J.lam1 = P->d_lam1; J.lam2 = P->d_lam2;
     J.part = P->d_part;
     for (int q = 0; q < 4; ++q) J.Ctc[q] = P->d_Ctc[q];
+    for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
     J.scale = P->d_scale;
     J.active = 1;
-    long long pref[20] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
+    if (P->use_tc && P->d_tmaps && b && u && t1 && t2) {
+        // TMA tensor maps of the X sources of the tensor-core passes
+        std::vector<unsigned char> maps(tc_map_bytes());
+        J.tmaps = P->d_tmaps;
+        J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)b, (const float*)u, (const float*)t1,
+                                  (const float*)t2, maps.data());
+        SAC_CUDA(cudaMemcpyAsync(P->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
+    }
+    long long pref[22] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
                           0, P->pass_tiles[3], 0, P->elem_blocks, 0, P->tc_tiles[0], 0, P->tc_tiles[1],
-                          0, P->tc_tiles[2], 0, P->tc_tiles[3]};
+                          0, P->tc_tiles[2], 0, P->tc_tiles[3], 0, P->admm_blocks};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -451,8 +466,12 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
         if (P.use_tc) {
             A.prefix = P.d_pref_tc[q];
             A.total_tiles = P.tc_tiles[q];
-            SAC_CUDA(launch_axis_pass_tc(A, P.tc_smem[q]));
-            if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.tc_tiles[3], 5, P.d_out + 16, st));
+            SAC_CUDA(launch_axis_pass_tc(A, P.tc_cfg[q]));
+            if (q == 3) {
+                // z^{k+1} is in t2: ADMM update and residual sums, element-wise
+                SAC_CUDA(launch_admm_update(P.d_job, 1, P.d_pref_admm, P.admm_blocks, P.d_part, st));
+                SAC_CUDA(launch_reduce(P.d_part, (int)P.admm_blocks, 5, P.d_out + 16, st));
+            }
         } else {
             A.prefix = P.d_pref_pass[q];
             A.total_tiles = P.pass_tiles[q];

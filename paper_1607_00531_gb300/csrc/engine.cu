@@ -52,7 +52,7 @@ void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W) {
 // ---------------------------------------------------------------- per-job state block
 struct StateLayout {
     size_t b32, z, u, t1, t2;          // face arrays
-    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4];
+    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4], tmap;
     size_t bytes;
 };
 
@@ -76,6 +76,7 @@ static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
     s.scale = take(4 * (size_t)L1 * L2);
     for (int q = 0; q < 4; ++q)
         s.tc[q] = take(use_tc ? 4 * (size_t)tc_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
+    s.tmap = take(use_tc ? tc_map_bytes() : 0);
     s.bytes = off;
     return s;
 }
@@ -84,6 +85,8 @@ size_t job_state_bytes(const Geometry& G, int prec, int use_tc) { return state_l
 
 // ---------------------------------------------------------------- kernels
 
+// pref3: partial-sum sets (5 each) per job: the blocks of the ADMM update
+// (tensor-core z-step) or the tiles of the last SIMT pass
 __global__ void k_admm_check(Job* __restrict__ jobs, int njobs, const long long* __restrict__ pref3,
                              const double* __restrict__ part, double eps_abs, double eps_rel, int max_iter,
                              double* __restrict__ stats, int* __restrict__ nactive) {
@@ -135,16 +138,16 @@ __global__ void k_init_state(long long n, const double* __restrict__ b, void* b3
 size_t Engine::table_bytes(const std::vector<EngineJob>& jobs, const sac_params& p) {
     (void)p;
     const size_t nj = jobs.size();
-    long long lines = 0, tiles3 = 0, tiles_ax3 = 0;
+    long long lines = 0, ablocks = 0, tiles_ax3 = 0;
     for (auto& j : jobs) {
         lines += (long long)j.G.n_outer * j.G.n_inner;
-        tiles3 += tc_pass_tiles(j.G.F, j.G.ax1, j.G.ax2, 3);
+        ablocks += admm_update_blocks(j.G.nf);
         tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
     }
-    long long np = 5 * std::max(tiles3, tiles_ax3) + 8;
+    long long np = 5 * std::max(ablocks, tiles_ax3) + 8;
     size_t off = 0;
     off += a256(sizeof(Job) * nj);
-    off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 4 classes) + 8 pass prefixes
+    off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 4 classes), 8 pass prefixes, ADMM update blocks, spare
     off += a256(sizeof(unsigned long long) * (size_t)lines);
     off += a256(sizeof(int) * 16);
     off += a256(sizeof(double) * (size_t)np);
@@ -192,12 +195,12 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     d_rcount_ = (int*)take(sizeof(int) * 16);
     d_status_ = d_rcount_ + 4;
     d_nactive_ = d_rcount_ + 5;
-    long long tiles3 = 0, tiles_ax3 = 0;
+    long long ablocks = 0, tiles_ax3 = 0;
     for (auto& j : jobs_) {
-        tiles3 += tc_pass_tiles(j.G.F, j.G.ax1, j.G.ax2, 3);
+        ablocks += admm_update_blocks(j.G.nf);
         tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
     }
-    d_part_ = (double*)take(sizeof(double) * (size_t)(5 * std::max(tiles3, tiles_ax3) + 8));
+    d_part_ = (double*)take(sizeof(double) * (size_t)(5 * std::max(ablocks, tiles_ax3) + 8));
     d_stats_ = (double*)take(sizeof(double) * 8 * nj);
     // classes
     std::vector<long long> hpref((nj + 1) * (4 + 8 + 8), 0);
@@ -247,16 +250,25 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         long long* ht = hpref.data() + (4 + q) * (nj + 1);
         long long* ha = hpref.data() + (8 + q) * (nj + 1);
         ht[0] = ha[0] = 0;
-        tc_smem_[q] = 0;
+        tc_cfg_[q] = TcCfg();
         for (size_t i = 0; i < nj; ++i) {
             const Geometry& G = jobs_[i].G;
             ht[i + 1] = ht[i] + tc_pass_tiles(G.F, G.ax1, G.ax2, q);
             const int axis = (q == 0 || q == 3) ? G.ax1 : G.ax2;
             ha[i + 1] = ha[i] + axis_pass_tiles(G.F, axis);
-            tc_smem_[q] = std::max(tc_smem_[q], tc_smem_bytes(G.F, G.ax1, G.ax2, q));
+            tc_cfg_add(&tc_cfg_[q], G.F, G.ax1, G.ax2, q);
         }
+        if (use_tc_ && !tc_cfg_finish(&tc_cfg_[q])) return SAC_EINVAL;
         tc_tiles_[q] = ht[nj];
         ax_tiles_[q] = ha[nj];
+    }
+    {
+        // ADMM update blocks per job (tensor-core z-step)
+        d_pref_admm_ = pref + 12 * (nj + 1);
+        long long* hb = hpref.data() + 12 * (nj + 1);
+        hb[0] = 0;
+        for (size_t i = 0; i < nj; ++i) hb[i + 1] = hb[i] + admm_update_blocks(jobs_[i].G.nf);
+        admm_blocks_ = hb[nj];
     }
     ENG_CUDA(cudaMemcpyAsync(pref, hpref.data(), hpref.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     // jobs: state layout, tables, initial state
@@ -284,6 +296,15 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         J.lam2 = (const double*)(s + L.l2);
         J.scale = (const float*)(s + L.scale);
         for (int q = 0; q < 4; ++q) J.Ctc[q] = use_tc_ ? (const void*)(s + L.tc[q]) : nullptr;
+        for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
+        if (use_tc_) {
+            // TMA tensor maps of the X sources of the tensor-core passes
+            std::vector<unsigned char> maps(tc_map_bytes());
+            J.tmaps = s + L.tmap;
+            J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)J.b, (const float*)J.u, (const float*)J.t1,
+                                      (const float*)J.t2, maps.data());
+            ENG_CUDA(cudaMemcpyAsync(s + L.tmap, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
+        }
         J.part = d_part_;
         J.active = 1;
         if (E.fresh) {
@@ -391,7 +412,9 @@ int Engine::enqueue_iteration(int slot) {
         if (use_tc_) {
             A.prefix = d_pref_tc_[q];
             A.total_tiles = tc_tiles_[q];
-            ENG_CUDA(launch_axis_pass_tc(A, tc_smem_[q]));
+            ENG_CUDA(launch_axis_pass_tc(A, tc_cfg_[q]));
+            // z^{k+1} is in t2: ADMM update and residual sums, element-wise
+            if (q == 3) ENG_CUDA(launch_admm_update(d_jobs_, nj, d_pref_admm_, admm_blocks_, d_part_, st_));
         } else {
             A.prefix = d_pref_ax_[q];
             A.total_tiles = ax_tiles_[q];
@@ -401,7 +424,7 @@ int Engine::enqueue_iteration(int slot) {
     }
     ENG_CUDA(cudaMemsetAsync(d_nactive_, 0, sizeof(int), st_));
     count_launch();
-    k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, use_tc_ ? d_pref_tc_[3] : d_pref_ax_[3], d_part_, p_.eps_abs,
+    k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, use_tc_ ? d_pref_admm_ : d_pref_ax_[3], d_part_, p_.eps_abs,
                                       p_.eps_rel, p_.max_iter, d_stats_, d_nactive_);
     ENG_CUDA(cudaGetLastError());
     prof_mark(slot, 5, 1);

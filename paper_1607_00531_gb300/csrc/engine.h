@@ -82,7 +82,9 @@ private:
     long long* d_pref_tc_[4] = {nullptr, nullptr, nullptr, nullptr};
     long long* d_pref_ax_[4] = {nullptr, nullptr, nullptr, nullptr};
     long long tc_tiles_[4] = {0, 0, 0, 0}, ax_tiles_[4] = {0, 0, 0, 0};
-    size_t tc_smem_[4] = {0, 0, 0, 0};
+    long long* d_pref_admm_ = nullptr;   // ADMM update blocks per job (tensor-core z-step)
+    long long admm_blocks_ = 0;
+    TcCfg tc_cfg_[4];
     unsigned long long* d_rlist_ = nullptr;
     int* d_rcount_ = nullptr;      // one counter per class
     int* d_status_ = nullptr;

@@ -38,8 +38,9 @@ struct Plan {
     long long line_tiles, pass_tiles[4], elem_blocks;
     int use_tc;                // tensor-core z-step passes
     long long tc_tiles[4];
+    long long admm_blocks;     // ADMM update blocks (tensor-core z-step)
     long long tc_floats[4];
-    size_t tc_smem[4];
+    TcCfg tc_cfg[4];           // ring / accumulator layout of each tensor-core pass
     int rcap;
     // device pointers inside ws
     Job* d_job;
@@ -47,7 +48,9 @@ struct Plan {
     long long* d_pref_pass[4];
     long long* d_pref_elem;
     long long* d_pref_tc[4];
+    long long* d_pref_admm;   // blocks of the ADMM update after the tensor-core passes
     float* d_Ctc[4];
+    void* d_tmaps;            // tensor maps of the tensor-core passes
     float* d_scale;
     int* d_status;
     int* d_rcount;

@@ -47,6 +47,10 @@ struct Job {
     double* part;      // per-block partial sums of this job
     int active;        // 0: tiles of this job return at once
     int pad_;
+    int tc_T[4];       // tensor-core z-step: lines per tile of each pass
+    const void* tmaps; // tensor-core z-step: TMA tensor maps of the X sources, [pass][source]
+    int tc_tma;        // bit q: pass q loads X with the tensor maps
+    int pad2_;
 };
 
 // ---------------------------------------------------------------- job lookup

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 namespace sac {
 
@@ -99,18 +100,46 @@ struct AxisLaunch {
     long long total_tiles;
     int pass;                   // see zstep_kernels.cu
     int prec;                   // 0 FP64, 1 FP32
-    double* part;               // pass 3: 5 partial sums per CTA
+    double* part;               // pass 3 (SIMT): 5 partial sums per tile
     int* status;
     cudaStream_t stream;
 };
 cudaError_t launch_axis_pass(const AxisLaunch& A);
-// tensor-core (tcgen05) passes, FP32 storage, split-TF32 arithmetic
-cudaError_t launch_axis_pass_tc(const AxisLaunch& A, size_t smem);
+// tensor-core (tcgen05) passes, FP32 storage, split-TF32 arithmetic.
+// Launch-wide layout of the persistent kernel: the shared-memory rings
+// (DCT chunks, split X chunks) and the TMEM accumulators, sized for the
+// largest job of the launch (tc_cfg_add per job, then tc_cfg_finish).
+struct TcCfg {
+    uint32_t dslot = 0, xslot = 0;   // bytes of one DCT / X ring slot
+    int acc_need = 0;                // TMEM columns of one tile's accumulator
+    int sd = 0, sx = 0;              // ring stages
+    int nacc = 0;                    // accumulator buffers (2 when both fit in TMEM)
+    uint32_t acc_cols = 0;           // TMEM columns per accumulator buffer
+    uint32_t epi_off = 0;            // shared-memory offset of the epilogue transpose buffers
+    int resident = 0;                // 1: the DCT chunks stay in their slots for all tiles
+    int nch = 0, geom[3] = {0, 0, 0};   // shared geometry of the launch's jobs (-1: mixed)
+    size_t smem = 0;                 // dynamic shared memory per CTA
+};
+constexpr int kTcMaps = 8;           // TMA tensor maps per job: [pass][source]
+size_t tc_map_bytes();
+// Host: encode the tensor maps of a job (FP32 device arrays b, u, t1, t2)
+// into `out` (tc_map_bytes() bytes, host memory); returns the mask of passes
+// that can load X with them
+int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float* u, const float* t1,
+                   const float* t2, void* out);
+// After the tensor-core passes (z^{k+1} in t2): u <- u + b - t2, z <- t2 and
+// 5 residual partial sums per block (FP32 state); blocks per job:
+long long admm_update_blocks(long long nf);
+cudaError_t launch_admm_update(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                               double* part, cudaStream_t st);
+void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass);
+bool tc_cfg_finish(TcCfg* c);
+cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg);
+int tc_tile_lines(const int F[3], int ax1, int ax2, int pass);
 long long tc_pass_tiles(const int F[3], int ax1, int ax2, int pass);
 bool tc_pass_supported(const int F[3], int ax1, int ax2, int pass);
 long long tc_matrix_floats(const int F[3], int ax1, int ax2, int pass);
 void tc_arrange_matrix(const int F[3], int ax1, int ax2, int pass, const double* M, float* out);
-size_t tc_smem_bytes(const int F[3], int ax1, int ax2, int pass);
 // tiles of one pass for a job with face dims F, non-PE axes ax1/ax2
 long long axis_pass_tiles(const int F[3], int axis);
 

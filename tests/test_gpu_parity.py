@@ -222,6 +222,9 @@ TC_CASES = [
     ((6, 7, 100), 2),       # PE last: axis 0 case A, axis 1 case A (post = 101)
     ((200, 20, 33), 1),     # two 128-row blocks (L = 200) and N = 48 (case B)
     ((300, 9, 5), 1),       # L = 300 > 256: falls back to the SIMT passes
+    ((64, 30, 48), 1),      # 16-byte vector paths: post = 1488, last axis 48
+    ((160, 11, 20), 1),     # two 128-row blocks with vector stores (post = 240)
+    ((80, 255, 24), 1),     # more tiles than SMs on the last axis (20480 lines)
 ]
 
 
