@@ -96,6 +96,7 @@ __global__ void k_admm_check(Job* __restrict__ jobs, int njobs, const long long*
     Job& J = jobs[j];
     if (!J.active) return;
     double acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 4
     for (long long t = pref3[j] + threadIdx.x; t < pref3[j + 1]; t += blockDim.x)
         for (int c = 0; c < 5; ++c) acc[c] += part[t * 5 + c];
     block_sum<5>(acc, red);

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
     const bool is_max = ncomp < 0;
     const int nc = is_max ? 1 : ncomp;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
     for (int p = threadIdx.x; p < nparts; p += blockDim.x)
         for (int c = 0; c < nc; ++c) {
             const double v = part[(long long)p * nc + c];

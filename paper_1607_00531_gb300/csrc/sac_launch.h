@@ -110,9 +110,9 @@ cudaError_t launch_axis_pass(const AxisLaunch& A);
 // (DCT chunks, split X chunks) and the TMEM accumulators, sized for the
 // largest job of the launch (tc_cfg_add per job, then tc_cfg_finish).
 struct TcCfg {
-    uint32_t dslot = 0, xslot = 0;   // bytes of one DCT / X ring slot
+    uint32_t dslot = 0, rslot = 0;   // bytes of one DCT / raw X ring slot (shared memory)
     int acc_need = 0;                // TMEM columns of one tile's accumulator
-    int sd = 0, sx = 0;              // ring stages
+    int sd = 0, sr = 0, st = 0;      // ring stages: DCT, raw X, split X (tensor memory)
     int nacc = 0;                    // accumulator buffers (2 when both fit in TMEM)
     uint32_t acc_cols = 0;           // TMEM columns per accumulator buffer
     uint32_t epi_off = 0;            // shared-memory offset of the epilogue transpose buffers

@@ -1,6 +1,6 @@
 // zstep_tc.cu -- the z-step DCT passes on the 5th-generation tensor cores
 // (tcgen05.mma kind::tf32, accumulators in tensor memory), for the FP32
-// (mixed-precision) path.  Same passes and epilogues as zstep_kernels.cu:
+// (mixed-precision) path.  The passes of zstep_kernels.cu:
 //
 //   pass 0:  t1 = C1 x_ax1 (b + u)             (scaled here when the grid is 2D)
 //   pass 1:  t2 = S .* (C2 x_ax2 t1)           S = rho / (alpha Lambda + rho)
@@ -15,40 +15,44 @@
 // The DCT matrices are split on the host; X is split on the chip.
 //
 // A pass contracts one axis of length L.  The "lines" are the 1D fibres
-// along that axis, line r holding X[r][j], j < L.  Two forms:
-//  form 0 (the axis is the fastest one, each line contiguous):
-//     D[line][k] = sum_j X[line][j] C[k][j]; MMA A = X (128 lines), B = C
-//     (N = L padded to 16); TMEM lane = line.  Tile = 128 lines.
+// along that axis, line r holding X[r][j], j < L; a tile is 128 lines:
+//     D[line][k] = sum_j X[line][j] C[k][j],
+// one MMA M = 128 (lines, TMEM lanes), N = L padded to 16 (k), K = 8 (j).
+// The A operand (X, split) lives in tensor memory, written there by the
+// converter warps; the B operand (C, split) is the only operand read from
+// shared memory, which keeps the MMAs clear of the shared-memory bandwidth.
+//  form 0 (the axis is the fastest one, each line contiguous): tiles of 128
+//     consecutive lines; an output row (line) is contiguous in k, written
+//     through a per-warp shared-memory transpose;
 //  form 1 (the axis is strided; lines r = (pr, po) with pr the index of the
 //     axes before it and po of the axes after it, consecutive po adjacent):
-//     D[k][line] = sum_j C[k][j] X[line][j]; MMA A = C (one or two 128-row
-//     blocks), B = X (N = the tile's lines); TMEM lane = k.  Tile = up to T
-//     consecutive po of one pr (never across a break of the line view).
-// In both forms an epilogue thread owns one TMEM lane and its registers map
-// to consecutive global addresses.
+//     tiles of up to 128 consecutive po of one pr; for each k the 32 lines
+//     of a warp are 128 contiguous bytes.
 //
 // The kernel is persistent (one CTA per SM, tiles strided by the grid) and
-// warp-specialised, with mbarrier-tracked rings in shared memory:
-//   warps 0-7   convert X chunks (32 values of j): read the raw tile, split
-//               it and store the hi / lo operand chunk in place;
-//   warps 8-15  drain the accumulators (double-buffered when two fit in
-//               TMEM) and write the pass's output;
-//   warp 16     owns TMEM; streams the pre-arranged DCT chunks (TMA bulk);
-//   warp 17     one thread issues the MMAs and commits ring slots;
-//   warp 18     streams the raw X chunks into the operand slots (TMA tensor
-//               copies; where the layout does not allow TMA, the converters
-//               load X from global memory themselves).
-// Every wait is bounded; a wait that gives up raises a CTA-wide abort flag,
-// the roles leave their loops, copies and MMAs in flight are drained, TMEM
-// is freed and the status word gets kStTimeout.
+// warp-specialised, with mbarrier-tracked rings:
+//   warp 18     TMA tensor copies of the raw X chunks (32 values of j x 128
+//               lines) into a shared-memory ring;
+//   warps 0-7   convert: warp w reads lines 32 (w % 4) .. +31, K values
+//               16 (w / 4) .. +15 of a chunk, splits them and stores hi / lo
+//               into a tensor-memory chunk slot (tcgen05.st);
+//   warp 16     owns TMEM; streams the pre-arranged DCT chunks (TMA bulk
+//               copies), or loads them once when they all fit;
+//   warp 17     one thread issues the MMAs and commits the ring slots;
+//   warps 8-15  drain the accumulators (double-buffered when two fit) and
+//               write the pass's output.
+// Where the strides do not allow TMA the converters load X from global
+// memory themselves.  Every wait is bounded; a wait that gives up raises a
+// CTA-wide abort flag, the roles leave their loops, copies and MMAs in
+// flight are drained, TMEM is freed and the status word gets kStTimeout.
 //
-// Shared-memory operand layout: canonical K-major, no swizzle.  A core matrix
-// is 8 rows x 16 bytes (8 x 4 FP32) stored as 128 contiguous bytes; within a
-// 32-wide K chunk the 8 core matrices of a row group are contiguous (leading
-// byte offset 128) and row groups are 1024 bytes apart (stride byte offset).
-// An X slot holds [hi: rows x 128 B][lo: rows x 128 B]; the raw TMA tile of
-// the (first) source lands in the hi half, the second source of pass 0 in
-// the lo half.
+// Shared-memory layout of a DCT chunk (B operand): canonical K-major, no
+// swizzle.  A core matrix is 8 rows x 16 bytes (8 x 4 FP32) stored as 128
+// contiguous bytes; within a 32-wide K chunk the 8 core matrices of a row
+// group are contiguous (leading byte offset 128) and row groups are 1024
+// bytes apart (stride byte offset).  A chunk is [hi: Np rows][lo: Np rows].
+// Tensor-memory layout of an X chunk slot (A operand): lane = line, 64
+// columns: hi of j = 0..31, then lo of j = 0..31.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <limits.h>
@@ -65,16 +69,18 @@ namespace tc {
 
 constexpr int kConvWarps = 8;                      // X converters
 constexpr int kEpiWarps = 8;                       // accumulator readers
-constexpr int kProdWarp = kConvWarps + kEpiWarps;  // DCT bulk copies, TMEM owner
+constexpr int kProdWarp = kConvWarps + kEpiWarps;  // DCT copies, TMEM owner
 constexpr int kMmaWarp = kProdWarp + 1;            // MMA issue
 constexpr int kXWarp = kMmaWarp + 1;               // X tensor copies
 constexpr int kThreads = (kXWarp + 1) * 32;
-constexpr int kConvBar = 1;                        // named barrier of the converter warps
 constexpr int kBK = 32;                            // K chunk
-constexpr uint32_t kBlockBytes = 128 * kBK * 4;    // one 128-row operand block of a chunk (16 KB)
-constexpr long long kSpinLimit = 1ll << 24;        // bounded mbarrier waits
-constexpr int kMaxStages = 4;
+constexpr int kTileLines = 128;                    // lines per tile (MMA M)
+constexpr uint32_t kRawBytes = kTileLines * kBK * 4;   // one source's raw chunk (16 KB)
+constexpr uint32_t kSuspendNs = 20000;             // longest suspension of one barrier test
+constexpr long long kWaitTests = 50000;            // barrier tests before a wait gives up (~1 s)
+constexpr int kMaxDStages = 4, kMaxRStages = 6, kMaxTStages = 4;
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kXCols = 2 * kBK;               // TMEM columns of an X chunk slot
 constexpr int kEpiPitch = 20;                      // floats per row of an epilogue transpose buffer
 constexpr uint32_t kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
 
@@ -98,12 +104,13 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (TMEM) += A (TMEM, lane = row, one column per K value) x B (shared memory)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 // arrive on mbar once every MMA issued so far by this thread has completed
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -112,7 +119,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
@@ -120,28 +126,32 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
 }
+// Test for the completion of the phase of the given parity; a thread whose
+// phase is not complete is suspended (at most kSuspendNs) instead of
+// spinning, which keeps the issue slots free for the warps that work.
 __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        : "=r"(ok) : "r"(a), "r"(parity), "n"(kSuspendNs) : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of the given parity.  Gives up early when the
-// CTA's abort flag is set; raises the flag when the limit is reached.
+// Bounded wait (at most kWaitTests tests, about a second) for the phase of
+// the given parity.  Gives up early when the CTA's abort flag is set; raises
+// the flag when the limit is reached.
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t a, uint32_t parity, volatile int* abort) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
+    for (long long i = 0; i < kWaitTests; ++i) {
         if (mbar_test(a, parity)) return true;
-        if ((i & 63) == 63 && *abort) return false;
+        if (*abort) return false;
     }
     *abort = 1;
     return false;
 }
 // bounded wait that ignores the abort flag (draining before exit)
 __device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i)
+    for (long long i = 0; i < kWaitTests; ++i)
         if (mbar_test(a, parity)) return true;
     return false;
 }
@@ -185,31 +195,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// named barrier of the converter warps, AND of a predicate over them
-__device__ __forceinline__ bool conv_bar_and(bool p) {
-    uint32_t r;
+// the inverse: 32 lanes x 16 consecutive columns from registers (no wait)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
     asm volatile(
-        "{\n\t.reg .pred q, d;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred d, %2, %3, q;\n\t"
-        "selp.u32 %0, 1, 0, d;\n\t}\n"
-        : "=r"(r) : "r"((uint32_t)p), "n"(kConvBar), "n"(kConvWarps * 32) : "memory");
-    return r != 0;
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :: "r"(taddr),
+           "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+           "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+           "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+           "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
 }
-__device__ __forceinline__ void conv_bar() {
-    asm volatile("bar.sync %0, %1;" :: "n"(kConvBar), "n"(kConvWarps * 32) : "memory");
-}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
-}
-
-// byte offset of element (row, kk) of a K-major operand chunk (kk < 32)
-__device__ __forceinline__ uint32_t core_off(int row, int kk) {
-    return (uint32_t)((row >> 3) * 1024 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4);
 }
 
 }  // namespace tc
@@ -219,8 +222,7 @@ struct TcPass {
     int axis, L;
     long long pre, post, N;
     int caseB;      // post == 1 (form 0)
-    int RB;         // form 1: 128-row blocks of the DCT (1 or 2)
-    int Np;         // form 0: L padded to 16
+    int Np;         // L padded to 16 (MMA N)
     int nch;        // K chunks of 32
 };
 
@@ -233,15 +235,15 @@ __host__ __device__ inline TcPass tc_pass_geom(const int F[3], int ax1, int ax2,
     for (int a = g.axis + 1; a < 3; ++a) g.post *= F[a];
     g.N = g.pre * g.post;
     g.caseB = (g.post == 1);
-    g.RB = (g.L + 127) / 128;
     g.Np = ((g.L + 15) / 16) * 16;
     g.nch = (g.L + tc::kBK - 1) / tc::kBK;
     return g;
 }
 
-// tiles of a pass with T lines per tile (form 1: per pr, ceil(post / T))
-__host__ __device__ inline long long tc_tiles_of(const TcPass& g, int T) {
-    if (g.L < 2 || T <= 0) return 0;
+// tiles of a pass (form 1: per pr, ceil(post / 128))
+__host__ __device__ inline long long tc_tiles_of(const TcPass& g) {
+    if (g.L < 2) return 0;
+    const int T = tc::kTileLines;
     return g.caseB ? (g.N + T - 1) / T : g.pre * ((g.post + T - 1) / T);
 }
 
@@ -259,65 +261,34 @@ static int tc_sm_count() {
     return n;
 }
 
-// form 1: most lines a tile may hold, so that two DCT slots (two 128-row
-// blocks) and two X slots of any job of a launch fit in shared memory together
-static constexpr int kMaxTileLines = 192;
-
-// Lines per tile of a pass, from the job's own geometry only (so that a job
-// is tiled the same way alone and in a batch): form 0 tiles hold 128 lines;
-// form 1 takes the multiple of 16 in [64, 192] that minimises
-// rounds x (lines + 48), rounds = tiles / SMs rounded up.
 int tc_tile_lines(const int F[3], int ax1, int ax2, int pass) {
-    const TcPass g = tc_pass_geom(F, ax1, ax2, pass);
-    if (g.L < 2) return 0;
-    if (g.caseB) return 128;
-    const long long nsm = tc_sm_count();
-    int best = 64;
-    long long bestc = LLONG_MAX;
-    for (int T = 64; T <= kMaxTileLines; T += 16) {
-        const long long tiles = tc_tiles_of(g, T);
-        const long long cost = ((tiles + nsm - 1) / nsm) * (T + 48);
-        if (cost < bestc) { bestc = cost; best = T; }
-    }
-    return best;
+    return tc_pass_geom(F, ax1, ax2, pass).L < 2 ? 0 : tc::kTileLines;
 }
 
 long long tc_pass_tiles(const int F[3], int ax1, int ax2, int pass) {
-    return tc_tiles_of(tc_pass_geom(F, ax1, ax2, pass), tc_tile_lines(F, ax1, ax2, pass));
+    return tc_tiles_of(tc_pass_geom(F, ax1, ax2, pass));
 }
 
 bool tc_pass_supported(const int F[3], int ax1, int ax2, int pass) {
     const TcPass g = tc_pass_geom(F, ax1, ax2, pass);
-    if (g.L < 2) return true;
-    return g.caseB ? (g.Np <= 256) : (g.RB <= 2);
+    return g.L < 2 || g.Np <= 256;
 }
 
 // floats of the pre-arranged split matrix for one pass
 long long tc_matrix_floats(const int F[3], int ax1, int ax2, int pass) {
     const TcPass g = tc_pass_geom(F, ax1, ax2, pass);
     if (g.L < 2) return 0;
-    const long long rows = g.caseB ? g.Np : 128LL * g.RB;
-    return rows * g.nch * tc::kBK * 2;
+    return (long long)g.Np * g.nch * tc::kBK * 2;
 }
 
 void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass) {
     const TcPass g = tc_pass_geom(F, ax1, ax2, pass);
     if (g.L < 2) return;
-    uint32_t d, x;
-    int acc;
-    if (g.caseB) {
-        d = 2u * (uint32_t)g.Np * 128u;
-        x = 2u * 128u * 128u;
-        acc = g.Np;
-    } else {
-        const int BN = tc_tile_lines(F, ax1, ax2, pass);
-        d = 2u * (uint32_t)g.RB * tc::kBlockBytes;
-        x = 2u * (uint32_t)BN * 128u;
-        acc = g.RB * ((BN + 31) & ~31);
-    }
+    const uint32_t d = 2u * (uint32_t)g.Np * 128u;                        // DCT chunk (hi | lo)
+    const uint32_t r = (pass == 0 ? 2u : 1u) * tc::kRawBytes;            // raw X chunk(s)
     if (d > c->dslot) c->dslot = d;
-    if (x > c->xslot) c->xslot = x;
-    if (acc > c->acc_need) c->acc_need = acc;
+    if (r > c->rslot) c->rslot = r;
+    if (g.Np > c->acc_need) c->acc_need = g.Np;
     // one DCT matrix for all tiles when every job has the same face dims and axes
     const int key[3] = {F[0] * 4 + ax1, F[1] * 4 + ax2, F[2]};
     if (c->nch == 0) {
@@ -332,13 +303,16 @@ bool tc_cfg_finish(TcCfg* c) {
     if (c->dslot == 0) { c->smem = 0; return true; }
     const size_t budget = 226 * 1024 - tc::kEpiBytes;   // rings; 1 KB of static shared memory
     c->sd = 2;
-    c->sx = 2;
-    auto need = [&]() { return (size_t)c->sd * c->dslot + (size_t)c->sx * c->xslot; };
-    if (need() > budget || c->acc_need > (int)tc::kTmemCols) return false;
-    while (c->sx < tc::kMaxStages && need() + c->xslot <= budget) c->sx++;
-    while (c->sd < tc::kMaxStages && need() + c->dslot <= budget) c->sd++;
-    c->nacc = (2 * c->acc_need <= (int)tc::kTmemCols) ? 2 : 1;
-    c->acc_cols = tc::kTmemCols / c->nacc;
+    c->sr = 2;
+    auto need = [&]() { return (size_t)c->sd * c->dslot + (size_t)c->sr * c->rslot; };
+    if (need() > budget || c->acc_need > 256) return false;
+    while (c->sr < tc::kMaxRStages && need() + c->rslot <= budget) c->sr++;
+    while (c->sd < tc::kMaxDStages && need() + c->dslot <= budget) c->sd++;
+    c->acc_cols = (uint32_t)((c->acc_need + 31) & ~31);
+    c->nacc = (2 * c->acc_cols + 2 * tc::kXCols <= tc::kTmemCols) ? 2 : 1;
+    int st = (int)((tc::kTmemCols - c->nacc * c->acc_cols) / tc::kXCols);
+    c->st = st > tc::kMaxTStages ? tc::kMaxTStages : st;
+    if (c->st < 2) return false;
     c->resident = (c->geom[0] >= 0 && c->nch <= c->sd) ? 1 : 0;
     c->epi_off = (uint32_t)need();
     c->smem = need() + tc::kEpiBytes;
@@ -348,8 +322,7 @@ bool tc_cfg_finish(TcCfg* c) {
 }
 
 // Host: arrange M (L x L, double, row-major; M[k][j]) for one pass:
-// [chunk][hi|lo][row block][rows x 32 in the core-matrix layout], with
-// row blocks of 128 rows (form 1) or one block of Np rows (form 0).
+// [chunk][hi|lo][Np rows x 32 in the core-matrix layout].
 static float tf32_round_host(float x) {
     uint32_t u;
     memcpy(&u, &x, 4);
@@ -365,25 +338,19 @@ static float tf32_round_host(float x) {
 void tc_arrange_matrix(const int F[3], int ax1, int ax2, int pass, const double* M, float* out) {
     const TcPass g = tc_pass_geom(F, ax1, ax2, pass);
     if (g.L < 2) return;
-    const int L = g.L;
-    const int rows_blk = g.caseB ? g.Np : 128;
-    const int nblk = g.caseB ? 1 : g.RB;
-    const long long blk_floats = (long long)rows_blk * tc::kBK;   // one (chunk, hi|lo) block
-    for (int rb = 0; rb < nblk; ++rb)
-        for (int c = 0; c < g.nch; ++c)
-            for (int r = 0; r < rows_blk; ++r)
-                for (int kk = 0; kk < tc::kBK; ++kk) {
-                    const int row = rb * 128 + r, j = c * tc::kBK + kk;
-                    const double v = (row < L && j < L) ? M[(long long)row * L + j] : 0.0;
-                    const float hi = tf32_round_host((float)v);
-                    const float lo = (float)(v - (double)hi);
-                    // chunk c holds [hi | lo] x [row block] contiguously, the
-                    // order of the ring slot it is copied into
-                    const long long chunk0 = (long long)c * 2 * nblk * blk_floats;
-                    const long long off = (r >> 3) * 256 + (kk >> 2) * 32 + (r & 7) * 4 + (kk & 3);
-                    out[chunk0 + (long long)rb * blk_floats + off] = hi;
-                    out[chunk0 + (long long)(nblk + rb) * blk_floats + off] = lo;
-                }
+    const int L = g.L, rows = g.Np;
+    const long long blk = (long long)rows * tc::kBK;   // floats of one (chunk, hi|lo) block
+    for (int c = 0; c < g.nch; ++c)
+        for (int r = 0; r < rows; ++r)
+            for (int kk = 0; kk < tc::kBK; ++kk) {
+                const int j = c * tc::kBK + kk;
+                const double v = (r < L && j < L) ? M[(long long)r * L + j] : 0.0;
+                const float hi = tf32_round_host((float)v);
+                const float lo = (float)(v - (double)hi);
+                const long long off = (r >> 3) * 256 + (kk >> 2) * 32 + (r & 7) * 4 + (kk & 3);
+                out[(long long)c * 2 * blk + off] = hi;
+                out[(long long)c * 2 * blk + blk + off] = lo;
+            }
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver at run time
@@ -406,8 +373,9 @@ size_t tc_map_bytes() { return (size_t)kTcMaps * sizeof(CUtensorMap); }
 
 // Host: tensor maps of the X sources of every pass of one job into `out`
 // (kTcMaps maps: [pass][source]; FP32 device arrays b, u, t1, t2 of the
-// job's faces).  Returns the mask of passes whose sources have maps; a pass
-// without one (strides not multiples of 16 bytes) loads X without TMA.
+// job's faces).  Box: 32 values of j x 128 lines.  Returns the mask of
+// passes whose sources have maps; a pass without one (strides not
+// multiples of 16 bytes) loads X without TMA.
 int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float* u, const float* t1,
                    const float* t2, void* out) {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
@@ -433,19 +401,20 @@ int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float
             CUresult r;
             const cuuint32_t es[3] = {1, 1, 1};
             if (g.caseB) {
+                // [N lines][L], box 32 x 128, 128-byte swizzle
                 if (g.L % 4 != 0) { ok = false; break; }
                 const cuuint64_t dim[2] = {(cuuint64_t)g.L, (cuuint64_t)g.N};
                 const cuuint64_t str[1] = {(cuuint64_t)g.L * 4};
-                const cuuint32_t box[2] = {(cuuint32_t)tc::kBK, 128};
+                const cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)tc::kTileLines};
                 r = enc(&maps[2 * q + i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)src[i], dim, str, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             } else {
+                // [pre][L][post], box 128 (po) x 32 (j) x 1
                 if (g.post % 4 != 0) { ok = false; break; }
-                const int BN = tc_tile_lines(F, ax1, ax2, q);
                 const cuuint64_t dim[3] = {(cuuint64_t)g.post, (cuuint64_t)g.L, (cuuint64_t)g.pre};
                 const cuuint64_t str[2] = {(cuuint64_t)g.post * 4, (cuuint64_t)g.post * g.L * 4};
-                const cuuint32_t box[3] = {(cuuint32_t)BN, (cuuint32_t)tc::kBK, 1};
+                const cuuint32_t box[3] = {(cuuint32_t)tc::kTileLines, (cuuint32_t)tc::kBK, 1};
                 r = enc(&maps[2 * q + i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)src[i], dim, str, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -462,10 +431,8 @@ int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float
 // One tile of one job's pass.
 struct TcTile {
     const Job* J;
-    int form;          // 0: lines in TMEM lanes; 1: DCT rows in TMEM lanes
-    int L, Np, RB, nch;
-    int BN;            // MMA N (form 0: Np; form 1: tile lines T)
-    int rows;          // rows of the X operand (form 0: 128; form 1: BN)
+    int form;          // 0: contracted axis contiguous; 1: strided
+    int L, Np, nch;
     int nl;            // valid lines
     long long post;
     long long line0;   // form 0: first line
@@ -479,26 +446,21 @@ __device__ __forceinline__ TcTile tc_tile(const Job* __restrict__ jobs, int njob
     const int jid = find_job(prefix, njobs, t);
     const Job& J = jobs[jid];
     const TcPass g = tc_pass_geom(J.F, J.ax1, J.ax2, pass);
-    const int T = J.tc_T[pass];
     const long long local = t - prefix[jid];
+    const int T = tc::kTileLines;
     s.J = &J;
     s.form = g.caseB ? 0 : 1;
     s.L = g.L;
     s.Np = g.Np;
-    s.RB = g.RB;
     s.nch = g.nch;
     s.post = g.post;
     if (s.form == 0) {
-        s.BN = g.Np;
-        s.rows = 128;
         s.line0 = local * T;
         const long long rem = g.N - s.line0;
         s.nl = (int)(rem < T ? rem : T);
         s.pr = 0;
         s.po0 = 0;
     } else {
-        s.BN = T;
-        s.rows = T;
         const long long tpp = (g.post + T - 1) / T;
         s.pr = local / tpp;
         s.po0 = (local - s.pr * tpp) * T;
@@ -514,34 +476,41 @@ __device__ __forceinline__ TcTile tc_tile(const Job* __restrict__ jobs, int njob
 template <int PASS>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_axis_tc(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, long long total,
-              TcCfg cfg, double* __restrict__ part, int* __restrict__ status) {
+              TcCfg cfg, int* __restrict__ status) {
     using namespace tc;
+    constexpr int NSRC = (PASS == 0) ? 2 : 1;   // X sources (pass 0: b + u)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bar[5 * kMaxStages + 5];
+    // barriers: DCT full / empty, raw X full / empty, TMEM X full / empty,
+    // accumulator full / empty, drain
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxDStages + 2 * kMaxRStages + 2 * kMaxTStages + 5];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int* abort = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // barriers: DCT slot full / empty, X slot raw / converted / empty,
-    // accumulator full / empty, drain
     const uint32_t b_dfull = smem_u32(&bar[0]);
-    const uint32_t b_dempty = smem_u32(&bar[kMaxStages]);
-    const uint32_t b_xraw = smem_u32(&bar[2 * kMaxStages]);
-    const uint32_t b_xfull = smem_u32(&bar[3 * kMaxStages]);
-    const uint32_t b_xempty = smem_u32(&bar[4 * kMaxStages]);
-    const uint32_t b_afull = smem_u32(&bar[5 * kMaxStages]);
-    const uint32_t b_aempty = smem_u32(&bar[5 * kMaxStages + 2]);
-    const uint32_t b_drain = smem_u32(&bar[5 * kMaxStages + 4]);
+    const uint32_t b_dempty = b_dfull + 8 * kMaxDStages;
+    const uint32_t b_rfull = b_dempty + 8 * kMaxDStages;
+    const uint32_t b_rempty = b_rfull + 8 * kMaxRStages;
+    const uint32_t b_tfull = b_rempty + 8 * kMaxRStages;
+    const uint32_t b_tempty = b_tfull + 8 * kMaxTStages;
+    const uint32_t b_afull = b_tempty + 8 * kMaxTStages;
+    const uint32_t b_aempty = b_afull + 16;
+    const uint32_t b_drain = b_aempty + 16;
     const uint32_t s_base = smem_u32(smem_raw);
-    const uint32_t s_x = s_base + (uint32_t)cfg.sd * cfg.dslot;   // X ring after the DCT ring
+    const uint32_t s_raw = s_base + (uint32_t)cfg.sd * cfg.dslot;   // raw X ring after the DCT ring
 
     if (tid == 0) {
-        for (int i = 0; i < kMaxStages; ++i) {
+        for (int i = 0; i < kMaxDStages; ++i) {
             mbar_init(b_dfull + 8 * i, 1);
             mbar_init(b_dempty + 8 * i, 1);
-            mbar_init(b_xraw + 8 * i, 1);
-            mbar_init(b_xfull + 8 * i, kConvWarps);
-            mbar_init(b_xempty + 8 * i, 1);
+        }
+        for (int i = 0; i < kMaxRStages; ++i) {
+            mbar_init(b_rfull + 8 * i, 1);
+            mbar_init(b_rempty + 8 * i, kConvWarps);
+        }
+        for (int i = 0; i < kMaxTStages; ++i) {
+            mbar_init(b_tfull + 8 * i, kConvWarps);
+            mbar_init(b_tempty + 8 * i, 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(b_afull + 8 * i, 1);
@@ -556,15 +525,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_slot;
+    const uint32_t xcol0 = (uint32_t)cfg.nacc * cfg.acc_cols;   // first TMEM column of the X slots
     const long long t0 = blockIdx.x, dt = gridDim.x;
 
     if (warp < kConvWarps) {
         // ------------------------------------------------ X converters
-        // warp w handles K values 4w .. 4w+3 of every chunk, lane i the rows
-        // i, i + 32, ...  All converter threads take the same branches: their
-        // waits are combined by a named-barrier AND.
-        const int quad = warp;
-        long long x_it = 0;
+        const int q = warp & 3, kh = warp >> 2;
+        const int lr = 32 * q + lane;              // line of the tile (TMEM lane)
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        long long r_it = 0, x_it = 0;
         bool run = true;
         for (long long t = t0; t < total && run; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
@@ -573,119 +542,106 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
                                          : (PASS == 2) ? (const float*)J.t2 : (const float*)J.t1;
             const float* __restrict__ X1 = (const float*)J.u;   // pass 0 only
-            // element index of row i's first element (-1: padding row)
-            long long rbase[6];
+            const bool lv = lr < s.nl;
+            const long long gbase = s.form ? s.pr * s.L * s.post + s.po0 + lr : (s.line0 + lr) * s.L;
             const long long js = s.form ? s.post : 1;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                const int row = lane + 32 * i;
-                rbase[i] = (row < s.nl) ? (s.form ? s.pr * s.L * s.post + s.po0 + row : (s.line0 + row) * s.L) : -1;
-            }
-            const uint32_t lo_off = (uint32_t)s.rows * 128u;
             for (int c = 0; c < s.nch; ++c) {
-                const int xs = (int)(x_it % cfg.sx);
-                const bool ok = mbar_wait_ab(b_xraw + 8 * xs, (uint32_t)((x_it / cfg.sx) & 1), abort);
-                if (!conv_bar_and(ok)) { run = false; break; }
-                unsigned char* xb = smem_raw + (size_t)cfg.sd * cfg.dslot + (size_t)xs * cfg.xslot;
-                const int j0 = c * kBK + 4 * quad;
-                float v[6][4];
+                const int rs = (int)(r_it % cfg.sr);
+                bool ok = mbar_wait_ab(b_rfull + 8 * rs, (uint32_t)((r_it / cfg.sr) & 1), abort);
+                if (!__all_sync(kFull, ok)) { run = false; break; }
+                float v[16];
                 if (s.tma) {
-                    // raw tile(s) in the slot: form 0 [line][32] 128B-swizzled,
-                    // form 1 [32][rows]; pass 0's second source in the lo half
+                    // raw tile(s): form 0 [line][32] 128B-swizzled, form 1 [32][line]
+                    const unsigned char* rb = smem_raw + (size_t)cfg.sd * cfg.dslot + (size_t)rs * cfg.rslot;
+                    if (s.form == 0) {
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        const int row = lane + 32 * i;
-                        v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.f;
-                        if (row < s.rows) {
-                            if (s.form == 0) {
-                                const uint32_t off = (uint32_t)row * 128u + (uint32_t)((quad ^ (row & 7)) << 4);
-                                float4 x = *reinterpret_cast<const float4*>(xb + off);
-                                if (PASS == 0) {
-                                    const float4 y = *reinterpret_cast<const float4*>(xb + lo_off + off);
-                                    x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
-                                }
-                                v[i][0] = x.x; v[i][1] = x.y; v[i][2] = x.z; v[i][3] = x.w;
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const uint32_t off = (uint32_t)((4 * quad + e) * s.rows + row) * 4u;
-                                    float x = *reinterpret_cast<const float*>(xb + off);
-                                    if (PASS == 0) x += *reinterpret_cast<const float*>(xb + lo_off + off);
-                                    v[i][e] = x;
-                                }
+                        for (int g = 0; g < 4; ++g) {
+                            const uint32_t off = (uint32_t)lr * 128u + (uint32_t)(((4 * kh + g) ^ (lr & 7)) << 4);
+                            float4 x = *reinterpret_cast<const float4*>(rb + off);
+                            if (NSRC == 2) {
+                                const float4 y = *reinterpret_cast<const float4*>(rb + kRawBytes + off);
+                                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
                             }
+                            v[4 * g] = x.x; v[4 * g + 1] = x.y; v[4 * g + 2] = x.z; v[4 * g + 3] = x.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const uint32_t off = (uint32_t)((16 * kh + e) * kTileLines + lr) * 4u;
+                            float x = *reinterpret_cast<const float*>(rb + off);
+                            if (NSRC == 2) x += *reinterpret_cast<const float*>(rb + kRawBytes + off);
+                            v[e] = x;
                         }
                     }
-                    conv_bar();   // every raw value is in registers before the slot is overwritten
                 } else {
+                    const int j0 = c * kBK + 16 * kh;
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0.f;
-                        if (rbase[i] >= 0 && j0 < s.L) {
-                            const long long a = rbase[i] + (long long)j0 * js;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (j0 + e < s.L) {
-                                    float x = __ldg(X0 + a + e * js);
-                                    if (PASS == 0) x += __ldg(X1 + a + e * js);
-                                    v[i][e] = x;
-                                }
+                    for (int e = 0; e < 16; ++e) {
+                        float x = 0.f;
+                        if (lv && j0 + e < s.L) {
+                            const long long a = gbase + (long long)(j0 + e) * js;
+                            x = __ldg(X0 + a);
+                            if (NSRC == 2) x += __ldg(X1 + a);
                         }
+                        v[e] = x;
                     }
                 }
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const int row = lane + 32 * i;
-                    if (row < s.rows) {
-                        float4 h, l;
-                        h.x = tf32_round(v[i][0]); l.x = v[i][0] - h.x;
-                        h.y = tf32_round(v[i][1]); l.y = v[i][1] - h.y;
-                        h.z = tf32_round(v[i][2]); l.z = v[i][2] - h.z;
-                        h.w = tf32_round(v[i][3]); l.w = v[i][3] - h.w;
-                        const uint32_t off = core_off(row, 4 * quad);
-                        *reinterpret_cast<float4*>(xb + off) = h;
-                        *reinterpret_cast<float4*>(xb + lo_off + off) = l;
-                    }
-                }
-                fence_async_smem();
+                // the raw slot may be refilled once every converter warp has its values
                 __syncwarp();
-                if (lane == 0) mbar_arrive(b_xfull + 8 * xs);
+                if (lane == 0) mbar_arrive(b_rempty + 8 * rs);
+                ++r_it;
+                const int ts = (int)(x_it % cfg.st);
+                ok = mbar_wait_ab(b_tempty + 8 * ts, (uint32_t)(((x_it / cfg.st) & 1) ^ 1), abort);
+                if (!__all_sync(kFull, ok)) { run = false; break; }
+                fence_after();
+                float hi[16], lo[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    hi[e] = tf32_round(v[e]);
+                    lo[e] = v[e] - hi[e];
+                }
+                const uint32_t col = xcol0 + (uint32_t)ts * kXCols + 16u * kh;
+                tmem_st16(tl + col, hi);
+                tmem_st16(tl + col + kBK, lo);
+                tmem_st_wait();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_tfull + 8 * ts);
                 ++x_it;
             }
         }
     } else if (warp == kXWarp) {
         // ------------------------------------------------ raw X chunks (TMA tensor copies)
         if (lane == 0) {
-            long long x_it = 0;
+            long long r_it = 0;
             for (long long t = t0; t < total && !*abort; t += dt) {
                 const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
                 if (!s.active) continue;
                 const char* maps = (const char*)s.J->tmaps + (size_t)2 * PASS * 128;
-                const uint32_t lo_off = (uint32_t)s.rows * 128u;
-                const uint32_t rb = s.form ? (uint32_t)s.rows * (uint32_t)kBK * 4u : 128u * (uint32_t)kBK * 4u;
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
-                    const int xs = (int)(x_it % cfg.sx);
-                    if (!mbar_wait_ab(b_xempty + 8 * xs, (uint32_t)(((x_it / cfg.sx) & 1) ^ 1), abort)) { ok = false; break; }
-                    const uint32_t xb = s_x + (uint32_t)xs * cfg.xslot;
+                    const int rs = (int)(r_it % cfg.sr);
+                    if (!mbar_wait_ab(b_rempty + 8 * rs, (uint32_t)(((r_it / cfg.sr) & 1) ^ 1), abort)) { ok = false; break; }
+                    const uint32_t dst = s_raw + (uint32_t)rs * cfg.rslot;
                     if (s.tma) {
-                        mbar_expect_tx(b_xraw + 8 * xs, (PASS == 0 ? 2u : 1u) * rb);
-                        for (int i = 0; i < (PASS == 0 ? 2 : 1); ++i) {
+                        mbar_expect_tx(b_rfull + 8 * rs, NSRC * kRawBytes);
+#pragma unroll
+                        for (int i = 0; i < NSRC; ++i) {
                             if (s.form == 0)
-                                tma_tile2d(xb + i * lo_off, maps + 128 * i, c * kBK, (int)s.line0, b_xraw + 8 * xs);
+                                tma_tile2d(dst + i * kRawBytes, maps + 128 * i, c * kBK, (int)s.line0, b_rfull + 8 * rs);
                             else
-                                tma_tile3d(xb + i * lo_off, maps + 128 * i, (int)s.po0, c * kBK, (int)s.pr, b_xraw + 8 * xs);
+                                tma_tile3d(dst + i * kRawBytes, maps + 128 * i, (int)s.po0, c * kBK, (int)s.pr, b_rfull + 8 * rs);
                         }
                     } else {
-                        mbar_arrive(b_xraw + 8 * xs);   // the converters load this chunk themselves
+                        mbar_arrive(b_rfull + 8 * rs);   // the converters load this chunk themselves
                     }
-                    ++x_it;
+                    ++r_it;
                 }
                 if (!ok) break;
             }
             // copies still in flight land before the CTA exits
-            for (long long i = (x_it > cfg.sx ? x_it - cfg.sx : 0); i < x_it; ++i)
-                mbar_wait_drain(b_xraw + 8 * (int)(i % cfg.sx), (uint32_t)((i / cfg.sx) & 1));
+            for (long long i = (r_it > cfg.sr ? r_it - cfg.sr : 0); i < r_it; ++i)
+                mbar_wait_drain(b_rfull + 8 * (int)(i % cfg.sr), (uint32_t)((i / cfg.sr) & 1));
         }
     } else if (warp == kProdWarp) {
         // ------------------------------------------------ DCT chunks (bulk copies)
@@ -695,7 +651,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
                 if (!s.active) continue;
                 const float* Mpre = (const float*)s.J->Ctc[PASS];
-                const uint32_t db = s.form ? 2u * (uint32_t)s.RB * kBlockBytes : 2u * (uint32_t)s.Np * 128u;
+                const uint32_t db = 2u * (uint32_t)s.Np * 128u;
                 bool ok = true;
                 if (cfg.resident) {
                     // every tile uses the same matrix: chunk c stays in slot c
@@ -730,62 +686,36 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 if (!mbar_wait_ab(b_aempty + 8 * a, (uint32_t)(((a_it / cfg.nacc) & 1) ^ 1), abort)) break;
                 fence_after();
                 const uint32_t dacc = tmem + (uint32_t)a * cfg.acc_cols;
-                const uint32_t bstride = (uint32_t)((s.BN + 31) & ~31);
-                const uint32_t idesc = idesc_tf32(128, s.BN);
-                const uint32_t xlo = (uint32_t)s.rows * 128u;
+                const uint32_t idesc = idesc_tf32(kTileLines, s.Np);
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
-                    const int ds = cfg.resident ? c : (int)(d_it % cfg.sd), xs = (int)(x_it % cfg.sx);
+                    const int ds = cfg.resident ? c : (int)(d_it % cfg.sd), ts = (int)(x_it % cfg.st);
                     const uint32_t dpar = cfg.resident ? 0u : (uint32_t)((d_it / cfg.sd) & 1);
                     if (!mbar_wait_ab(b_dfull + 8 * ds, dpar, abort) ||
-                        !mbar_wait_ab(b_xfull + 8 * xs, (uint32_t)((x_it / cfg.sx) & 1), abort)) {
+                        !mbar_wait_ab(b_tfull + 8 * ts, (uint32_t)((x_it / cfg.st) & 1), abort)) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    // descriptors of the chunk's operands; a K step of 8 adds
-                    // 256 bytes (16 in descriptor units) to the start address
-                    const uint64_t xh = sdesc(s_x + (uint32_t)xs * cfg.xslot, 128, 1024);
-                    const uint64_t xl = xh + (xlo >> 4);
+                    // B: the DCT chunk [hi: Np rows][lo: Np rows]; a K step of 8
+                    // adds 256 bytes (16 in descriptor units).  A: TMEM columns
+                    // of the X slot, hi then lo; a K step adds 8 columns.
                     const uint64_t ch = sdesc(s_base + (uint32_t)ds * cfg.dslot, 128, 1024);
-                    const uint32_t en = (c > 0) ? 1u : 0u;   // first K step of a tile overwrites
-                    if (s.form == 0) {
-                        const uint64_t cl = ch + ((uint32_t)s.Np * 8u);   // Np * 128 bytes
+                    const uint64_t cl = ch + (uint32_t)s.Np * 8u;
+                    const uint32_t xh = tmem + xcol0 + (uint32_t)ts * kXCols, xl = xh + kBK;
+                    const uint32_t en = (c > 0) ? 1u : 0u;   // the tile's first K step overwrites
+                    // product by product (hi x hi over the chunk's K steps, then
+                    // hi x lo, then lo x hi): consecutive MMAs walk along K, which
+                    // issues measurably faster than alternating the split
+                    // operands at every K step
 #pragma unroll
-                        for (int ks = 0; ks < kBK / 8; ++ks) {
-                            const uint64_t o = 16u * ks;
-                            mma_tf32(dacc, xh + o, ch + o, idesc, ks ? 1u : en);
-                            mma_tf32(dacc, xh + o, cl + o, idesc, 1u);
-                            mma_tf32(dacc, xl + o, ch + o, idesc, 1u);
-                        }
-                    } else if (s.RB == 1) {
-                        const uint64_t cl = ch + (kBlockBytes >> 4);
+                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xh + 8 * ks, ch + 16u * ks, idesc, ks ? 1u : en);
 #pragma unroll
-                        for (int ks = 0; ks < kBK / 8; ++ks) {
-                            const uint64_t o = 16u * ks;
-                            mma_tf32(dacc, ch + o, xh + o, idesc, ks ? 1u : en);
-                            mma_tf32(dacc, ch + o, xl + o, idesc, 1u);
-                            mma_tf32(dacc, cl + o, xh + o, idesc, 1u);
-                        }
-                    } else {
-                        // [hi: block 0 | block 1][lo: block 0 | block 1]
-                        const uint64_t ch1 = ch + (kBlockBytes >> 4);
-                        const uint64_t cl0 = ch + (2 * kBlockBytes >> 4), cl1 = ch + (3 * kBlockBytes >> 4);
-                        const uint32_t d1 = dacc + bstride;
+                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xh + 8 * ks, cl + 16u * ks, idesc, 1u);
 #pragma unroll
-                        for (int ks = 0; ks < kBK / 8; ++ks) {
-                            const uint64_t o = 16u * ks;
-                            const uint32_t e0 = ks ? 1u : en;
-                            mma_tf32(dacc, ch + o, xh + o, idesc, e0);
-                            mma_tf32(d1, ch1 + o, xh + o, idesc, e0);
-                            mma_tf32(dacc, ch + o, xl + o, idesc, 1u);
-                            mma_tf32(d1, ch1 + o, xl + o, idesc, 1u);
-                            mma_tf32(dacc, cl0 + o, xh + o, idesc, 1u);
-                            mma_tf32(d1, cl1 + o, xh + o, idesc, 1u);
-                        }
-                    }
+                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xl + 8 * ks, ch + 16u * ks, idesc, 1u);
                     if (!cfg.resident) mma_commit(b_dempty + 8 * ds);
-                    mma_commit(b_xempty + 8 * xs);
+                    mma_commit(b_tempty + 8 * ts);
                     ++d_it;
                     ++x_it;
                 }
@@ -801,71 +731,63 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         // ------------------------------------------------ epilogue
         const int ew = warp - kConvWarps;   // 0..7
         const int q = warp & 3;             // TMEM lane quadrant of this warp
-        const int h = ew >> 2;              // half: DCT row block (form 1, two blocks) or column pieces
+        const int h = ew >> 2;              // half: even or odd column pieces
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        const int lr = 32 * q + lane;       // line of the tile
         long long a_it = 0;
         for (long long t = t0; t < total && !*abort; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
-            if (s.active) {
-                const Job& J = *s.J;
-                const int a = (int)(a_it % cfg.nacc);
-                const bool ok = mbar_wait_ab(b_afull + 8 * a, (uint32_t)((a_it / cfg.nacc) & 1), abort);
-                if (!__all_sync(kFull, ok)) break;
-                fence_after();
-                float* __restrict__ Y = (PASS == 0 || PASS == 2) ? (float*)J.t1 : (float*)J.t2;
-                const bool scaled = (PASS == 1) || (PASS == 0 && J.F[J.ax2] < 2);
-                const int L2s = J.F[J.ax2];
-                long long s_between = 1;
-                for (int ax = J.ax1 + 1; ax < J.ax2; ++ax) s_between *= J.F[ax];
-                const int F1 = J.F[J.ax1];
-                const int npieces = s.BN / 16;
-                const int two_blocks = (s.form == 1 && s.RB == 2);
-                const int rb = two_blocks ? h : 0;
-                const int p0 = two_blocks ? 0 : h, pstep = two_blocks ? 1 : 2;
-                const uint32_t tcol = (uint32_t)a * cfg.acc_cols + (uint32_t)rb * (uint32_t)((s.BN + 31) & ~31);
-                // The warp's accumulator block is 32 rows (its TMEM lanes) by
-                // 16 columns per piece; a row's columns are consecutive in
-                // global memory.  Each lane writes its row into the warp's
-                // transpose buffer; then lane i handles rows 8m + i / 4
-                // (m = 0..3), columns 4 (i % 4) .. +3: eight rows x 64 bytes
-                // per memory instruction.
-                //  form 0: row = line (lane 32q + r), column = k;
-                //  form 1: row = DCT row k = 128 rb + 32q + r, column = line.
+            if (!s.active) continue;
+            const Job& J = *s.J;
+            const int a = (int)(a_it % cfg.nacc);
+            const bool ok = mbar_wait_ab(b_afull + 8 * a, (uint32_t)((a_it / cfg.nacc) & 1), abort);
+            if (!__all_sync(kFull, ok)) break;
+            fence_after();
+            float* __restrict__ Y = (PASS == 0 || PASS == 2) ? (float*)J.t1 : (float*)J.t2;
+            const bool scaled = (PASS == 1) || (PASS == 0 && J.F[J.ax2] < 2);
+            const int L2s = J.F[J.ax2];
+            long long s_between = 1;
+            for (int ax = J.ax1 + 1; ax < J.ax2; ++ax) s_between *= J.F[ax];
+            const int F1 = J.F[J.ax1];
+            const int npieces = s.Np / 16;
+            const uint32_t tcol = tmem + lane_addr + (uint32_t)a * cfg.acc_cols;
+            const bool lv = lr < s.nl;
+            if (s.form == 1) {
+                // thread = line; for each k the warp's 32 lines are 128 contiguous bytes
+                const long long g0 = s.pr * s.L * s.post + s.po0 + lr;
+                const float* __restrict__ srow = J.scale;
+                if (PASS == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
+                for (int p = h; p < npieces; p += 2) {
+                    float v[16];
+                    tmem_ld16(tcol + 16 * p, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int k = 16 * p + i;
+                        if (k < s.L) {
+                            const float y = scaled ? v[i] * __ldg(srow + k) : v[i];
+                            if (lv) Y[g0 + (long long)k * s.post] = y;
+                        }
+                    }
+                }
+            } else {
+                // thread = line, 16 consecutive k per piece.  Each lane writes
+                // its row into the warp's transpose buffer; then lane i handles
+                // lines 8m + i / 4 (m = 0..3), k = 4 (i % 4) .. +3: eight lines
+                // x 64 bytes per memory instruction.
                 float* Ew = reinterpret_cast<float*>(smem_raw + cfg.epi_off) + ew * 32 * kEpiPitch;
                 const int rsub = lane >> 2, csub = 4 * (lane & 3);
-                // this lane's rows 8m + rsub start at global index rbase0 + m * rstep
-                long long rbase0, rstep;
-                unsigned rok = 0;            // bit m: row valid
-                float rsc[4] = {1.f, 1.f, 1.f, 1.f};   // form 1: the row's scale factor
-                const float* __restrict__ srow = J.scale;   // form 0: scale row of the lane's own line
-                if (s.form == 0) {
-                    const long long myline = s.line0 + 32 * q + lane;
-                    if (PASS == 1) srow = J.scale + (long long)((myline / s_between) % F1) * L2s;
-                    rbase0 = (s.line0 + 32 * q + rsub) * s.L;
-                    rstep = 8LL * s.L;
+                const float* __restrict__ srow = J.scale;
+                if (PASS == 1) srow = J.scale + (long long)(((s.line0 + lr) / s_between) % F1) * L2s;
+                const long long rbase0 = (s.line0 + 32 * q + rsub) * s.L, rstep = 8LL * s.L;
+                unsigned rok = 0;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (32 * q + 8 * m + rsub < s.nl) rok |= 1u << m;
-                } else {
-                    const int k0 = 128 * rb + 32 * q + rsub;
-                    rbase0 = s.pr * s.L * s.post + s.po0 + (long long)k0 * s.post;
-                    rstep = 8LL * s.post;
-                    const long long k1 = (PASS == 1) ? (s.pr / s_between) % F1 : 0;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (k0 + 8 * m < s.L) {
-                            rok |= 1u << m;
-                            if (scaled) rsc[m] = __ldg(J.scale + k1 * L2s + k0 + 8 * m);
-                        }
-                }
-                // columns of a row are 16-byte aligned groups of four when
-                // the row length (form 0) or the line stride (form 1) is
-                const bool colvec = s.form ? ((s.post & 3) == 0) : ((s.L & 3) == 0);
-                const int ncols = s.form ? s.nl : s.L;   // valid columns of a row
-                for (int p = p0; p < npieces; p += pstep) {
+                for (int m = 0; m < 4; ++m)
+                    if (32 * q + 8 * m + rsub < s.nl) rok |= 1u << m;
+                const bool colvec = (s.L & 3) == 0;
+                for (int p = h; p < npieces; p += 2) {
                     float v[16];
-                    tmem_ld16(tmem + lane_addr + tcol + 16 * p, v);
-                    if (s.form == 0 && scaled) {
+                    tmem_ld16(tcol + 16 * p, v);
+                    if (scaled) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int k = 16 * p + i;
@@ -879,33 +801,29 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     __syncwarp();
                     float4 y[4];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        y[m] = *reinterpret_cast<const float4*>(Ew + (8 * m + rsub) * kEpiPitch + csub);
-                        if (s.form) { y[m].x *= rsc[m]; y[m].y *= rsc[m]; y[m].z *= rsc[m]; y[m].w *= rsc[m]; }
-                    }
+                    for (int m = 0; m < 4; ++m) y[m] = *reinterpret_cast<const float4*>(Ew + (8 * m + rsub) * kEpiPitch + csub);
                     __syncwarp();   // the buffer is rewritten by the next piece
                     const int c0 = 16 * p + csub;
-                    const unsigned vm = (colvec && c0 + 3 < ncols) ? rok : 0u;   // rows written as 16-byte groups
+                    const unsigned vm = (colvec && c0 + 3 < s.L) ? rok : 0u;   // lines written as 16-byte groups
                     const long long gb = rbase0 + c0;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (vm & (1u << m)) *reinterpret_cast<float4*>(Y + gb + m * rstep) = y[m];
-                    // rows or groups that are not whole 16-byte groups: one element at a time
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if ((rok & (1u << m)) && !(vm & (1u << m))) {
+                    for (int m = 0; m < 4; ++m) {
+                        if (vm & (1u << m)) {
+                            *reinterpret_cast<float4*>(Y + gb + m * rstep) = y[m];
+                        } else if (rok & (1u << m)) {
                             const float yv[4] = {y[m].x, y[m].y, y[m].z, y[m].w};
 #pragma unroll
                             for (int e = 0; e < 4; ++e)
-                                if (c0 + e < ncols) Y[gb + m * rstep + e] = yv[e];
+                                if (c0 + e < s.L) Y[gb + m * rstep + e] = yv[e];
                         }
+                    }
                 }
-                // the accumulator is free for the next tile's MMAs
-                fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(b_aempty + 8 * a);
-                ++a_it;
             }
+            // the accumulator is free for the next tile's MMAs
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_aempty + 8 * a);
+            ++a_it;
         }
     }
 
@@ -926,10 +844,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 // with one set of partial sums per block of
 //   |b - z^{k+1}|^2, |z^{k+1} - z^k|^2, |b|^2, |z^{k+1}|^2, |u^{k+1}|^2
 // (the residuals of the stopping test).  A block covers kAdmmFaces
-// consecutive faces of one job; blocks of a stopped job write zeros.
+// consecutive faces of one job in kAdmmIters rounds of 16 loads per thread;
+// blocks of a stopped job write zeros.
 constexpr int kAdmmThreads = 256;
-constexpr int kAdmmGroups = 4;                                  // float4 groups per thread
-constexpr long long kAdmmFaces = kAdmmThreads * kAdmmGroups * 4;
+constexpr int kAdmmGroups = 4;                                  // float4 groups per thread and round
+constexpr int kAdmmIters = 4;
+constexpr long long kAdmmFaces = (long long)kAdmmThreads * kAdmmGroups * 4 * kAdmmIters;
 
 long long admm_update_blocks(long long nf) { return (nf + kAdmmFaces - 1) / kAdmmFaces; }
 
@@ -943,7 +863,7 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(const Job* __restr
     float tn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (J.active) {
         const long long nf = J.nf;
-        const long long e0 = (blk - prefix[jid]) * kAdmmFaces;
+        const long long e00 = (blk - prefix[jid]) * kAdmmFaces;
         float* __restrict__ z = (float*)J.z;
         float* __restrict__ u = (float*)J.u;
         const float* __restrict__ b = (const float*)J.b;
@@ -953,33 +873,36 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(const Job* __restr
             tn[0] += dbz * dbz; tn[1] += dzz * dzz; tn[2] += bb * bb; tn[3] += zz * zz; tn[4] += un * un;
         };
         if ((nf & 3) == 0) {
-            float4 vb[kAdmmGroups], vz[kAdmmGroups], vu[kAdmmGroups], vn[kAdmmGroups];
-            long long ei[kAdmmGroups];
+            for (int r = 0; r < kAdmmIters; ++r) {
+                const long long e0 = e00 + (long long)r * kAdmmThreads * kAdmmGroups * 4;
+                float4 vb[kAdmmGroups], vz[kAdmmGroups], vu[kAdmmGroups], vn[kAdmmGroups];
+                long long ei[kAdmmGroups];
 #pragma unroll
-            for (int g = 0; g < kAdmmGroups; ++g) {
-                ei[g] = e0 + 4LL * (g * kAdmmThreads + threadIdx.x);
-                if (ei[g] < nf) {
-                    vb[g] = __ldg(reinterpret_cast<const float4*>(b + ei[g]));
-                    vz[g] = *reinterpret_cast<const float4*>(z + ei[g]);
-                    vu[g] = *reinterpret_cast<const float4*>(u + ei[g]);
-                    vn[g] = __ldg(reinterpret_cast<const float4*>(zn + ei[g]));
+                for (int g = 0; g < kAdmmGroups; ++g) {
+                    ei[g] = e0 + 4LL * (g * kAdmmThreads + threadIdx.x);
+                    if (ei[g] < nf) {
+                        vb[g] = __ldg(reinterpret_cast<const float4*>(b + ei[g]));
+                        vz[g] = *reinterpret_cast<const float4*>(z + ei[g]);
+                        vu[g] = *reinterpret_cast<const float4*>(u + ei[g]);
+                        vn[g] = __ldg(reinterpret_cast<const float4*>(zn + ei[g]));
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < kAdmmGroups; ++g) {
+                    if (ei[g] >= nf) continue;
+                    float4 un;
+                    un.x = vu[g].x + vb[g].x - vn[g].x; un.y = vu[g].y + vb[g].y - vn[g].y;
+                    un.z = vu[g].z + vb[g].z - vn[g].z; un.w = vu[g].w + vb[g].w - vn[g].w;
+                    acc(vb[g].x, vz[g].x, vn[g].x, un.x);
+                    acc(vb[g].y, vz[g].y, vn[g].y, un.y);
+                    acc(vb[g].z, vz[g].z, vn[g].z, un.z);
+                    acc(vb[g].w, vz[g].w, vn[g].w, un.w);
+                    *reinterpret_cast<float4*>(z + ei[g]) = vn[g];
+                    *reinterpret_cast<float4*>(u + ei[g]) = un;
                 }
             }
-#pragma unroll
-            for (int g = 0; g < kAdmmGroups; ++g) {
-                if (ei[g] >= nf) continue;
-                float4 un;
-                un.x = vu[g].x + vb[g].x - vn[g].x; un.y = vu[g].y + vb[g].y - vn[g].y;
-                un.z = vu[g].z + vb[g].z - vn[g].z; un.w = vu[g].w + vb[g].w - vn[g].w;
-                acc(vb[g].x, vz[g].x, vn[g].x, un.x);
-                acc(vb[g].y, vz[g].y, vn[g].y, un.y);
-                acc(vb[g].z, vz[g].z, vn[g].z, un.z);
-                acc(vb[g].w, vz[g].w, vn[g].w, un.w);
-                *reinterpret_cast<float4*>(z + ei[g]) = vn[g];
-                *reinterpret_cast<float4*>(u + ei[g]) = un;
-            }
         } else {
-            for (long long e = e0 + threadIdx.x; e < e0 + kAdmmFaces && e < nf; e += kAdmmThreads) {
+            for (long long e = e00 + threadIdx.x; e < e00 + kAdmmFaces && e < nf; e += kAdmmThreads) {
                 const float bb = __ldg(b + e), zo = z[e], uu = u[e], zz = __ldg(zn + e);
                 const float un = uu + bb - zz;
                 acc(bb, zo, zz, un);
@@ -1007,15 +930,15 @@ cudaError_t launch_admm_update(const Job* jobs, int njobs, const long long* pref
 
 cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg) {
     if (A.total_tiles <= 0) return cudaSuccess;
-    if (cfg.smem == 0 || cfg.sd < 2 || cfg.sx < 2 || cfg.nacc < 1) return cudaErrorInvalidValue;
+    if (cfg.smem == 0 || cfg.sd < 2 || cfg.sr < 2 || cfg.st < 2 || cfg.nacc < 1) return cudaErrorInvalidValue;
     const long long nsm = tc_sm_count();
     const unsigned grid = (unsigned)(A.total_tiles < nsm ? A.total_tiles : nsm);
     count_launch();
     switch (A.pass) {
-        case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.part, A.status); break;
-        case 1: k_axis_tc<1><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.part, A.status); break;
-        case 2: k_axis_tc<2><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.part, A.status); break;
-        default: k_axis_tc<3><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.part, A.status); break;
+        case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
+        case 1: k_axis_tc<1><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
+        case 2: k_axis_tc<2><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
+        default: k_axis_tc<3><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
     }
     return cudaGetLastError();
 }
