@@ -201,6 +201,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
         if (!tc_pass_supported(G.F, G.ax1, G.ax2, q)) P->use_tc = 0;
         P->tc_tiles[q] = tc_pass_tiles(G.F, G.ax1, G.ax2, q);
         P->tc_floats[q] = tc_matrix_floats(G.F, G.ax1, G.ax2, q);
+        P->tn_floats[q] = tcn_matrix_floats(G.F, G.ax1, G.ax2, q);
         P->tc_cfg[q] = TcCfg();
         tc_cfg_add(&P->tc_cfg[q], G.F, G.ax1, G.ax2, q);
         if (!tc_cfg_finish(&P->tc_cfg[q])) P->use_tc = 0;
@@ -233,6 +234,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t o_scale = take(sizeof(float) * (size_t)L1 * L2);
     size_t o_tc[4];
     for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
+    size_t o_tn[4];
+    for (int q = 0; q < 4; ++q) o_tn[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tn_floats[q] : 0));
     size_t o_tmap = take(P->use_tc ? tc_map_bytes() : 0);
     size_t o_arr[10];
     for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
@@ -248,6 +251,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) P->d_pref_tc[q] = pref + 12 + 2 * q;
     P->d_pref_admm = pref + 20;
     for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
+    for (int q = 0; q < 4; ++q) P->d_Ctn[q] = (P->use_tc && P->tn_floats[q]) ? (float*)(base + o_tn[q]) : nullptr;
     P->d_scale = (float*)(base + o_scale);
     P->d_tmaps = P->use_tc ? (void*)(base + o_tmap) : nullptr;
     P->d_status = (int*)(base + o_stat);
@@ -285,6 +289,7 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     J.lam1 = P->d_lam1; J.lam2 = P->d_lam2;
     J.part = P->d_part;
     for (int q = 0; q < 4; ++q) J.Ctc[q] = P->d_Ctc[q];
+    for (int q = 0; q < 4; ++q) J.Ctn[q] = P->d_Ctn[q];
     for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
     J.scale = P->d_scale;
     J.active = 1;
@@ -329,6 +334,11 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
             std::vector<float> arr((size_t)P->tc_floats[q], 0.f);
             tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
             SAC_CUDA(cudaMemcpyAsync(P->d_Ctc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
+            if (P->tn_floats[q]) {
+                std::vector<float> tn((size_t)P->tn_floats[q], 0.f);
+                tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], tn.data());
+                SAC_CUDA(cudaMemcpyAsync(P->d_Ctn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
+            }
         }
     }
     SAC_CUDA(cudaMemcpyAsync(P->d_C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));

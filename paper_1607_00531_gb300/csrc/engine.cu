@@ -52,7 +52,7 @@ void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W) {
 // ---------------------------------------------------------------- per-job state block
 struct StateLayout {
     size_t b32, z, u, t1, t2;          // face arrays
-    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4], tmap;
+    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4], tn[4], tmap;
     size_t bytes;
 };
 
@@ -76,6 +76,8 @@ static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
     s.scale = take(4 * (size_t)L1 * L2);
     for (int q = 0; q < 4; ++q)
         s.tc[q] = take(use_tc ? 4 * (size_t)tc_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
+    for (int q = 0; q < 4; ++q)
+        s.tn[q] = take(use_tc ? 4 * (size_t)tcn_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
     s.tmap = take(use_tc ? tc_map_bytes() : 0);
     s.bytes = off;
     return s;
@@ -149,6 +151,7 @@ size_t Engine::table_bytes(const std::vector<EngineJob>& jobs, const sac_params&
     size_t off = 0;
     off += a256(sizeof(Job) * nj);
     off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 4 classes), 8 pass prefixes, ADMM update blocks, spare
+    off += a256(sizeof(long long) * (nj + 1) * 4 * nj);        // tensor-core pass prefixes per geometry group
     off += a256(sizeof(unsigned long long) * (size_t)lines);
     off += a256(sizeof(int) * 16);
     off += a256(sizeof(double) * (size_t)np);
@@ -246,22 +249,50 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         i = k;
     }
     for (int q = 0; q < 4; ++q) {
-        d_pref_tc_[q] = pref + (4 + q) * (nj + 1);
         d_pref_ax_[q] = pref + (8 + q) * (nj + 1);
-        long long* ht = hpref.data() + (4 + q) * (nj + 1);
         long long* ha = hpref.data() + (8 + q) * (nj + 1);
-        ht[0] = ha[0] = 0;
-        tc_cfg_[q] = TcCfg();
+        ha[0] = 0;
         for (size_t i = 0; i < nj; ++i) {
             const Geometry& G = jobs_[i].G;
-            ht[i + 1] = ht[i] + tc_pass_tiles(G.F, G.ax1, G.ax2, q);
             const int axis = (q == 0 || q == 3) ? G.ax1 : G.ax2;
             ha[i + 1] = ha[i] + axis_pass_tiles(G.F, axis);
-            tc_cfg_add(&tc_cfg_[q], G.F, G.ax1, G.ax2, q);
         }
-        if (use_tc_ && !tc_cfg_finish(&tc_cfg_[q])) return SAC_EINVAL;
-        tc_tiles_[q] = ht[nj];
         ax_tiles_[q] = ha[nj];
+    }
+    {
+        // geometry groups of the tensor-core passes: a prefix per pass and
+        // group in which the other groups' jobs have no tiles
+        std::vector<int> gid(nj, -1);
+        std::vector<size_t> rep;
+        for (size_t i = 0; i < nj; ++i) {
+            const Geometry& G = jobs_[i].G;
+            for (size_t r = 0; r < rep.size() && gid[i] < 0; ++r) {
+                const Geometry& H = jobs_[rep[r]].G;
+                if (H.F[0] == G.F[0] && H.F[1] == G.F[1] && H.F[2] == G.F[2] && H.ax1 == G.ax1 && H.ax2 == G.ax2)
+                    gid[i] = (int)r;
+            }
+            if (gid[i] < 0) { gid[i] = (int)rep.size(); rep.push_back(i); }
+        }
+        ngeo_ = (int)rep.size();
+        long long* zp = (long long*)take(sizeof(long long) * (nj + 1) * 4 * ngeo_);
+        std::vector<long long> hz((nj + 1) * 4 * ngeo_, 0);
+        zpref_.assign(4 * ngeo_, nullptr);
+        ztiles_.assign(4 * ngeo_, 0);
+        zcfg_.assign(4 * ngeo_, TcCfg());
+        for (int q = 0; q < 4; ++q)
+            for (int gr = 0; gr < ngeo_; ++gr) {
+                const int z = q * ngeo_ + gr;
+                zpref_[z] = zp + (size_t)z * (nj + 1);
+                long long* h = hz.data() + (size_t)z * (nj + 1);
+                for (size_t i = 0; i < nj; ++i) {
+                    const Geometry& G = jobs_[i].G;
+                    h[i + 1] = h[i] + (gid[i] == gr ? tc_pass_tiles(G.F, G.ax1, G.ax2, q) : 0);
+                    if (gid[i] == gr) tc_cfg_add(&zcfg_[z], G.F, G.ax1, G.ax2, q);
+                }
+                ztiles_[z] = h[nj];
+                if (use_tc_ && !tc_cfg_finish(&zcfg_[z])) return SAC_EINVAL;
+            }
+        ENG_CUDA(cudaMemcpyAsync(zp, hz.data(), hz.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     }
     {
         // ADMM update blocks per job (tensor-core z-step)
@@ -297,6 +328,8 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         J.lam2 = (const double*)(s + L.l2);
         J.scale = (const float*)(s + L.scale);
         for (int q = 0; q < 4; ++q) J.Ctc[q] = use_tc_ ? (const void*)(s + L.tc[q]) : nullptr;
+        for (int q = 0; q < 4; ++q)
+            J.Ctn[q] = (use_tc_ && tcn_matrix_floats(G.F, G.ax1, G.ax2, q)) ? (const void*)(s + L.tn[q]) : nullptr;
         for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
         if (use_tc_) {
             // TMA tensor maps of the X sources of the tensor-core passes
@@ -339,6 +372,12 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
                     std::vector<float> arr((size_t)nfl, 0.f);
                     tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
                     ENG_CUDA(cudaMemcpyAsync(s + L.tc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
+                    const long long ntn = tcn_matrix_floats(G.F, G.ax1, G.ax2, q);
+                    if (ntn) {
+                        std::vector<float> tn((size_t)ntn, 0.f);
+                        tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], tn.data());
+                        ENG_CUDA(cudaMemcpyAsync(s + L.tn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
+                    }
                 }
             }
             count_launch();
@@ -411,9 +450,13 @@ int Engine::enqueue_iteration(int slot) {
         A.status = d_status_;
         A.stream = st_;
         if (use_tc_) {
-            A.prefix = d_pref_tc_[q];
-            A.total_tiles = tc_tiles_[q];
-            ENG_CUDA(launch_axis_pass_tc(A, tc_cfg_[q]));
+            for (int gr = 0; gr < ngeo_; ++gr) {
+                const int z = q * ngeo_ + gr;
+                if (ztiles_[z] == 0) continue;
+                A.prefix = zpref_[z];
+                A.total_tiles = ztiles_[z];
+                ENG_CUDA(launch_axis_pass_tc(A, zcfg_[z]));
+            }
             // z^{k+1} is in t2: ADMM update and residual sums, element-wise
             if (q == 3) ENG_CUDA(launch_admm_update(d_jobs_, nj, d_pref_admm_, admm_blocks_, d_part_, st_));
         } else {

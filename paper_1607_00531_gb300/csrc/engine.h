@@ -79,12 +79,17 @@ private:
     };
     std::vector<Cls> cls_;
     Job* d_jobs_ = nullptr;
-    long long* d_pref_tc_[4] = {nullptr, nullptr, nullptr, nullptr};
+    // tensor-core passes: one launch per pass and geometry group (jobs with
+    // the same face dims and axes), so that a job is processed by the same
+    // kernel alone and in any batch; [pass * ngeo_ + group]
+    int ngeo_ = 0;
+    std::vector<long long*> zpref_;
+    std::vector<long long> ztiles_;
+    std::vector<TcCfg> zcfg_;
     long long* d_pref_ax_[4] = {nullptr, nullptr, nullptr, nullptr};
-    long long tc_tiles_[4] = {0, 0, 0, 0}, ax_tiles_[4] = {0, 0, 0, 0};
+    long long ax_tiles_[4] = {0, 0, 0, 0};
     long long* d_pref_admm_ = nullptr;   // ADMM update blocks per job (tensor-core z-step)
     long long admm_blocks_ = 0;
-    TcCfg tc_cfg_[4];
     unsigned long long* d_rlist_ = nullptr;
     int* d_rcount_ = nullptr;      // one counter per class
     int* d_status_ = nullptr;

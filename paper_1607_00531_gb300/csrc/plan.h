@@ -40,6 +40,7 @@ struct Plan {
     long long tc_tiles[4];
     long long admm_blocks;     // ADMM update blocks (tensor-core z-step)
     long long tc_floats[4];
+    long long tn_floats[4];    // tensor-memory DCT operands (axes of at most 128 faces)
     TcCfg tc_cfg[4];           // ring / accumulator layout of each tensor-core pass
     int rcap;
     // device pointers inside ws
@@ -50,6 +51,7 @@ struct Plan {
     long long* d_pref_tc[4];
     long long* d_pref_admm;   // blocks of the ADMM update after the tensor-core passes
     float* d_Ctc[4];
+    float* d_Ctn[4];
     void* d_tmaps;            // tensor maps of the tensor-core passes
     float* d_scale;
     int* d_status;

@@ -43,6 +43,7 @@ struct Job {
     const double* lam1;  // eigenvalues 4/h^2 sin^2(pi k / (2 m)) along ax1
     const double* lam2;
     const void* Ctc[4];  // tensor-core z-step: split TF32 DCT matrices per pass
+    const void* Ctn[4];  // the same as tensor-memory operands (axes of at most 128 faces)
     const float* scale;  // [k1][k2] = rho / (alpha (lam1[k1] + lam2[k2]) + rho), FP32
     double* part;      // per-block partial sums of this job
     int active;        // 0: tiles of this job return at once

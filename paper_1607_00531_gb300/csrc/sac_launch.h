@@ -118,6 +118,9 @@ struct TcCfg {
     uint32_t epi_off = 0;            // shared-memory offset of the epilogue transpose buffers
     int resident = 0;                // 1: the DCT chunks stay in their slots for all tiles
     int nch = 0, geom[3] = {0, 0, 0};   // shared geometry of the launch's jobs (-1: mixed)
+    int lmax = 0;                    // longest contracted axis of the launch
+    int caseB = 0;                   // the contracted axis is the fastest one (first job)
+    int tn = 0;                      // 1: the lines-in-N kernel (zstep_tcn.cu), sr = its ring stages
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
 constexpr int kTcMaps = 8;           // TMA tensor maps per job: [pass][source]
@@ -140,6 +143,13 @@ long long tc_pass_tiles(const int F[3], int ax1, int ax2, int pass);
 bool tc_pass_supported(const int F[3], int ax1, int ax2, int pass);
 long long tc_matrix_floats(const int F[3], int ax1, int ax2, int pass);
 void tc_arrange_matrix(const int F[3], int ax1, int ax2, int pass, const double* M, float* out);
+// lines-in-N variant (contracted axis of at most 128 faces): the DCT as a
+// tensor-memory A operand [hi: 128 x Kp][lo: 128 x Kp]
+bool tcn_pass_usable(const int F[3], int ax1, int ax2, int pass);
+long long tcn_matrix_floats(const int F[3], int ax1, int ax2, int pass);
+void tcn_arrange_matrix(const int F[3], int ax1, int ax2, int pass, const double* M, float* out);
+cudaError_t launch_axis_pass_tcn(const AxisLaunch& A, const TcCfg& cfg, unsigned grid);
+cudaError_t prepare_axis_tcn();
 // tiles of one pass for a job with face dims F, non-PE axes ax1/ax2
 long long axis_pass_tiles(const int F[3], int axis);
 

@@ -1,0 +1,198 @@
+// tc_ptx.cuh -- inline-PTX building blocks of the tensor-core z-step kernels
+// (5th-generation tensor cores: tcgen05.mma / ld / st, tensor memory, TMA and
+// mbarrier-tracked pipelines), shared by zstep_tc.cu and zstep_tcn.cu.
+#pragma once
+
+#include <stdint.h>
+
+#include "sac_dev.cuh"
+
+namespace sac {
+namespace tcx {
+
+constexpr uint32_t kSuspendNs = 20000;             // longest suspension of one barrier test
+constexpr long long kWaitTests = 50000;            // barrier tests before a wait gives up (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (all >> 4), version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor: D FP32, A and B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) += A (TMEM, lane = row, one column per K value) x B (shared memory)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// arrive on mbar once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
+}
+// Test for the completion of the phase of the given parity; a thread whose
+// phase is not complete is suspended (at most kSuspendNs) instead of
+// spinning, which keeps the issue slots free for the warps that work.
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(a), "r"(parity), "n"(kSuspendNs) : "memory");
+    return ok != 0;
+}
+// Bounded wait (at most kWaitTests tests, about a second) for the phase of
+// the given parity.  Gives up early when the CTA's abort flag is set; raises
+// the flag when the limit is reached.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t a, uint32_t parity, volatile int* abort) {
+    for (long long i = 0; i < kWaitTests; ++i) {
+        if (mbar_test(a, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+// bounded wait that ignores the abort flag (draining before exit)
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
+    for (long long i = 0; i < kWaitTests; ++i)
+        if (mbar_test(a, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+// TMA (bulk) copy global -> shared, completing `bytes` transactions on mbar
+__device__ __forceinline__ void tma_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+// TMA tensor tile copies global -> shared (tensor map in global memory)
+__device__ __forceinline__ void tma_tile2d(uint32_t dst, const void* map, int x, int y, uint32_t mbar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tma_tile3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t mbar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(slot), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns (one register per column)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// the inverse: 32 lanes x 16 consecutive columns from registers (no wait)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :: "r"(taddr),
+           "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+           "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+           "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+           "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Position in a ring of n slots: the slot and the parity of its current use
+// (kept incrementally: a modulo of a 64-bit counter by a run-time n is a long
+// software division on the single-thread producer and MMA roles).  A consumer
+// waits for phase `phase`, a producer for the release of the previous use,
+// phase ^ 1 (immediately true on the first round).
+struct RingPos {
+    int slot = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void next(int n) {
+        if (++slot == n) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// fence: generic-proxy shared-memory writes before the tensor core reads them
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// byte offset of element (row, kk) of a K-major, non-swizzled operand chunk
+// of 32 K values: core matrices of 8 rows x 16 bytes, 128 contiguous bytes
+// each, the 8 of a row group contiguous, row groups 1024 bytes apart
+__device__ __forceinline__ uint32_t core_off(int row, int kk) {
+    return (uint32_t)((row >> 3) * 1024 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4);
+}
+
+}  // namespace tcx
+
+// Per-pass geometry of a job, computed identically by host and device.
+struct TcPass {
+    int axis, L;
+    long long pre, post, N;
+    int caseB;      // post == 1 (the contracted axis is the fastest one)
+    int Np;         // L padded to 16
+    int nch;        // K chunks of 32
+};
+
+__host__ __device__ inline TcPass tc_pass_geom(const int F[3], int ax1, int ax2, int pass) {
+    TcPass g;
+    g.axis = (pass == 0 || pass == 3) ? ax1 : ax2;
+    g.L = F[g.axis];
+    g.pre = 1; g.post = 1;
+    for (int a = 0; a < g.axis; ++a) g.pre *= F[a];
+    for (int a = g.axis + 1; a < 3; ++a) g.post *= F[a];
+    g.N = g.pre * g.post;
+    g.caseB = (g.post == 1);
+    g.Np = ((g.L + 15) / 16) * 16;
+    g.nch = (g.L + 31) / 32;
+    return g;
+}
+
+}  // namespace sac

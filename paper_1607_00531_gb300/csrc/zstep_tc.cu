@@ -62,6 +62,7 @@
 
 #include "sac_dev.cuh"
 #include "sac_launch.h"
+#include "tc_ptx.cuh"
 
 namespace sac {
 
@@ -76,169 +77,15 @@ constexpr int kThreads = (kXWarp + 1) * 32;
 constexpr int kBK = 32;                            // K chunk
 constexpr int kTileLines = 128;                    // lines per tile (MMA M)
 constexpr uint32_t kRawBytes = kTileLines * kBK * 4;   // one source's raw chunk (16 KB)
-constexpr uint32_t kSuspendNs = 20000;             // longest suspension of one barrier test
-constexpr long long kWaitTests = 50000;            // barrier tests before a wait gives up (~1 s)
 constexpr int kMaxDStages = 4, kMaxRStages = 6, kMaxTStages = 4;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kXCols = 2 * kBK;               // TMEM columns of an X chunk slot
 constexpr int kEpiPitch = 20;                      // floats per row of an epilogue transpose buffer
 constexpr uint32_t kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// tcgen05 shared-memory matrix descriptor: start address, leading and stride
-// byte offsets (all >> 4), version 1, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// instruction descriptor: D FP32, A and B TF32, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// D (TMEM) += A (TMEM, lane = row, one column per K value) x B (shared memory)
-__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
-        :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc) : "memory");
-}
-// arrive on mbar once every MMA issued so far by this thread has completed
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(mbar) : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
-}
-// Test for the completion of the phase of the given parity; a thread whose
-// phase is not complete is suspended (at most kSuspendNs) instead of
-// spinning, which keeps the issue slots free for the warps that work.
-__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok) : "r"(a), "r"(parity), "n"(kSuspendNs) : "memory");
-    return ok != 0;
-}
-// Bounded wait (at most kWaitTests tests, about a second) for the phase of
-// the given parity.  Gives up early when the CTA's abort flag is set; raises
-// the flag when the limit is reached.
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t a, uint32_t parity, volatile int* abort) {
-    for (long long i = 0; i < kWaitTests; ++i) {
-        if (mbar_test(a, parity)) return true;
-        if (*abort) return false;
-    }
-    *abort = 1;
-    return false;
-}
-// bounded wait that ignores the abort flag (draining before exit)
-__device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
-    for (long long i = 0; i < kWaitTests; ++i)
-        if (mbar_test(a, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
-}
-// TMA (bulk) copy global -> shared, completing `bytes` transactions on mbar
-__device__ __forceinline__ void tma_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-// TMA tensor tile copies global -> shared (tensor map in global memory)
-__device__ __forceinline__ void tma_tile2d(uint32_t dst, const void* map, int x, int y, uint32_t mbar) {
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar) : "memory");
-}
-__device__ __forceinline__ void tma_tile3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t mbar) {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(slot), "r"(ncols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
-}
-
-// 32 lanes x 16 consecutive 32-bit columns (one register per column)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-// the inverse: 32 lanes x 16 consecutive columns from registers (no wait)
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
-        :: "r"(taddr),
-           "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-           "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-           "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-           "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-        : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+using namespace tcx;
 
 }  // namespace tc
-
-// Per-pass geometry of a job, computed identically by host and device.
-struct TcPass {
-    int axis, L;
-    long long pre, post, N;
-    int caseB;      // post == 1 (form 0)
-    int Np;         // L padded to 16 (MMA N)
-    int nch;        // K chunks of 32
-};
-
-__host__ __device__ inline TcPass tc_pass_geom(const int F[3], int ax1, int ax2, int pass) {
-    TcPass g;
-    g.axis = (pass == 0 || pass == 3) ? ax1 : ax2;
-    g.L = F[g.axis];
-    g.pre = 1; g.post = 1;
-    for (int a = 0; a < g.axis; ++a) g.pre *= F[a];
-    for (int a = g.axis + 1; a < 3; ++a) g.post *= F[a];
-    g.N = g.pre * g.post;
-    g.caseB = (g.post == 1);
-    g.Np = ((g.L + 15) / 16) * 16;
-    g.nch = (g.L + tc::kBK - 1) / tc::kBK;
-    return g;
-}
 
 // tiles of a pass (form 1: per pr, ceil(post / 128))
 __host__ __device__ inline long long tc_tiles_of(const TcPass& g) {
@@ -289,10 +136,12 @@ void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass) {
     if (d > c->dslot) c->dslot = d;
     if (r > c->rslot) c->rslot = r;
     if (g.Np > c->acc_need) c->acc_need = g.Np;
+    if (g.L > c->lmax) c->lmax = g.L;
     // one DCT matrix for all tiles when every job has the same face dims and axes
     const int key[3] = {F[0] * 4 + ax1, F[1] * 4 + ax2, F[2]};
     if (c->nch == 0) {
         c->nch = g.nch;
+        c->caseB = g.caseB;
         for (int i = 0; i < 3; ++i) c->geom[i] = key[i];
     } else if (c->geom[0] != key[0] || c->geom[1] != key[1] || c->geom[2] != key[2]) {
         c->geom[0] = -1;
@@ -301,6 +150,22 @@ void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass) {
 
 bool tc_cfg_finish(TcCfg* c) {
     if (c->dslot == 0) { c->smem = 0; return true; }
+    if (c->geom[0] >= 0 && c->lmax <= 128) {
+        // one geometry, axis of at most 128 faces: the lines-in-N kernel with
+        // the DCT resident in tensor memory, a ring of X chunks and, when the
+        // axis is contiguous with rows of 16-byte multiples, two staging
+        // buffers of an output tile (128 lines x L)
+        c->tn = 1;
+        const size_t slot = 2 * 128 * tc::kBK * 4;
+        const size_t stage = (c->caseB && (c->lmax & 3) == 0) ? (size_t)128 * c->lmax * 4 : 0;
+        const size_t avail = 226 * 1024 - 2 * stage;
+        c->sr = (int)(avail / slot);
+        if (c->sr > 6) c->sr = 6;
+        if (c->sr < 2) return false;
+        c->epi_off = (uint32_t)(c->sr * slot);
+        c->smem = c->sr * slot + 2 * stage;
+        return true;
+    }
     const size_t budget = 226 * 1024 - tc::kEpiBytes;   // rings; 1 KB of static shared memory
     c->sd = 2;
     c->sr = 2;
@@ -533,7 +398,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const int q = warp & 3, kh = warp >> 2;
         const int lr = 32 * q + lane;              // line of the tile (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-        long long r_it = 0, x_it = 0;
+        RingPos rr, tr;
         bool run = true;
         for (long long t = t0; t < total && run; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
@@ -546,8 +411,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const long long gbase = s.form ? s.pr * s.L * s.post + s.po0 + lr : (s.line0 + lr) * s.L;
             const long long js = s.form ? s.post : 1;
             for (int c = 0; c < s.nch; ++c) {
-                const int rs = (int)(r_it % cfg.sr);
-                bool ok = mbar_wait_ab(b_rfull + 8 * rs, (uint32_t)((r_it / cfg.sr) & 1), abort);
+                const int rs = rr.slot;
+                bool ok = mbar_wait_ab(b_rfull + 8 * rs, rr.phase, abort);
                 if (!__all_sync(kFull, ok)) { run = false; break; }
                 float v[16];
                 if (s.tma) {
@@ -589,9 +454,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 // the raw slot may be refilled once every converter warp has its values
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_rempty + 8 * rs);
-                ++r_it;
-                const int ts = (int)(x_it % cfg.st);
-                ok = mbar_wait_ab(b_tempty + 8 * ts, (uint32_t)(((x_it / cfg.st) & 1) ^ 1), abort);
+                rr.next(cfg.sr);
+                const int ts = tr.slot;
+                ok = mbar_wait_ab(b_tempty + 8 * ts, tr.phase ^ 1u, abort);
                 if (!__all_sync(kFull, ok)) { run = false; break; }
                 fence_after();
                 float hi[16], lo[16];
@@ -607,21 +472,22 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_tfull + 8 * ts);
-                ++x_it;
+                tr.next(cfg.st);
             }
         }
     } else if (warp == kXWarp) {
         // ------------------------------------------------ raw X chunks (TMA tensor copies)
         if (lane == 0) {
             long long r_it = 0;
+            RingPos rr;
             for (long long t = t0; t < total && !*abort; t += dt) {
                 const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
                 if (!s.active) continue;
                 const char* maps = (const char*)s.J->tmaps + (size_t)2 * PASS * 128;
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
-                    const int rs = (int)(r_it % cfg.sr);
-                    if (!mbar_wait_ab(b_rempty + 8 * rs, (uint32_t)(((r_it / cfg.sr) & 1) ^ 1), abort)) { ok = false; break; }
+                    const int rs = rr.slot;
+                    if (!mbar_wait_ab(b_rempty + 8 * rs, rr.phase ^ 1u, abort)) { ok = false; break; }
                     const uint32_t dst = s_raw + (uint32_t)rs * cfg.rslot;
                     if (s.tma) {
                         mbar_expect_tx(b_rfull + 8 * rs, NSRC * kRawBytes);
@@ -636,6 +502,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         mbar_arrive(b_rfull + 8 * rs);   // the converters load this chunk themselves
                     }
                     ++r_it;
+                    rr.next(cfg.sr);
                 }
                 if (!ok) break;
             }
@@ -647,6 +514,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         // ------------------------------------------------ DCT chunks (bulk copies)
         if (lane == 0) {
             long long d_it = 0;
+            RingPos dr;
             for (long long t = t0; t < total && !*abort; t += dt) {
                 const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
                 if (!s.active) continue;
@@ -663,11 +531,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     break;
                 }
                 for (int c = 0; c < s.nch; ++c) {
-                    const int ds = (int)(d_it % cfg.sd);
-                    if (!mbar_wait_ab(b_dempty + 8 * ds, (uint32_t)(((d_it / cfg.sd) & 1) ^ 1), abort)) { ok = false; break; }
+                    const int ds = dr.slot;
+                    if (!mbar_wait_ab(b_dempty + 8 * ds, dr.phase ^ 1u, abort)) { ok = false; break; }
                     mbar_expect_tx(b_dfull + 8 * ds, db);
                     tma_bulk_g2s(s_base + (uint32_t)ds * cfg.dslot, Mpre + (long long)c * (db / 4), db, b_dfull + 8 * ds);
                     ++d_it;
+                    dr.next(cfg.sd);
                 }
                 if (!ok) break;
             }
@@ -678,21 +547,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
-            long long d_it = 0, x_it = 0, a_it = 0;
+            RingPos dr, tr, ar;
             for (long long t = t0; t < total && !*abort; t += dt) {
                 const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
                 if (!s.active) continue;
-                const int a = (int)(a_it % cfg.nacc);
-                if (!mbar_wait_ab(b_aempty + 8 * a, (uint32_t)(((a_it / cfg.nacc) & 1) ^ 1), abort)) break;
+                const int a = ar.slot;
+                if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
                 fence_after();
                 const uint32_t dacc = tmem + (uint32_t)a * cfg.acc_cols;
                 const uint32_t idesc = idesc_tf32(kTileLines, s.Np);
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
-                    const int ds = cfg.resident ? c : (int)(d_it % cfg.sd), ts = (int)(x_it % cfg.st);
-                    const uint32_t dpar = cfg.resident ? 0u : (uint32_t)((d_it / cfg.sd) & 1);
+                    const int ds = cfg.resident ? c : dr.slot, ts = tr.slot;
+                    const uint32_t dpar = cfg.resident ? 0u : dr.phase;
                     if (!mbar_wait_ab(b_dfull + 8 * ds, dpar, abort) ||
-                        !mbar_wait_ab(b_tfull + 8 * ts, (uint32_t)((x_it / cfg.st) & 1), abort)) {
+                        !mbar_wait_ab(b_tfull + 8 * ts, tr.phase, abort)) {
                         ok = false;
                         break;
                     }
@@ -716,12 +585,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xl + 8 * ks, ch + 16u * ks, idesc, 1u);
                     if (!cfg.resident) mma_commit(b_dempty + 8 * ds);
                     mma_commit(b_tempty + 8 * ts);
-                    ++d_it;
-                    ++x_it;
+                    dr.next(cfg.sd);
+                    tr.next(cfg.st);
                 }
                 if (!ok) break;
                 mma_commit(b_afull + 8 * a);
-                ++a_it;
+                ar.next(cfg.nacc);
             }
             // every MMA of this thread completes before TMEM is freed
             mma_commit(b_drain);
@@ -734,13 +603,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const int h = ew >> 2;              // half: even or odd column pieces
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
         const int lr = 32 * q + lane;       // line of the tile
-        long long a_it = 0;
+        RingPos ar;
         for (long long t = t0; t < total && !*abort; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
             if (!s.active) continue;
             const Job& J = *s.J;
-            const int a = (int)(a_it % cfg.nacc);
-            const bool ok = mbar_wait_ab(b_afull + 8 * a, (uint32_t)((a_it / cfg.nacc) & 1), abort);
+            const int a = ar.slot;
+            const bool ok = mbar_wait_ab(b_afull + 8 * a, ar.phase, abort);
             if (!__all_sync(kFull, ok)) break;
             fence_after();
             float* __restrict__ Y = (PASS == 0 || PASS == 2) ? (float*)J.t1 : (float*)J.t2;
@@ -823,7 +692,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(b_aempty + 8 * a);
-            ++a_it;
+            ar.next(cfg.nacc);
         }
     }
 
@@ -930,9 +799,10 @@ cudaError_t launch_admm_update(const Job* jobs, int njobs, const long long* pref
 
 cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg) {
     if (A.total_tiles <= 0) return cudaSuccess;
-    if (cfg.smem == 0 || cfg.sd < 2 || cfg.sr < 2 || cfg.st < 2 || cfg.nacc < 1) return cudaErrorInvalidValue;
     const long long nsm = tc_sm_count();
     const unsigned grid = (unsigned)(A.total_tiles < nsm ? A.total_tiles : nsm);
+    if (cfg.tn) return cfg.sr >= 2 ? launch_axis_pass_tcn(A, cfg, grid) : cudaErrorInvalidValue;
+    if (cfg.smem == 0 || cfg.sd < 2 || cfg.sr < 2 || cfg.st < 2 || cfg.nacc < 1) return cudaErrorInvalidValue;
     count_launch();
     switch (A.pass) {
         case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
@@ -945,6 +815,7 @@ cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg) {
 
 cudaError_t prepare_axis_tc() {
     cudaError_t e;
+    if ((e = prepare_axis_tcn()) != cudaSuccess) return e;
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<0>)) != cudaSuccess) return e;
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<1>)) != cudaSuccess) return e;
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<2>)) != cudaSuccess) return e;
