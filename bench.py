@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tts-cap", type=int, default=400)
+    ap.add_argument("--profile-direct", type=int, default=0, metavar="K",
+                    help="only run K mixed ADMM iterations through sac_admm_solve (no CUDA graphs, no "
+                         "timing line): the launch sequence for kernel profilers")
     ap.add_argument("--only-mixed", action="store_true",
                     help="only the warm-up and the timed mixed-precision iterations (profiling runs)")
     return ap.parse_args()
@@ -179,20 +182,42 @@ def roofline(prof, w, g, nf, sac):
                    "frac_tensor_tf32": ach_f / tf32_peak}
             ent["bound"] = "hbm" if ent["frac_hbm"] >= ent["frac_tensor_tf32"] else "tensor"
         kernels[k] = ent
+    # kernels behind each phase: axes of at most 128 faces run the lines-in-N
+    # tensor-core kernel, longer ones the lines-in-M kernel; the last phase
+    # also holds the element-wise ADMM update and the stopping test
+    def zk(L, q):
+        return (f"k_axis_tcn<{q}>" if L <= 128 else f"k_axis_tc<{q}>")
+    names = {"bstep": "k_bstep<float,float,9>", "bstep_refine": "k_bstep_list<double,float,9>",
+             "zpass0": zk(L1, 0), "zpass1": zk(L2, 1), "zpass2": zk(L2, 2),
+             "zpass3": zk(L1, 3) + " + k_admm_update + k_admm_check"}
+    for k in kernels:
+        kernels[k]["kernel"] = names.get(k, k)
     dom = max(nphase, key=lambda k: nphase[k][0])
     e = kernels[dom]
+    traffic = ncu_traffic().get(names[dom].split(" ")[0])
     if e.get("bound") == "tensor":
-        roof = {"kernel": f"k_axis_tc {dom}", "bound": "tensor", "achieved": e["achieved_tflops"],
-                "peak": tf32_peak, "unit": "TFLOP/s", "frac": e["frac_tensor_tf32"], "traffic": None,
+        roof = {"kernel": names[dom], "bound": "tensor", "achieved": e["achieved_tflops"],
+                "peak": tf32_peak, "unit": "TFLOP/s", "frac": e["frac_tensor_tf32"], "traffic": traffic,
                 "algorithmic_flops_per_launch": e["flops"],
                 "peak_source": f"{src}: bf16 {bf16:.1f} TFLOP/s x nominal TF32/BF16 1.1/2.25 (split TF32 runs 3 MMAs per product)"}
     else:
-        name = "k_bstep<float,float,9>" if dom == "bstep" else f"k_axis_tc {dom}"
-        roof = {"kernel": name, "bound": "hbm", "achieved": e["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": e["frac_hbm"], "traffic": None, "algorithmic_bytes_per_launch": e["bytes"],
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": e["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": e["frac_hbm"], "traffic": traffic, "algorithmic_bytes_per_launch": e["bytes"],
                 "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
     roof["fp32_simt_peak_tflops"] = fp32_peak
     return roof, kernels
+
+
+def ncu_traffic():
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of kernels from one ncu capture each, as recorded in
+    profiles/ncu_traffic.json (absent: null traffic)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        d = json.load(fh)
+    return {k: v.get("bytes_per_launch") for k, v in d.get("kernels", {}).items()}
 
 
 def oracle_cpu_baseline(d, w, iters=1, nthreads=0):
@@ -274,6 +299,16 @@ def main():
         return sac.Batch([g], p, [I1x], [I2x], [bb]), bb
 
     stream = torch.cuda.current_stream()
+
+    if args.profile_direct > 0:
+        pm = sac.params(alpha=w.alpha, rho=w.rho, prec="mixed", max_iter=args.profile_direct, eps_abs=0.0,
+                        eps_rel=0.0, check_every=args.profile_direct, near_bound=1e-3)
+        b0 = torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
+        r = sac.admm_solve(g, pm, I1, I2, b0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_direct": args.profile_direct, "workload": args.workload, "iters": r["iters"],
+                          "r_pri": r["r_pri"]}))
+        return
 
     def barrier():
         if dist:

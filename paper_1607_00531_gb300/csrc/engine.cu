@@ -105,9 +105,12 @@ __global__ void k_admm_check(Job* __restrict__ jobs, int njobs, const long long*
     if (threadIdx.x == 0) {
         double* st = stats + (size_t)j * 8;
         const int it = (int)st[4] + 1;
-        const double rhd = J.rho * J.hd, sqn = sqrt((double)J.nf);
-        const double rp = sqrt(acc[0]), rd = rhd * sqrt(acc[1]);
-        const double nb = sqrt(acc[2]), nz = sqrt(acc[3]), nu = sqrt(acc[4]);
+        // square roots in FP32 (a stopping test; FP64 square roots are long
+        // dependent chains on the FP64 unit of this GPU)
+        const double rhd = J.rho * J.hd, sqn = (double)sqrtf((float)J.nf);
+        const double rp = (double)sqrtf((float)acc[0]), rd = rhd * (double)sqrtf((float)acc[1]);
+        const double nb = (double)sqrtf((float)acc[2]), nz = (double)sqrtf((float)acc[3]),
+                     nu = (double)sqrtf((float)acc[4]);
         const double ep = sqn * eps_abs + eps_rel * fmax(nb, nz);
         const double ed = sqn * eps_abs + eps_rel * rhd * nu;
         const bool conv = (rp <= ep) && (rd <= ed);
