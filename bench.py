@@ -187,7 +187,15 @@ def roofline(prof, w, g, nf, sac):
     # also holds the element-wise ADMM update and the stopping test
     def zk(L, q):
         return (f"k_axis_tcn<{q}>" if L <= 128 else f"k_axis_tc<{q}>")
-    names = {"bstep": "k_bstep<float,float,9>", "bstep_refine": "k_bstep_list<double,float,9>",
+    # b-step: strided PE lines of at most 272 faces take the segment kernel
+    # (9 faces per segment up to 144 faces, else 17), others one warp per line
+    nfl = w.m[w.pe] + 1
+    kpl = next(k for k in (3, 5, 9, 15) if (nfl + 31) // 32 <= k)
+    if w.pe < len(w.m) - 1 and nfl <= 272:
+        bname = f"k_bstep_seg<{9 if nfl <= 144 else 17}>"
+    else:
+        bname = f"k_bstep<float,float,{kpl}>"
+    names = {"bstep": bname, "bstep_refine": f"k_bstep_list<double,float,{kpl}>",
              "zpass0": zk(L1, 0), "zpass1": zk(L2, 1), "zpass2": zk(L2, 2),
              "zpass3": zk(L1, 3) + " + k_admm_update + k_admm_check"}
     for k in kernels:

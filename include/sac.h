@@ -100,7 +100,10 @@ typedef struct {
                             where the grid allows (else SIMT), 1 SIMT FP32 */
     int autotune;        /* batched runs: 1 = pick the b-step tile width on the
                             first live iterations (results do not depend on it) */
-    int reserved[1];
+    int bstep_kernel;    /* SAC_MIXED b-step with n_sqp = 1: 0 one thread per
+                            (line, segment of 9 or 17 faces) where the PE lines
+                            are strided and have at most 272 faces, else one
+                            warp per line; 1 always one warp per line */
 } sac_params;
 
 void sac_params_default(sac_params* p);

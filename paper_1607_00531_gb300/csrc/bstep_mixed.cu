@@ -10,7 +10,10 @@ cudaError_t prepare_bstep_mixed() { return prepare_bstep_t<double, float>(); }
 // list (mode 1); prec 2: FP64 compute on FP32 storage (both kernels)
 cudaError_t launch_bstep(int prec, const LineLaunch& L) {
     if (prec == 0) return launch_bstep_f64(L);
-    if (prec == 1) return L.mode == 0 ? launch_bstep_f32(L) : launch_bstep_mixed(L);
+    if (prec == 1) {
+        if (L.mode == 1) return launch_bstep_mixed(L);
+        return L.seg_S > 0 ? launch_bstep_seg(L) : launch_bstep_f32(L);
+    }
     return launch_bstep_mixed(L);
 }
 }  // namespace sac

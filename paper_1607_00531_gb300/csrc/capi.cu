@@ -27,7 +27,7 @@ int prepare_kernels() {
     if (g_prep_device == dev) return SAC_OK;
     if (prepare_bstep_f64() != cudaSuccess || prepare_bstep_f32() != cudaSuccess ||
         prepare_bstep_mixed() != cudaSuccess || prepare_line_eval() != cudaSuccess ||
-        prepare_axis_tc() != cudaSuccess) {
+        prepare_axis_tc() != cudaSuccess || prepare_bstep_seg() != cudaSuccess) {
         cudaGetLastError();
         return SAC_ECUDA;
     }
@@ -151,6 +151,7 @@ int check_params(const sac_params* p) {
     if (p->prec != SAC_F64 && p->prec != SAC_MIXED) return SAC_EINVAL;
     if (!(p->near_bound >= 0)) return SAC_EINVAL;
     if (p->zstep_kernel < 0 || p->zstep_kernel > 1) return SAC_EINVAL;
+    if (p->bstep_kernel < 0 || p->bstep_kernel > 1) return SAC_EINVAL;
     return SAC_OK;
 }
 
@@ -193,6 +194,9 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->W = W;
     P->RLf = smem_row(G.mpe + 1, W, 8);
     P->line_tiles = line_tiles(G.n_outer, G.n_inner, W);
+    P->seg_S = seg_faces(G.mpe, G.n_inner, p->n_sqp, p->prec == SAC_MIXED, p->bstep_kernel);
+    P->seg_G = seg_warps(G.mpe, P->seg_S);
+    P->seg_tiles = seg_tiles((long long)G.n_outer * G.n_inner);
     const int axes[4] = {G.ax1, G.ax2, G.ax2, G.ax1};
     for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
     P->elem_blocks = (G.nf + 255) / 256;
@@ -220,7 +224,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     size_t o_job = take(sizeof(Job));
-    size_t o_pref = take(sizeof(long long) * 2 * 11);
+    size_t o_pref = take(sizeof(long long) * 2 * 12);
     size_t o_stat = take(256);
     size_t o_out = take(sizeof(double) * 64);
     size_t o_rlist = take(sizeof(unsigned long long) * (size_t)P->rcap);
@@ -250,6 +254,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->d_pref_elem = pref + 10;
     for (int q = 0; q < 4; ++q) P->d_pref_tc[q] = pref + 12 + 2 * q;
     P->d_pref_admm = pref + 20;
+    P->d_pref_seg = pref + 22;
     for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
     for (int q = 0; q < 4; ++q) P->d_Ctn[q] = (P->use_tc && P->tn_floats[q]) ? (float*)(base + o_tn[q]) : nullptr;
     P->d_scale = (float*)(base + o_scale);
@@ -301,9 +306,9 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                                   (const float*)t2, maps.data());
         SAC_CUDA(cudaMemcpyAsync(P->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
     }
-    long long pref[22] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
+    long long pref[24] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
                           0, P->pass_tiles[3], 0, P->elem_blocks, 0, P->tc_tiles[0], 0, P->tc_tiles[1],
-                          0, P->tc_tiles[2], 0, P->tc_tiles[3], 0, P->admm_blocks};
+                          0, P->tc_tiles[2], 0, P->tc_tiles[3], 0, P->admm_blocks, 0, P->seg_tiles};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -499,6 +504,13 @@ static int bstep_dev(Plan& P, const sac_params* p, cudaStream_t st) {
     const bool mixed = (P.prec == SAC_MIXED);
     SAC_CUDA(cudaMemsetAsync(P.d_rcount, 0, sizeof(int), st));
     LineLaunch L = plan_line_launch(&P, p->n_sqp, mixed ? p->near_bound : 0.0, st);
+    if (P.seg_S > 0 && p->n_sqp == 1) {
+        L.seg_S = P.seg_S;
+        L.seg_G = P.seg_G;
+        L.seg_m = P.G.mpe;
+        L.prefix = P.d_pref_seg;
+        L.total_tiles = P.seg_tiles;
+    }
     {
         PhaseScope ps(0, st);
         SAC_CUDA(launch_bstep(mixed ? 1 : 0, L));
@@ -540,6 +552,7 @@ void sac_params_default(sac_params* p) {
     p->near_bound = 1e-3;
     p->check_every = 1;
     p->zstep_kernel = 0;
+    p->bstep_kernel = 0;
 }
 
 int sac_version(void) { return SAC_VERSION; }

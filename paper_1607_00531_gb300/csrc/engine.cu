@@ -179,10 +179,16 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     if (!ws || ((uintptr_t)ws & 255)) return SAC_EINVAL;
     if (ws_bytes < table_bytes(in, p)) return SAC_ENOMEM;
     const int prec = p.prec;
-    // group by K class, stable in the caller's order
+    // group by b-step class (faces per lane, segment kernel), stable in the
+    // caller's order
+    const bool mixed_p = (prec == SAC_MIXED);
+    auto seg_of = [&](const EngineJob& j) {
+        return seg_faces(j.G.mpe, j.G.n_inner, p.n_sqp, mixed_p, p.bstep_kernel);
+    };
+    auto cls_key = [&](const EngineJob& j) { return j.K * 64 + seg_of(j); };
     order_.resize(in.size());
     for (size_t i = 0; i < in.size(); ++i) order_[i] = (int)i;
-    std::stable_sort(order_.begin(), order_.end(), [&](int a, int b) { return in[a].K < in[b].K; });
+    std::stable_sort(order_.begin(), order_.end(), [&](int a, int b) { return cls_key(in[a]) < cls_key(in[b]); });
     jobs_.clear();
     for (int i : order_) jobs_.push_back(in[i]);
     use_tc_ = (prec == SAC_MIXED && p.zstep_kernel == 0);
@@ -200,8 +206,8 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     for (auto& j : jobs_) { j.nlines = (long long)j.G.n_outer * j.G.n_inner; lines += j.nlines; }
     d_rlist_ = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)lines);
     d_rcount_ = (int*)take(sizeof(int) * 16);
-    d_status_ = d_rcount_ + 4;
-    d_nactive_ = d_rcount_ + 5;
+    d_status_ = d_rcount_ + kMaxCls;
+    d_nactive_ = d_rcount_ + kMaxCls + 1;
     long long ablocks = 0, tiles_ax3 = 0;
     for (auto& j : jobs_) {
         ablocks += admm_update_blocks(j.G.nf);
@@ -216,12 +222,17 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     for (size_t i = 0; i < nj;) {
         Cls c;
         c.K = jobs_[i].K;
+        c.seg = seg_of(jobs_[i]);
+        c.segG = 0;
+        c.maxm = 0;
         c.first = (int)i;
         size_t k = i;
         int maxm = 0, inner_fast = 0;
-        while (k < nj && jobs_[k].K == c.K) {
+        while (k < nj && cls_key(jobs_[k]) == cls_key(jobs_[i])) {
             maxm = std::max(maxm, jobs_[k].G.mpe);
             inner_fast |= (jobs_[k].G.n_inner > 1);
+            c.segG = std::max(c.segG, seg_warps(jobs_[k].G.mpe, c.seg));
+            c.maxm = std::max(c.maxm, jobs_[k].G.mpe);
             ++k;
         }
         c.count = (int)(k - i);
@@ -235,14 +246,14 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         }
         c.W = W;
         c.RLf = smem_row(maxm + 1, W, 8);
-        if ((int)cls_.size() >= 4) return SAC_EINVAL;
+        if ((int)cls_.size() >= kMaxCls) return SAC_EINVAL;
         c.d_pref = pref + cls_.size() * (nj + 1);
         long long* hp = hpref.data() + cls_.size() * (nj + 1);
         hp[0] = 0;
         c.lines = 0;
         for (int q = 0; q < c.count; ++q) {
             const Geometry& G = jobs_[c.first + q].G;
-            hp[q + 1] = hp[q] + line_tiles(G.n_outer, G.n_inner, W);
+            hp[q + 1] = hp[q] + (c.seg ? seg_tiles(jobs_[c.first + q].nlines) : line_tiles(G.n_outer, G.n_inner, W));
             c.lines += jobs_[c.first + q].nlines;
         }
         c.tiles = hp[c.count];
@@ -411,7 +422,7 @@ void Engine::prof_mark(int slot, int phase, int end) {
 
 int Engine::enqueue_iteration(int slot) {
     const bool mixed = (p_.prec == SAC_MIXED);
-    ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * 4, st_));
+    ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * kMaxCls, st_));
     for (int pass = 0; pass < 2; ++pass) {
     prof_mark(slot, pass, 0);
     for (size_t c = 0; c < cls_.size(); ++c) {
@@ -437,6 +448,9 @@ int Engine::enqueue_iteration(int slot) {
         L.status = d_status_;
         L.stream = st_;
         L.mode = pass;
+        L.seg_S = C.seg;
+        L.seg_G = C.segG;
+        L.seg_m = C.maxm;
         ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
     }
     prof_mark(slot, pass, 1);
@@ -519,6 +533,7 @@ int Engine::tune() {
     ENG_CUDA(cudaEventCreate(&b));
     for (size_t c = 0; c < cls_.size(); ++c) {
         Cls& C = cls_[c];
+        if (C.seg) continue;   // the segment kernel has no tile width to pick
         int inner_fast = 0, maxm = 0;
         for (int q = 0; q < C.count; ++q) {
             inner_fast |= (jobs_[C.first + q].G.n_inner > 1);

@@ -72,8 +72,11 @@ private:
     cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
     int use_tc_ = 1;
     // classes
+    static constexpr int kMaxCls = 8;   // b-step classes: faces per lane x segment kernel
     struct Cls {
         int K, W, RLf, first, count;
+        int seg, segG, maxm;            // segment kernel: faces per segment (0: warp per line),
+                                        // segments per line, longest line (cells)
         long long tiles, lines, line_off;
         long long* d_pref;
     };
@@ -91,7 +94,7 @@ private:
     long long* d_pref_admm_ = nullptr;   // ADMM update blocks per job (tensor-core z-step)
     long long admm_blocks_ = 0;
     unsigned long long* d_rlist_ = nullptr;
-    int* d_rcount_ = nullptr;      // one counter per class
+    int* d_rcount_ = nullptr;      // one counter per class, then status and active count
     int* d_status_ = nullptr;
     int* d_nactive_ = nullptr;
     double* d_part_ = nullptr;

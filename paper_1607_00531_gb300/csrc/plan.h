@@ -35,6 +35,8 @@ struct Plan {
     Geometry G;
     int prec;                 // SAC_F64 / SAC_MIXED
     int W, K, RLf;            // line kernels: lines per CTA, faces per lane, smem row
+    int seg_S, seg_G;          // b-step segment kernel: faces per segment (0: off), warps
+    long long seg_tiles;       // its tiles of seg_lines() lines
     long long line_tiles, pass_tiles[4], elem_blocks;
     int use_tc;                // tensor-core z-step passes
     long long tc_tiles[4];
@@ -50,6 +52,7 @@ struct Plan {
     long long* d_pref_elem;
     long long* d_pref_tc[4];
     long long* d_pref_admm;   // blocks of the ADMM update after the tensor-core passes
+    long long* d_pref_seg;    // tiles of the b-step segment kernel
     float* d_Ctc[4];
     float* d_Ctn[4];
     void* d_tmaps;            // tensor maps of the tensor-core passes

@@ -52,6 +52,12 @@ struct LineLaunch {
     long long list_blocks;       // grid size in mode 1
     int* status;
     cudaStream_t stream;
+    // b-step fast path with one thread per (line, segment) (bstep_seg.cu):
+    // faces per segment (0: the warp-per-line kernel) and warps per CTA (the
+    // largest segment count of the launch's jobs); prefix then counts tiles
+    // of seg_lines() lines
+    int seg_S, seg_G;
+    int seg_m;                   // longest line of the launch (cells): shared memory
 };
 
 // faces per lane for a line of m cells (m + 1 faces); 0 if too long
@@ -81,6 +87,17 @@ inline long long line_tiles(int n_outer, int n_inner, int W) {
     if (n_inner > 1) return (long long)n_outer * ((n_inner + W - 1) / W);
     return (n_outer + W - 1) / W;
 }
+
+// Segment kernel of the b-step: faces per segment for a job (0 when the job
+// takes the warp-per-line kernel: contiguous lines, n_sqp > 1, FP64, lines
+// of more than 272 faces, or kernel != 0; 9 faces up to 144, else 17), segments per line, its launch
+int seg_faces(int mpe, int n_inner, int n_sqp, bool mixed, int kernel);
+int seg_warps(int mpe, int S);
+int seg_lines();   // lines per CTA
+inline long long seg_tiles(long long nlines) { return (nlines + seg_lines() - 1) / seg_lines(); }
+size_t seg_smem_bytes(int mpe);   // dynamic shared memory of a CTA
+cudaError_t launch_bstep_seg(const LineLaunch& L);
+cudaError_t prepare_bstep_seg();
 
 // prec: 0 FP64, 1 FP32, 2 FP64 compute on FP32 storage
 cudaError_t launch_bstep(int prec, const LineLaunch& L);

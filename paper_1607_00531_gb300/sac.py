@@ -34,7 +34,7 @@ class SacParams(ctypes.Structure):
                  "eps_grad", "gn_rel_grad")] + \
                [(n, ctypes.c_int) for n in ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "prec")] + \
                [("near_bound", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("zstep_kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("zstep_kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("bstep_kernel", ctypes.c_int)]
 
 
 class SacError(RuntimeError):

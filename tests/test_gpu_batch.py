@@ -21,9 +21,10 @@ def sac():
 
 
 def volumes():
-    # different classes of line length (faces per lane 3, 5, 9), 2D and 3D, PE axes
+    # different classes of line length (faces per lane 3, 5, 9), 2D and 3D, PE axes;
+    # two volumes of the b-step segment kernel with 16 and 12 segments per line
     specs = [((24, 40), 1, 1), ((10, 70, 9), 1, 2), ((12, 150), 1, 3), ((8, 9, 30), 2, 4),
-             ((6, 260, 5), 1, 5), ((30, 33), 1, 6)]
+             ((6, 260, 5), 1, 5), ((30, 33), 1, 6), ((7, 200, 6), 1, 7)]
     out = []
     for m, pe, seed in specs:
         w = ph.small_workload(m, pe, seed=seed, peak_px=2.0, max_d=0.5)

@@ -212,6 +212,58 @@ def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
     assert abs(J_mix - J_ref) <= 1e-6 * abs(J_ref)
 
 
+# ---------------------------------------------------------------- b-step segment kernel (mixed path)
+
+# strided PE lines: 9 faces per segment up to 144 faces, 17 up to 272; line
+# counts with ragged 32-line tiles, segment counts from 5 to 16, the last
+# segment partly past the line end
+SEG_CASES = [
+    ((9, 70, 21), 1),       # 71 faces: 8 segments of 9, 189 lines (5 full tiles + 29)
+    ((40, 7, 9), 0),        # PE first: 41 faces, 63 lines in one outer slab
+    ((3, 143, 40), 1),      # 144 faces: exactly 16 segments of 9
+    ((4, 145, 10), 1),      # 146 faces: 9 segments of 17
+    ((5, 256, 11), 1),      # 257 faces: 16 segments of 17, 55 lines
+    ((2, 271, 17), 1),      # 272 faces: exactly 16 segments of 17
+]
+
+
+@pytest.mark.parametrize("m,pe", SEG_CASES)
+def test_bstep_mixed_segment_kernel(sac, m, pe):
+    # the mixed b-step (one thread per line segment) against the FP64 oracle
+    # (1e-3 voxel) and against the warp-per-line FP32 kernel
+    h, I1, I2, b, z, u = case_data(m, pe, seed=30)
+    og = oracle.Grid(m, h, pe)
+    b_ref, st = oracle.bstep(og, oracle.Params(alpha=0.5, rho=100.0), I1, I2, b, z, u)
+    g = sac.grid(m, h, pe)
+    outs = []
+    for kern in (0, 1):
+        p = sac.params(alpha=0.5, rho=100.0, prec="mixed", bstep_kernel=kern)
+        out, capped = sac.bstep(g, p, cu(I1, torch.float32), cu(I2, torch.float32), cu(b), cu(z), cu(u))
+        assert not capped
+        outs.append(out.cpu().numpy())
+        assert np.max(np.abs(outs[-1] - b_ref)) / h[pe] <= 1e-3
+    assert np.max(np.abs(outs[0] - outs[1])) / h[pe] <= 1e-4
+
+
+@pytest.mark.parametrize("m,pe", [((9, 70, 21), 1), ((5, 256, 11), 1)])
+def test_bstep_mixed_segment_kernel_queues_blocked_lines(sac, m, pe):
+    # steep targets: many lines' unconstrained steps cross |D1 b| = 1; the
+    # segment kernel leaves them to the FP64 active-set method
+    h, I1, I2, b, _, u = case_data(m, pe, seed=40, max_d=0.8)
+    rng = np.random.default_rng(6)
+    z = b + 3.0 * h[pe] * rng.normal(size=b.shape)
+    og = oracle.Grid(m, h, pe)
+    b_ref, st = oracle.bstep(og, oracle.Params(alpha=1e-3, rho=1e5), I1, I2, b, z, u)
+    assert st["active"] > 0 and st["capped"] == 0
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=1e-3, rho=1e5, prec="mixed", bstep_kernel=0)
+    out, capped = sac.bstep(g, p, cu(I1, torch.float32), cu(I2, torch.float32), cu(b), cu(z), cu(u))
+    assert not capped
+    out = out.cpu().numpy()
+    assert np.max(np.abs(out - b_ref)) / h[pe] <= 1e-3
+    assert oracle.max_abs_d1(og, out) <= 1 + 1e-5
+
+
 # ---------------------------------------------------------------- tensor-core z-step (mixed path)
 
 TC_CASES = [
