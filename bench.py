@@ -161,14 +161,21 @@ def roofline(prof, w, g, nf, sac):
     axes = [a for a in range(3) if a != w.pe]
     L1 = F[axes[0]] if axes[0] < len(F) else 1
     L2 = F[axes[1]] if axes[1] < len(F) else 1
-    per_face_bytes = {"zpass0": 12, "zpass1": 8, "zpass2": 8, "zpass3": 24}
+    # FP32 arrays read + written per face: pass 0 b, u -> t1; passes 1-3
+    # one array in, one out; the update reads b, u, t2, z and writes u, z
+    per_face_bytes = {"zpass0": 12, "zpass1": 8, "zpass2": 8, "zpass3": 8, "admm_update": 24}
     flops = {"zpass0": 2 * L1 * nf, "zpass3": 2 * L1 * nf, "zpass1": 2 * L2 * nf, "zpass2": 2 * L2 * nf}
     nphase = {k: v for k, v in prof.items() if v[1] > 0}
     tot_ms = sum(v[0] for v in nphase.values())
     kernels = {}
     for k, (ms, n) in nphase.items():
         avg = ms / n / 1e3
-        if k in ("bstep", "bstep_refine"):
+        if k == "admm_update":
+            byts = per_face_bytes[k] * nf
+            ach_b = byts / avg / 1e9
+            ent = {"ms_total": ms, "launches": n, "share": ms / tot_ms, "bytes": byts, "achieved_gbs": ach_b,
+                   "frac_hbm": ach_b / hbm, "bound": "hbm"}
+        elif k in ("bstep", "bstep_refine"):
             byts = 2 * 4 * cells + 4 * 4 * nf if k == "bstep" else None
             ent = {"ms_total": ms, "launches": n, "share": ms / tot_ms}
             if byts:
@@ -183,8 +190,8 @@ def roofline(prof, w, g, nf, sac):
             ent["bound"] = "hbm" if ent["frac_hbm"] >= ent["frac_tensor_tf32"] else "tensor"
         kernels[k] = ent
     # kernels behind each phase: axes of at most 128 faces run the lines-in-N
-    # tensor-core kernel, longer ones the lines-in-M kernel; the last phase
-    # also holds the element-wise ADMM update and the stopping test
+    # tensor-core kernel, longer ones the lines-in-M kernel; the element-wise
+    # ADMM update also runs the stopping test (in each volume's last block)
     def zk(L, q):
         return (f"k_axis_tcn<{q}>" if L <= 128 else f"k_axis_tc<{q}>")
     # b-step: strided PE lines of at most 272 faces take the segment kernel
@@ -197,7 +204,7 @@ def roofline(prof, w, g, nf, sac):
         bname = f"k_bstep<float,float,{kpl}>"
     names = {"bstep": bname, "bstep_refine": f"k_bstep_list<double,float,{kpl}>",
              "zpass0": zk(L1, 0), "zpass1": zk(L2, 1), "zpass2": zk(L2, 2),
-             "zpass3": zk(L1, 3) + " + k_admm_update + k_admm_check"}
+             "zpass3": zk(L1, 3), "admm_update": "k_admm_update"}
     for k in kernels:
         kernels[k]["kernel"] = names.get(k, k)
     dom = max(nphase, key=lambda k: nphase[k][0])

@@ -261,11 +261,13 @@ void sac_server_destroy(sac_server s);
  *   2 z-step pass 0 (DCT along the first non-PE axis, fused b + u)
  *   3 z-step pass 1 (DCT along the second non-PE axis, spectral scaling)
  *   4 z-step pass 2 (inverse DCT along the second non-PE axis)
- *   5 z-step pass 3 (inverse DCT along the first non-PE axis, dual update,
- *     residual-norm partial sums and their reduction)
+ *   5 z-step pass 3 (inverse DCT along the first non-PE axis)
+ *   6 dual update u <- u + b - z, z update, residual-norm partial sums and
+ *     the stopping test (tensor-core z-step: the element-wise update kernel;
+ *     SIMT z-step: the reduction of the sums pass 3 produced)
  * sac_launch_count returns the number of kernels this library has launched
  * in the process so far. */
-#define SAC_NPHASES 6
+#define SAC_NPHASES 7
 int sac_profile_enable(int on);
 int sac_profile_read(double* ms, long long* launches, int reset);
 long long sac_launch_count(void);

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "admm_check.cuh"
 #include "plan.h"
 
 namespace sac {
@@ -482,17 +483,21 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
             A.prefix = P.d_pref_tc[q];
             A.total_tiles = P.tc_tiles[q];
             SAC_CUDA(launch_axis_pass_tc(A, P.tc_cfg[q]));
-            if (q == 3) {
-                // z^{k+1} is in t2: ADMM update and residual sums, element-wise
-                SAC_CUDA(launch_admm_update(P.d_job, 1, P.d_pref_admm, P.admm_blocks, P.d_part, st));
-                SAC_CUDA(launch_reduce(P.d_part, (int)P.admm_blocks, 5, P.d_out + 16, st));
-            }
         } else {
             A.prefix = P.d_pref_pass[q];
             A.total_tiles = P.pass_tiles[q];
             SAC_CUDA(launch_axis_pass(A));
-            if (q == 3) SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
         }
+    }
+    PhaseScope ps(6, st);
+    if (P.use_tc) {
+        // z^{k+1} is in t2: ADMM update and residual sums, element-wise
+        AdmmCheck none;
+        memset(&none, 0, sizeof(none));
+        SAC_CUDA(launch_admm_update(P.d_job, 1, P.d_pref_admm, P.admm_blocks, P.d_part, none, st));
+        SAC_CUDA(launch_reduce(P.d_part, (int)P.admm_blocks, 5, P.d_out + 16, st));
+    } else {
+        SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
     }
     return SAC_OK;
 }

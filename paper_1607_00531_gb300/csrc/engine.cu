@@ -87,41 +87,16 @@ size_t job_state_bytes(const Geometry& G, int prec, int use_tc) { return state_l
 
 // ---------------------------------------------------------------- kernels
 
-// pref3: partial-sum sets (5 each) per job: the blocks of the ADMM update
-// (tensor-core z-step) or the tiles of the last SIMT pass
+// pref3: partial-sum sets (5 each) per job: the tiles of the last SIMT pass
+// (the tensor-core z-step runs the test inside its element-wise update)
 __global__ void k_admm_check(Job* __restrict__ jobs, int njobs, const long long* __restrict__ pref3,
-                             const double* __restrict__ part, double eps_abs, double eps_rel, int max_iter,
-                             double* __restrict__ stats, int* __restrict__ nactive) {
+                             const double* __restrict__ part, AdmmCheck chk) {
     __shared__ double red[32 * 5];
     const int j = blockIdx.x;
     if (j >= njobs) return;
     Job& J = jobs[j];
     if (!J.active) return;
-    double acc[5] = {0, 0, 0, 0, 0};
-#pragma unroll 4
-    for (long long t = pref3[j] + threadIdx.x; t < pref3[j + 1]; t += blockDim.x)
-        for (int c = 0; c < 5; ++c) acc[c] += part[t * 5 + c];
-    block_sum<5>(acc, red);
-    if (threadIdx.x == 0) {
-        double* st = stats + (size_t)j * 8;
-        const int it = (int)st[4] + 1;
-        // square roots in FP32 (a stopping test; FP64 square roots are long
-        // dependent chains on the FP64 unit of this GPU)
-        const double rhd = J.rho * J.hd, sqn = (double)sqrtf((float)J.nf);
-        const double rp = (double)sqrtf((float)acc[0]), rd = rhd * (double)sqrtf((float)acc[1]);
-        const double nb = (double)sqrtf((float)acc[2]), nz = (double)sqrtf((float)acc[3]),
-                     nu = (double)sqrtf((float)acc[4]);
-        const double ep = sqn * eps_abs + eps_rel * fmax(nb, nz);
-        const double ed = sqn * eps_abs + eps_rel * rhd * nu;
-        const bool conv = (rp <= ep) && (rd <= ed);
-        st[0] = rp; st[1] = rd; st[2] = ep; st[3] = ed; st[4] = it; st[5] = conv ? 1.0 : 0.0;
-        if (!(rp == rp) || !(rd == rd)) st[6] = 1.0;   // non-finite
-        if (conv || it >= max_iter || st[6] != 0.0) {
-            J.active = 0;
-        } else {
-            atomicAdd(nactive, 1);
-        }
-    }
+    admm_check_job(J, j, part, pref3[j], pref3[j + 1], chk, red);
 }
 
 // state initialisation: z = b, u = 0 (FP32 state: b32 = z = float(b))
@@ -153,10 +128,11 @@ size_t Engine::table_bytes(const std::vector<EngineJob>& jobs, const sac_params&
     long long np = 5 * std::max(ablocks, tiles_ax3) + 8;
     size_t off = 0;
     off += a256(sizeof(Job) * nj);
-    off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 4 classes), 8 pass prefixes, ADMM update blocks, spare
+    off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 8 classes), 4 pass prefixes, ADMM update blocks, spare
     off += a256(sizeof(long long) * (nj + 1) * 4 * nj);        // tensor-core pass prefixes per geometry group
     off += a256(sizeof(unsigned long long) * (size_t)lines);
     off += a256(sizeof(int) * 16);
+    off += a256(sizeof(int) * nj);                             // fused stopping test: finished blocks per job
     off += a256(sizeof(double) * (size_t)np);
     off += a256(sizeof(double) * 8 * nj);
     return off;
@@ -208,6 +184,7 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     d_rcount_ = (int*)take(sizeof(int) * 16);
     d_status_ = d_rcount_ + kMaxCls;
     d_nactive_ = d_rcount_ + kMaxCls + 1;
+    d_counters_ = (int*)take(sizeof(int) * nj);
     long long ablocks = 0, tiles_ax3 = 0;
     for (auto& j : jobs_) {
         ablocks += admm_update_blocks(j.G.nf);
@@ -407,6 +384,11 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         ENG_CUDA(cudaMemcpyAsync(d_stats_, hs.data(), hs.size() * 8, cudaMemcpyHostToDevice, st));
     }
     ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * 16, st));
+    ENG_CUDA(cudaMemsetAsync(d_counters_, 0, sizeof(int) * nj, st));
+    {
+        const int na = (int)nj;   // every job starts active; the test counts retirements down
+        ENG_CUDA(cudaMemcpyAsync(d_nactive_, &na, sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     ENG_CUDA(cudaStreamSynchronize(st));
     iters_done_ = 0;
     return SAC_OK;
@@ -474,21 +456,26 @@ int Engine::enqueue_iteration(int slot) {
                 A.total_tiles = ztiles_[z];
                 ENG_CUDA(launch_axis_pass_tc(A, zcfg_[z]));
             }
-            // z^{k+1} is in t2: ADMM update and residual sums, element-wise
-            if (q == 3) ENG_CUDA(launch_admm_update(d_jobs_, nj, d_pref_admm_, admm_blocks_, d_part_, st_));
         } else {
             A.prefix = d_pref_ax_[q];
             A.total_tiles = ax_tiles_[q];
             ENG_CUDA(launch_axis_pass(A));
         }
-        if (q < 3) prof_mark(slot, 2 + q, 1);
+        prof_mark(slot, 2 + q, 1);
     }
-    ENG_CUDA(cudaMemsetAsync(d_nactive_, 0, sizeof(int), st_));
-    count_launch();
-    k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, use_tc_ ? d_pref_admm_ : d_pref_ax_[3], d_part_, p_.eps_abs,
-                                      p_.eps_rel, p_.max_iter, d_stats_, d_nactive_);
-    ENG_CUDA(cudaGetLastError());
-    prof_mark(slot, 5, 1);
+    prof_mark(slot, 6, 0);
+    if (use_tc_) {
+        // z^{k+1} is in t2: ADMM update, residual sums and (in the last block
+        // of each job) the stopping test, element-wise
+        ENG_CUDA(launch_admm_update(d_jobs_, nj, d_pref_admm_, admm_blocks_, d_part_, check_args(), st_));
+    } else {
+        count_launch();
+        AdmmCheck chk = check_args();
+        chk.counters = nullptr;
+        k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, d_pref_ax_[3], d_part_, chk);
+        ENG_CUDA(cudaGetLastError());
+    }
+    prof_mark(slot, 6, 1);
     return SAC_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <map>
 #include <vector>
 
+#include "admm_check.cuh"
 #include "plan.h"
 
 extern "C" long long sac_launch_count(void);
@@ -95,6 +96,17 @@ private:
     long long admm_blocks_ = 0;
     unsigned long long* d_rlist_ = nullptr;
     int* d_rcount_ = nullptr;      // one counter per class, then status and active count
+    int* d_counters_ = nullptr;    // per job: finished blocks of the ADMM update (fused stopping test)
+    AdmmCheck check_args() const {
+        AdmmCheck c;
+        c.counters = d_counters_;
+        c.eps_abs = p_.eps_abs;
+        c.eps_rel = p_.eps_rel;
+        c.max_iter = p_.max_iter;
+        c.stats = d_stats_;
+        c.nactive = d_nactive_;
+        return c;
+    }
     int* d_status_ = nullptr;
     int* d_nactive_ = nullptr;
     double* d_part_ = nullptr;

@@ -8,6 +8,7 @@
 namespace sac {
 
 struct Job;
+struct AdmmCheck;
 
 // number of kernels launched by this library (instrumentation)
 void count_launch(long long n = 1);
@@ -148,10 +149,11 @@ size_t tc_map_bytes();
 int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float* u, const float* t1,
                    const float* t2, void* out);
 // After the tensor-core passes (z^{k+1} in t2): u <- u + b - t2, z <- t2 and
-// 5 residual partial sums per block (FP32 state); blocks per job:
+// 5 residual partial sums per block (FP32 state) and, when chk.counters is
+// set, the stopping test of each job in its last block; blocks per job:
 long long admm_update_blocks(long long nf);
-cudaError_t launch_admm_update(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
-                               double* part, cudaStream_t st);
+cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                               double* part, const AdmmCheck& chk, cudaStream_t st);
 void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass);
 bool tc_cfg_finish(TcCfg* c);
 cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg);

@@ -60,6 +60,7 @@
 
 #include <mutex>
 
+#include "admm_check.cuh"
 #include "sac_dev.cuh"
 #include "sac_launch.h"
 #include "tc_ptx.cuh"
@@ -713,24 +714,29 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 // with one set of partial sums per block of
 //   |b - z^{k+1}|^2, |z^{k+1} - z^k|^2, |b|^2, |z^{k+1}|^2, |u^{k+1}|^2
 // (the residuals of the stopping test).  A block covers kAdmmFaces
-// consecutive faces of one job in kAdmmIters rounds of 16 loads per thread;
-// blocks of a stopped job write zeros.
+// consecutive faces of one job in kAdmmIters rounds of 16 loads per thread
+// (about four blocks per SM for a volume of 5M faces, all resident at once);
+// blocks of a stopped job write zeros.  With chk.counters set, the last
+// block of a job to finish (counted with an atomic after a fence) also runs
+// the job's stopping test on the job's partial sums.
 constexpr int kAdmmThreads = 256;
 constexpr int kAdmmGroups = 4;                                  // float4 groups per thread and round
-constexpr int kAdmmIters = 4;
+constexpr int kAdmmIters = 2;
 constexpr long long kAdmmFaces = (long long)kAdmmThreads * kAdmmGroups * 4 * kAdmmIters;
 
 long long admm_update_blocks(long long nf) { return (nf + kAdmmFaces - 1) / kAdmmFaces; }
 
-__global__ void __launch_bounds__(kAdmmThreads) k_admm_update(const Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ jobs, int njobs,
                                                               const long long* __restrict__ prefix,
-                                                              double* __restrict__ part) {
+                                                              double* __restrict__ part, AdmmCheck chk) {
     __shared__ double red[32 * 5];
+    __shared__ int last;
     const long long blk = blockIdx.x;
     const int jid = find_job(prefix, njobs, blk);
-    const Job& J = jobs[jid];
+    Job& J = jobs[jid];
+    const bool active = J.active != 0;
     float tn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (J.active) {
+    if (active) {
         const long long nf = J.nf;
         const long long e00 = (blk - prefix[jid]) * kAdmmFaces;
         float* __restrict__ z = (float*)J.z;
@@ -742,6 +748,7 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(const Job* __restr
             tn[0] += dbz * dbz; tn[1] += dzz * dzz; tn[2] += bb * bb; tn[3] += zz * zz; tn[4] += un * un;
         };
         if ((nf & 3) == 0) {
+#pragma unroll
             for (int r = 0; r < kAdmmIters; ++r) {
                 const long long e0 = e00 + (long long)r * kAdmmThreads * kAdmmGroups * 4;
                 float4 vb[kAdmmGroups], vz[kAdmmGroups], vu[kAdmmGroups], vn[kAdmmGroups];
@@ -780,20 +787,42 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(const Job* __restr
             }
         }
     }
-    double nrm[5] = {tn[0], tn[1], tn[2], tn[3], tn[4]};
-    block_sum<5>(nrm, red);
-    if (threadIdx.x == 0) {
-        double* p = part + blk * 5;
+    // warp sums in FP32, the block's total in FP64 (stand-alone form: the
+    // caller reduces the doubles) or FP32 (fused form: float partial sets in
+    // the same array, reduced by the job's last block)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) p[c] = nrm[c];
+    for (int c = 0; c < 5; ++c) tn[c] = warp_sum(tn[c]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* redf = reinterpret_cast<float*>(red);
+    if (lane == 0)
+        for (int c = 0; c < 5; ++c) redf[wid * 5 + c] = tn[c];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        float v = 0.f;
+        for (int w = 0; w < kAdmmThreads / 32; ++w) v += redf[w * 5 + threadIdx.x];
+        if (chk.counters) reinterpret_cast<float*>(part)[blk * 5 + threadIdx.x] = v;
+        else part[blk * 5 + threadIdx.x] = (double)v;
     }
+    if (!chk.counters || !active) return;
+    // the last block of the job runs the job's stopping test
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nb = (int)(prefix[jid + 1] - prefix[jid]);
+        last = (atomicAdd(&chk.counters[jid], 1) == nb - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    admm_check_job_f32(J, jid, reinterpret_cast<const float*>(part), prefix[jid], prefix[jid + 1], chk, redf);
+    if (threadIdx.x == 0) chk.counters[jid] = 0;
 }
 
-cudaError_t launch_admm_update(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
-                               double* part, cudaStream_t st) {
+cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, long long total_blocks,
+                               double* part, const AdmmCheck& chk, cudaStream_t st) {
     if (total_blocks <= 0) return cudaSuccess;
     count_launch();
-    k_admm_update<<<(unsigned)total_blocks, kAdmmThreads, 0, st>>>(jobs, njobs, prefix, part);
+    k_admm_update<<<(unsigned)total_blocks, kAdmmThreads, 0, st>>>(jobs, njobs, prefix, part, chk);
     return cudaGetLastError();
 }
 

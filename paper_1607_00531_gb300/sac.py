@@ -297,7 +297,7 @@ def gnpcg_solve(g, p, I1, I2, b, want_hist=False, ws=None, stream=None):
     return res
 
 
-PHASES = ["bstep", "bstep_refine", "zpass0", "zpass1", "zpass2", "zpass3"]
+PHASES = ["bstep", "bstep_refine", "zpass0", "zpass1", "zpass2", "zpass3", "admm_update"]
 
 
 def profile_enable(on=True):
