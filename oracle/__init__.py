@@ -58,6 +58,7 @@ def lib():
             "ref_precond_solve": g + [P, dp, dp, dp, dp, dp],
             "ref_pcg": g + [P, dp, dp, dp, dp, dp, dp],
             "ref_gnpcg": g + [P, dp, dp, dp, dp, lp, dp, dp],
+            "ref_corrected": g + [dp, dp, dp, dp, dp, dp],
         }.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -251,6 +252,17 @@ def gnpcg(grid, prm, I1, I2, b0, want_hist=False):
     if want_hist:
         res["hist"] = hist[:info[0]]
     return res
+
+
+def corrected(grid, I1, I2, b):
+    """Transformed images T1 = I1(x + A b)(1 + D1 b), T2 = I2(x - A b)(1 - D1 b),
+    SSD = h^d/2 |T1 - T2|^2 and NCC = <T1,T2>^2 / (|T1|^2 |T2|^2)."""
+    T1 = np.zeros(grid.cell_shape)
+    T2 = np.zeros(grid.cell_shape)
+    out = np.zeros(2)
+    _check(lib().ref_corrected(*grid.args(), _dp(_f64(I1)), _dp(_f64(I2)), _dp(_f64(b)), _dp(T1), _dp(T2),
+                               _dp(out)), "ref_corrected")
+    return dict(T1=T1, T2=T2, ssd=out[0], ncc=out[1])
 
 
 def max_abs_d1(grid, b):

@@ -751,6 +751,49 @@ static double norm2(long n, const double* v) {
     return sqrt(s);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Corrected images and image similarity (Sec. 6, comparison of the 3D       */
+/* results: SSD and NCC between the transformed blip-up and blip-down data). */
+/*                                                                           */
+/* The transformed images are the two terms of the residual of Eq. D:       */
+/*   T1 = I_v(x + A b) .* (1 + D1 b),   T2 = I_-v(x - A b) .* (1 - D1 b).     */
+/* Readings (the paper cites the measures without formulas):                 */
+/*   SSD(b) = h^d / 2 |T1 - T2|^2 (the sum-of-squared-differences distance,  */
+/*            the same value as D(b) of Eq. D);                              */
+/*   NCC(b) = <T1, T2>^2 / (|T1|^2 |T2|^2), in [0, 1] with 1 optimal.        */
+/* out[0] = SSD, out[1] = NCC; T1, T2 (cell arrays) may be NULL.            */
+/* ------------------------------------------------------------------------ */
+int ref_corrected(int nd, const int* m, const double* h, int pe, const double* I1, const double* I2,
+                  const double* b, double* T1, double* T2, double* out) {
+    grid_t g;
+    int st = make_grid(nd, m, h, pe, &g);
+    if (st) return st;
+    long L = n_lines(&g);
+    double hp = g.h[g.pe];
+    double s_dd = 0.0, s_12 = 0.0, s_11 = 0.0, s_22 = 0.0;
+    for (long l = 0; l < L; ++l) {
+        long c0 = line_cell0(&g, l), f0 = line_face0(&g, l);
+        for (long j = 0; j < g.mpe; ++j) {
+            double b0 = b[f0 + j * g.n_inner], b1 = b[f0 + (j + 1) * g.n_inner];
+            double a = 0.5 * (b0 + b1);       /* A1 b */
+            double d = (b1 - b0) / hp;        /* D1 b */
+            double v1, s1, v2, s2;
+            interp_line(I1 + c0, g.n_inner, g.mpe, (double)j + a / hp, &v1, &s1);
+            interp_line(I2 + c0, g.n_inner, g.mpe, (double)j - a / hp, &v2, &s2);
+            double t1 = v1 * (1.0 + d), t2 = v2 * (1.0 - d);
+            if (T1) T1[c0 + j * g.n_inner] = t1;
+            if (T2) T2[c0 + j * g.n_inner] = t2;
+            s_dd += (t1 - t2) * (t1 - t2);
+            s_12 += t1 * t2;
+            s_11 += t1 * t1;
+            s_22 += t2 * t2;
+        }
+    }
+    out[0] = 0.5 * g.hd * s_dd;
+    out[1] = (s_11 > 0.0 && s_22 > 0.0) ? (s_12 * s_12) / (s_11 * s_22) : 0.0;
+    return REF_OK;
+}
+
 /* max |D1 b| over all cells (feasibility of b for the constraint set C) */
 double ref_max_abs_d1(int nd, const int* m, const double* h, int pe, const double* b) {
     grid_t g;

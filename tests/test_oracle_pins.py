@@ -112,6 +112,79 @@ def test_distance_for_subvoxel_shift_of_a_tent_is_closed_form():
         assert D == pytest.approx(3 * 0.5 * 0.2 * h * np.sum(r * r), rel=1e-12)
 
 
+# ---------------------------------------------------------------- corrected images, SSD, NCC (Sec. 6)
+
+def _ncc(a, b):
+    return float(np.sum(a * b) ** 2 / (np.sum(a * a) * np.sum(b * b)))
+
+
+def test_corrected_images_for_zero_field_are_the_inputs():
+    # b = 0: A1 b = D1 b = 0 and the interpolant passes through the samples
+    for m, pe in [((12, 9), 1), ((6, 7, 5), 1), ((5, 6, 4), 0), ((5, 4, 6), 2)]:
+        g = grid_of(m, pe)
+        I1, I2 = ph.random_images(m, seed=7), ph.random_images(m, seed=8)
+        c = oracle.corrected(g, I1, I2, np.zeros(g.face_shape))
+        assert np.array_equal(c["T1"], I1) and np.array_equal(c["T2"], I2)
+        hd = float(np.prod(g.h))
+        assert c["ssd"] == pytest.approx(0.5 * hd * np.sum((I1 - I2) ** 2), rel=1e-13)
+        assert c["ncc"] == pytest.approx(_ncc(I1, I2), rel=1e-13)
+
+
+def test_corrected_images_for_whole_voxel_shift_are_shifted_samples():
+    # b = k h constant: T1[j] = I1[j + k], T2[j] = I2[j - k], zero outside the line
+    m, pe = (7, 10), 1
+    h = (0.1, 0.1)
+    g = oracle.Grid(m, h, pe)
+    rng = np.random.default_rng(1)
+    I1, I2 = rng.uniform(size=m), rng.uniform(size=m)
+    for k in (-3, -1, 1, 2, 11):
+        c = oracle.corrected(g, I1, I2, np.full(g.face_shape, k * h[1]))
+        P1 = np.zeros((m[0], m[1] + 40)); P1[:, 20:20 + m[1]] = I1
+        P2 = np.zeros((m[0], m[1] + 40)); P2[:, 20:20 + m[1]] = I2
+        assert np.allclose(c["T1"], P1[:, 20 + k:20 + k + m[1]], rtol=0, atol=1e-15)
+        assert np.allclose(c["T2"], P2[:, 20 - k:20 - k + m[1]], rtol=0, atol=1e-15)
+
+
+def test_corrected_image_for_subvoxel_shift_of_a_tent_is_closed_form():
+    m = 24
+    h = 1.0 / m
+    t0, w = 11, 5
+    tent = lambda t: np.maximum(0.0, 1.0 - np.abs(t - t0) / w)
+    I = tent(np.arange(m, dtype=float))[None, :].repeat(3, axis=0)
+    g = oracle.Grid((3, m), (0.2, h), 1)
+    j = np.arange(m, dtype=float)
+    for sft in (0.37, -1.6, 2.25):
+        c = oracle.corrected(g, I, I, np.full(g.face_shape, sft * h))
+        assert np.allclose(c["T1"], tent(j + sft)[None, :], rtol=0, atol=1e-14)
+        assert np.allclose(c["T2"], tent(j - sft)[None, :], rtol=0, atol=1e-14)
+
+
+def test_ssd_is_the_distance_and_the_image_difference_is_the_residual():
+    for m, pe in [((9, 16), 1), ((5, 12, 6), 1), ((10, 4, 5), 0), ((4, 5, 14), 2)]:
+        g = grid_of(m, pe)
+        I1, I2 = ph.random_images(m, seed=11), ph.random_images(m, seed=12)
+        b = ph.random_field(m, pe, g.h, seed=13, max_d=0.6)
+        c = oracle.corrected(g, I1, I2, b)
+        D = oracle.objective(g, oracle.Params(alpha=0.0), I1, I2, b)["D"]
+        assert c["ssd"] == pytest.approx(D, rel=1e-12)
+        assert np.allclose(c["T1"] - c["T2"], oracle.residual(g, I1, I2, b), rtol=0, atol=1e-13)
+
+
+def test_ncc_scale_invariance_swap_symmetry_and_optimum():
+    m, pe = (6, 11, 5), 1
+    g = grid_of(m, pe)
+    I1, I2 = ph.random_images(m, seed=21), ph.random_images(m, seed=22)
+    b = ph.random_field(m, pe, g.h, seed=23, max_d=0.5)
+    c = oracle.corrected(g, I1, I2, b)
+    assert 0.0 <= c["ncc"] <= 1.0
+    assert oracle.corrected(g, I1, 3.0 * I2, b)["ncc"] == pytest.approx(c["ncc"], rel=1e-12)
+    # swapping the images and negating b swaps the transformed images
+    s = oracle.corrected(g, I2, I1, -b)
+    assert np.allclose(s["T1"], c["T2"], rtol=0, atol=1e-14) and np.allclose(s["T2"], c["T1"], rtol=0, atol=1e-14)
+    # proportional transformed images: NCC = 1
+    assert oracle.corrected(g, I1, 2.0 * I1, np.zeros(g.face_shape))["ncc"] == pytest.approx(1.0, rel=1e-14)
+
+
 def test_regulariser_and_penalty_of_linear_ramps():
     m, pe = (6, 8, 5), 1
     h = (0.5, 0.25, 0.2)
