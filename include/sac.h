@@ -141,6 +141,19 @@ int sac_objective_noalloc(const sac_grid* g, const sac_params* p, const void* I1
                           const double* b, double* out4, void* stream);
 size_t sac_objective_noalloc_max_bytes(void);
 
+/* Corrected images and their similarity (Sec. 6, comparison of the 3D
+   results): the transformed blip-up / blip-down images
+     T1 = I1(x + A b) .* (1 + D1 b),   T2 = I2(x - A b) .* (1 - D1 b)
+   (cell arrays in the image type: float for SAC_MIXED, double for SAC_F64;
+   device pointers, either may be NULL), the sum of squared differences
+   *ssd = h^d/2 |T1 - T2|^2 (the value of D(b), Eq. D) and the normalised
+   cross-correlation *ncc = <T1,T2>^2 / (|T1|^2 |T2|^2) in [0, 1], 1 optimal
+   (host pointers, either may be NULL).  b (device, double) need not be
+   feasible.  Synchronises `stream` before returning. */
+int sac_corrected_images(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                         const double* b, void* T1, void* T2, double* ssd, double* ncc, void* ws,
+                         size_t ws_bytes, void* stream);
+
 /* Gradient of J_GN (Sec. 3: grad D = h^d J_r^T r, grad S = h^d sum_a D_a^T D_a b,
    grad P = beta h^d D1^T phi'(D1 b)) into grad (face array, double). */
 int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,

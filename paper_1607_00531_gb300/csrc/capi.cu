@@ -613,6 +613,25 @@ int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const 
     return status_of(P, st, nullptr);
 }
 
+int sac_corrected_images(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
+                         const double* b, void* T1, void* T2, double* ssd, double* ncc, void* ws,
+                         size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b) return SAC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P;
+    SAC_TRY(setup(g, p, ws, ws_bytes, &P));
+    SAC_TRY(plan_upload(&P, p, I1, I2, (void*)b, nullptr, nullptr, nullptr, nullptr, st));
+    const int blocks = corrected_blocks(P.G.nc);
+    if (4LL * blocks > P.n_part) return SAC_EINVAL;
+    SAC_CUDA(launch_corrected(P.prec == SAC_MIXED ? 1 : 0, P.d_job, P.G.nc, b, T1, T2, P.d_part, st));
+    SAC_CUDA(launch_reduce(P.d_part, blocks, 4, P.d_out + 24, st));
+    double s[4];
+    SAC_TRY(read_back(s, P.d_out + 24, sizeof(s), st));
+    if (ssd) *ssd = 0.5 * P.G.hd * s[0];
+    if (ncc) *ncc = (s[2] > 0.0 && s[3] > 0.0) ? (s[1] * s[1]) / (s[2] * s[3]) : 0.0;
+    return status_of(P, st, nullptr);
+}
+
 int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
                  double* grad, void* ws, size_t ws_bytes, void* stream) {
     if (!I1 || !I2 || !b || !grad) return SAC_EINVAL;

@@ -187,6 +187,12 @@ cudaError_t launch_dot2(long long n, const double* x, const double* y, const dou
 cudaError_t launch_cast(long long n, const double* src, float* dst, cudaStream_t st);
 cudaError_t launch_cast_back(long long n, const float* src, double* dst, cudaStream_t st);
 cudaError_t launch_fill(long long n, double v, double* dst, cudaStream_t st);
+// transformed images T1, T2 (either may be null; image type: FP64 for prec
+// 0, else FP32) and corrected_blocks(nc) sets of 4 partial sums
+// (corrected.cu); b is the FP64 field
+int corrected_blocks(long long nc);
+cudaError_t launch_corrected(int prec, const Job* job, long long nc, const double* b, void* T1, void* T2,
+                             double* part, cudaStream_t st);
 cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
                               const double* b, double* part, cudaStream_t st);
 

@@ -339,10 +339,30 @@ __device__ __forceinline__ TcTile tc_tile(const Job* __restrict__ jobs, int njob
     return s;
 }
 
+// Work units of a launch: units below nfull are whole tiles; the tiles from
+// nfull on (the last, partial round over the SMs) are split into two units
+// each, the two halves of the output columns (N), so that the last round
+// takes about half a tile's time on twice as many SMs.
+__device__ __forceinline__ long long tc_unit_tile(long long u, long long nfull) {
+    return u < nfull ? u : nfull + ((u - nfull) >> 1);
+}
+// output columns [n0, n0 + nN) of unit u (Np: the tile's padded L)
+__device__ __forceinline__ void tc_unit_cols(long long u, long long nfull, int Np, int& n0, int& nN) {
+    if (u < nfull) {
+        n0 = 0;
+        nN = Np;
+        return;
+    }
+    const int h0 = ((Np / 2 + 15) / 16) * 16;
+    const bool second = ((u - nfull) & 1) != 0;
+    n0 = second ? h0 : 0;
+    nN = second ? Np - h0 : h0;
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_axis_tc(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, long long total,
-              TcCfg cfg, int* __restrict__ status) {
+              long long nfull, TcCfg cfg, int* __restrict__ status) {
     using namespace tc;
     constexpr int NSRC = (PASS == 0) ? 2 : 1;   // X sources (pass 0: b + u)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -402,7 +422,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         RingPos rr, tr;
         bool run = true;
         for (long long t = t0; t < total && run; t += dt) {
-            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
+            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
             if (!s.active) continue;
             const Job& J = *s.J;
             const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
@@ -482,7 +502,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             long long r_it = 0;
             RingPos rr;
             for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
+                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
                 const char* maps = (const char*)s.J->tmaps + (size_t)2 * PASS * 128;
                 bool ok = true;
@@ -517,7 +537,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             long long d_it = 0;
             RingPos dr;
             for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
+                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
                 const float* Mpre = (const float*)s.J->Ctc[PASS];
                 const uint32_t db = 2u * (uint32_t)s.Np * 128u;
@@ -550,13 +570,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         if (lane == 0) {
             RingPos dr, tr, ar;
             for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
+                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
                 const int a = ar.slot;
                 if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
                 fence_after();
                 const uint32_t dacc = tmem + (uint32_t)a * cfg.acc_cols;
-                const uint32_t idesc = idesc_tf32(kTileLines, s.Np);
+                int n0, nN;
+                tc_unit_cols(t, nfull, s.Np, n0, nN);
+                const uint32_t idesc = idesc_tf32(kTileLines, nN);
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
                     const int ds = cfg.resident ? c : dr.slot, ts = tr.slot;
@@ -570,7 +592,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     // B: the DCT chunk [hi: Np rows][lo: Np rows]; a K step of 8
                     // adds 256 bytes (16 in descriptor units).  A: TMEM columns
                     // of the X slot, hi then lo; a K step adds 8 columns.
-                    const uint64_t ch = sdesc(s_base + (uint32_t)ds * cfg.dslot, 128, 1024);
+                    // rows n0.. of the chunk: 8-row groups are 1024 bytes apart
+                    const uint64_t ch = sdesc(s_base + (uint32_t)ds * cfg.dslot + (uint32_t)(n0 / 8) * 1024u, 128, 1024);
                     const uint64_t cl = ch + (uint32_t)s.Np * 8u;
                     const uint32_t xh = tmem + xcol0 + (uint32_t)ts * kXCols, xl = xh + kBK;
                     const uint32_t en = (c > 0) ? 1u : 0u;   // the tile's first K step overwrites
@@ -606,7 +629,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const int lr = 32 * q + lane;       // line of the tile
         RingPos ar;
         for (long long t = t0; t < total && !*abort; t += dt) {
-            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, t);
+            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
             if (!s.active) continue;
             const Job& J = *s.J;
             const int a = ar.slot;
@@ -619,7 +642,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             long long s_between = 1;
             for (int ax = J.ax1 + 1; ax < J.ax2; ++ax) s_between *= J.F[ax];
             const int F1 = J.F[J.ax1];
-            const int npieces = s.Np / 16;
+            int n0, nN;
+            tc_unit_cols(t, nfull, s.Np, n0, nN);
+            const int npieces = nN / 16;   // accumulator column c holds output k = n0 + c
             const uint32_t tcol = tmem + lane_addr + (uint32_t)a * cfg.acc_cols;
             const bool lv = lr < s.nl;
             if (s.form == 1) {
@@ -632,7 +657,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     tmem_ld16(tcol + 16 * p, v);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const int k = 16 * p + i;
+                        const int k = n0 + 16 * p + i;
                         if (k < s.L) {
                             const float y = scaled ? v[i] * __ldg(srow + k) : v[i];
                             if (lv) Y[g0 + (long long)k * s.post] = y;
@@ -660,7 +685,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     if (scaled) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int k = 16 * p + i;
+                            const int k = n0 + 16 * p + i;
                             v[i] *= (k < s.L) ? __ldg(srow + k) : 0.f;
                         }
                     }
@@ -673,7 +698,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 #pragma unroll
                     for (int m = 0; m < 4; ++m) y[m] = *reinterpret_cast<const float4*>(Ew + (8 * m + rsub) * kEpiPitch + csub);
                     __syncwarp();   // the buffer is rewritten by the next piece
-                    const int c0 = 16 * p + csub;
+                    const int c0 = n0 + 16 * p + csub;
                     const unsigned vm = (colvec && c0 + 3 < s.L) ? rok : 0u;   // lines written as 16-byte groups
                     const long long gb = rbase0 + c0;
 #pragma unroll
@@ -829,15 +854,27 @@ cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, lo
 cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg) {
     if (A.total_tiles <= 0) return cudaSuccess;
     const long long nsm = tc_sm_count();
-    const unsigned grid = (unsigned)(A.total_tiles < nsm ? A.total_tiles : nsm);
-    if (cfg.tn) return cfg.sr >= 2 ? launch_axis_pass_tcn(A, cfg, grid) : cudaErrorInvalidValue;
+    if (cfg.tn) {
+        const unsigned g = (unsigned)(A.total_tiles < nsm ? A.total_tiles : nsm);
+        return cfg.sr >= 2 ? launch_axis_pass_tcn(A, cfg, g) : cudaErrorInvalidValue;
+    }
     if (cfg.smem == 0 || cfg.sd < 2 || cfg.sr < 2 || cfg.st < 2 || cfg.nacc < 1) return cudaErrorInvalidValue;
+    // units: whole tiles, then the tiles of a last round that would occupy at
+    // most half of the SMs as two column halves each (one geometry, N >= 32)
+    const long long T = A.total_tiles;
+    long long nfull = T;
+    if (cfg.geom[0] >= 0 && cfg.acc_need >= 32) {
+        const long long extra = (T <= nsm) ? T : T % nsm;
+        if (extra > 0 && 2 * extra <= nsm) nfull = T - extra;
+    }
+    const long long units = nfull + 2 * (T - nfull);
+    const unsigned grid = (unsigned)(units < nsm ? units : nsm);
     count_launch();
     switch (A.pass) {
-        case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
-        case 1: k_axis_tc<1><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
-        case 2: k_axis_tc<2><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
-        default: k_axis_tc<3><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, A.total_tiles, cfg, A.status); break;
+        case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
+        case 1: k_axis_tc<1><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
+        case 2: k_axis_tc<2><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
+        default: k_axis_tc<3><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
     }
     return cudaGetLastError();
 }

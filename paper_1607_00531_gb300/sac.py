@@ -62,6 +62,7 @@ def lib():
             "sac_workspace_bytes": (sz, [G, P]),
             "sac_objective": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp, sz, vp]),
             "sac_gradient": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, sz, vp]),
+            "sac_corrected_images": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, dp, dp, vp, sz, vp]),
             "sac_objective_noalloc": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp]),
             "sac_objective_noalloc_max_bytes": (sz, []),
             "sac_bstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]),
@@ -201,6 +202,21 @@ def objective(g, p, I1, I2, b, ws=None, stream=None):
     _check("sac_objective", lib().sac_objective(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), out,
                                                 _ptr(ws), ws.numel(), _stream(stream)))
     return dict(J=out[0], D=out[1], S=out[2], P=out[3])
+
+
+def corrected_images(g, p, I1, I2, b, T1=None, T2=None, ws=None, stream=None):
+    """Transformed images T1, T2 (new tensors of the image dtype unless given)
+    and the SSD / NCC similarity (Sec. 6)."""
+    _check_inputs(g, p, I1, I2)
+    ws = _ws(g, p, ws)
+    T1 = _torch().empty_like(I1) if T1 is None else T1
+    T2 = _torch().empty_like(I2) if T2 is None else T2
+    ssd, ncc = ctypes.c_double(0), ctypes.c_double(0)
+    _check("sac_corrected_images",
+           lib().sac_corrected_images(ctypes.byref(g), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), _ptr(T1),
+                                      _ptr(T2), ctypes.byref(ssd), ctypes.byref(ncc), _ptr(ws), ws.numel(),
+                                      _stream(stream)))
+    return dict(T1=T1, T2=T2, ssd=ssd.value, ncc=ncc.value)
 
 
 def objective_noalloc(g, p, I1, I2, b, stream=None):

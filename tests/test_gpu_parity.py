@@ -6,6 +6,8 @@ class (K = 3, 5, 9, 15), and lines with active constraints.  The FP64 path
 must match to 1e-9 relative (Sec. 4.2 ADMM after a fixed number of
 iterations); the mixed path to 1e-3 voxel in b and 1e-6 relative objective.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -212,6 +214,47 @@ def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
     assert abs(J_mix - J_ref) <= 1e-6 * abs(J_ref)
 
 
+# ---------------------------------------------------------------- corrected images, SSD, NCC (Sec. 6)
+
+@pytest.mark.parametrize("m,pe", CASES)
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_corrected_images(sac, m, pe, prec):
+    h, I1, I2, b, _, _ = case_data(m, pe, seed=50, max_d=0.7)
+    ref = oracle.corrected(oracle.Grid(m, h, pe), I1, I2, b)
+    g = sac.grid(m, h, pe)
+    p = sac.params(prec=prec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    out = sac.corrected_images(g, p, cu(I1, dt), cu(I2, dt), cu(b))
+    T1, T2 = out["T1"].double().cpu().numpy(), out["T2"].double().cpu().numpy()
+    if prec == "f64":
+        assert rel(T1, ref["T1"]) < 1e-12 and rel(T2, ref["T2"]) < 1e-12
+        assert out["ssd"] == pytest.approx(ref["ssd"], rel=1e-10)
+        assert out["ncc"] == pytest.approx(ref["ncc"], rel=1e-12)
+    else:
+        # FP32 images and arithmetic: a few ulp of the image scale per cell
+        assert rel(T1, ref["T1"]) < 2e-5 and rel(T2, ref["T2"]) < 2e-5
+        assert out["ssd"] == pytest.approx(ref["ssd"], rel=1e-3)
+        assert out["ncc"] == pytest.approx(ref["ncc"], rel=1e-5)
+
+
+def test_corrected_images_measures_only(sac):
+    # T1 / T2 may be left out; the measures are the same
+    m, pe = (9, 70, 21), 1
+    h, I1, I2, b, _, _ = case_data(m, pe, seed=51)
+    g = sac.grid(m, h, pe)
+    p = sac.params(prec="f64")
+    full = sac.corrected_images(g, p, cu(I1), cu(I2), cu(b))
+    out = (ctypes.c_double(0), ctypes.c_double(0))
+    ws = sac.workspace(g, p)
+    dI1, dI2, db = cu(I1), cu(I2), cu(b)
+    st = sac.lib().sac_corrected_images(ctypes.byref(g), ctypes.byref(p), dI1.data_ptr(), dI2.data_ptr(),
+                                        db.data_ptr(), None, None, ctypes.byref(out[0]), ctypes.byref(out[1]),
+                                        ws.data_ptr(), ws.numel(), None)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert out[0].value == full["ssd"] and out[1].value == full["ncc"]
+
+
 # ---------------------------------------------------------------- b-step segment kernel (mixed path)
 
 # strided PE lines: 9 faces per segment up to 144 faces, 17 up to 272; line
@@ -277,6 +320,8 @@ TC_CASES = [
     ((64, 30, 48), 1),      # 16-byte vector paths: post = 1488, last axis 48
     ((160, 11, 20), 1),     # two 128-row blocks with vector stores (post = 240)
     ((80, 255, 24), 1),     # more tiles than SMs on the last axis (20480 lines)
+    ((6, 10, 200), 1),      # contiguous axis of 200 faces: one tile as two column halves
+    ((136, 150, 130), 1),   # 154 and 161 tiles: full tiles, then the last round as column halves
 ]
 
 
