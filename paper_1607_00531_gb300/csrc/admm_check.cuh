@@ -18,6 +18,8 @@ struct AdmmCheck {
     double* stats;       // per job 8 doubles: r_pri, r_dual, eps_pri, eps_dual, iterations, converged, non-finite
     int* nactive;        // jobs still running: set to the number of jobs by the host, one
                          // less for every job the test retires
+    int* rcount;         // fused form: counters zeroed by the update for the next
+    int nrcount;         // iteration's b-step (null: none)
 };
 
 // Thread 0 applies the test to the job's totals and retires the job (active

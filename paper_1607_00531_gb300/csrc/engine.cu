@@ -404,7 +404,9 @@ void Engine::prof_mark(int slot, int phase, int end) {
 
 int Engine::enqueue_iteration(int slot) {
     const bool mixed = (p_.prec == SAC_MIXED);
-    ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * kMaxCls, st_));
+    // the b-step's list counters: zeroed by the previous iteration's update
+    // kernel (tensor-core z-step; also at creation), else here
+    if (!use_tc_) ENG_CUDA(cudaMemsetAsync(d_rcount_, 0, sizeof(int) * kMaxCls, st_));
     for (int pass = 0; pass < 2; ++pass) {
     prof_mark(slot, pass, 0);
     for (size_t c = 0; c < cls_.size(); ++c) {
@@ -472,6 +474,7 @@ int Engine::enqueue_iteration(int slot) {
         count_launch();
         AdmmCheck chk = check_args();
         chk.counters = nullptr;
+        chk.rcount = nullptr;
         k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, d_pref_ax_[3], d_part_, chk);
         ENG_CUDA(cudaGetLastError());
     }

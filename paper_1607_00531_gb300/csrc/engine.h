@@ -105,6 +105,8 @@ private:
         c.max_iter = p_.max_iter;
         c.stats = d_stats_;
         c.nactive = d_nactive_;
+        c.rcount = d_rcount_;
+        c.nrcount = kMaxCls;
         return c;
     }
     int* d_status_ = nullptr;

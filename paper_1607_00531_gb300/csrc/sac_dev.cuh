@@ -50,7 +50,7 @@ struct Job {
     int pad_;
     int tc_T[4];       // tensor-core z-step: lines per tile of each pass
     const void* tmaps; // tensor-core z-step: TMA tensor maps of the X sources, [pass][source]
-    int tc_tma;        // bit q: pass q loads X with the tensor maps
+    int tc_tma;        // bit q: pass q loads X with the tensor maps; bit 4 + q: pass q stores with one
     int pad2_;
 };
 

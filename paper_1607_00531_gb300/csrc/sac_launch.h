@@ -141,11 +141,12 @@ struct TcCfg {
     int tn = 0;                      // 1: the lines-in-N kernel (zstep_tcn.cu), sr = its ring stages
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
-constexpr int kTcMaps = 8;           // TMA tensor maps per job: [pass][source]
+constexpr int kTcMaps = 12;          // TMA tensor maps per job: [pass][source] X sources, then [pass] outputs
 size_t tc_map_bytes();
 // Host: encode the tensor maps of a job (FP32 device arrays b, u, t1, t2)
-// into `out` (tc_map_bytes() bytes, host memory); returns the mask of passes
-// that can load X with them
+// into `out` (tc_map_bytes() bytes, host memory); returns a mask: bit q, pass
+// q loads X with the maps; bit 4 + q, pass q (strided axis) writes its output
+// with a map
 int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float* u, const float* t1,
                    const float* t2, void* out);
 // After the tensor-core passes (z^{k+1} in t2): u <- u + b - t2, z <- t2 and

@@ -82,7 +82,11 @@ constexpr int kMaxDStages = 4, kMaxRStages = 6, kMaxTStages = 4;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kXCols = 2 * kBK;               // TMEM columns of an X chunk slot
 constexpr int kEpiPitch = 20;                      // floats per row of an epilogue transpose buffer
-constexpr uint32_t kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
+constexpr uint32_t kEpiStage = 16 * 32 * 4;        // strided-line output piece: 16 k x 32 lines
+// per epilogue warp: a transpose buffer (contiguous lines) or two staged
+// output pieces (strided lines, written by TMA tensor stores)
+constexpr uint32_t kEpiWarpBytes = (2 * kEpiStage > 32 * kEpiPitch * 4) ? 2 * kEpiStage : 32 * kEpiPitch * 4;
+constexpr uint32_t kEpiBytes = kEpiWarps * kEpiWarpBytes;
 
 using namespace tcx;
 
@@ -238,10 +242,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
 size_t tc_map_bytes() { return (size_t)kTcMaps * sizeof(CUtensorMap); }
 
 // Host: tensor maps of the X sources of every pass of one job into `out`
-// (kTcMaps maps: [pass][source]; FP32 device arrays b, u, t1, t2 of the
-// job's faces).  Box: 32 values of j x 128 lines.  Returns the mask of
-// passes whose sources have maps; a pass without one (strides not
-// multiples of 16 bytes) loads X without TMA.
+// (kTcMaps maps: [pass][source], then the outputs [pass]; FP32 device arrays
+// b, u, t1, t2 of the job's faces).  Source box: 32 values of j x 128 lines.
+// Returns the mask of passes whose sources have maps (bit q; a pass without
+// one, strides not multiples of 16 bytes, loads X without TMA) and of the
+// strided-axis passes whose output has one (bit 4 + q; otherwise the
+// epilogue stores directly).
 int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float* u, const float* t1,
                    const float* t2, void* out) {
     static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
@@ -288,6 +294,19 @@ int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float
             if (r != CUDA_SUCCESS) ok = false;
         }
         if (ok) mask |= 1 << q;
+        // output of a strided-axis pass: [pre][L][post], box 32 (po) x 16 (k) x 1,
+        // written by TMA tensor stores from the epilogue's staging buffers
+        const float* dst = (q == 0 || q == 2) ? t1 : t2;
+        if (!g.caseB && dst && (((uintptr_t)dst) & 15) == 0 && g.post % 4 == 0) {
+            const cuuint32_t es[3] = {1, 1, 1};
+            const cuuint64_t dim[3] = {(cuuint64_t)g.post, (cuuint64_t)g.L, (cuuint64_t)g.pre};
+            const cuuint64_t str[2] = {(cuuint64_t)g.post * 4, (cuuint64_t)g.post * g.L * 4};
+            const cuuint32_t box[3] = {32, 16, 1};
+            if (enc(&maps[8 + q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)dst, dim, str, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                mask |= 1 << (4 + q);
+        }
     }
     return mask;
 }
@@ -303,7 +322,7 @@ struct TcTile {
     long long post;
     long long line0;   // form 0: first line
     long long pr, po0; // form 1: line-view break and first po
-    bool active, tma;
+    bool active, tma, ytma;   // X / output through TMA tensor copies
 };
 
 __device__ __forceinline__ TcTile tc_tile(const Job* __restrict__ jobs, int njobs,
@@ -336,6 +355,7 @@ __device__ __forceinline__ TcTile tc_tile(const Job* __restrict__ jobs, int njob
     }
     s.active = J.active != 0;
     s.tma = (J.tc_tma >> pass) & 1;
+    s.ytma = (J.tc_tma >> (4 + pass)) & 1;
     return s;
 }
 
@@ -627,6 +647,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const int h = ew >> 2;              // half: even or odd column pieces
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
         const int lr = 32 * q + lane;       // line of the tile
+        int ybuf = 0;                       // staging buffer of the next TMA tensor store
         RingPos ar;
         for (long long t = t0; t < total && !*abort; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
@@ -647,7 +668,35 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const int npieces = nN / 16;   // accumulator column c holds output k = n0 + c
             const uint32_t tcol = tmem + lane_addr + (uint32_t)a * cfg.acc_cols;
             const bool lv = lr < s.nl;
-            if (s.form == 1) {
+            if (s.form == 1 && s.ytma) {
+                // thread = line: a piece of 16 k x the warp's 32 lines is
+                // staged as [k][line] (128 contiguous bytes per k) and written
+                // by one TMA tensor store (box 32 x 16 x 1); two staging
+                // buffers per warp, a buffer is rewritten once the store
+                // issued from it two pieces earlier has read it
+                const char* ymap = (const char*)J.tmaps + (size_t)(8 + PASS) * 128;
+                const float* __restrict__ srow = J.scale;
+                if (PASS == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
+                float* stage0 = reinterpret_cast<float*>(smem_raw + cfg.epi_off + ew * kEpiWarpBytes);
+                for (int p = h; p < npieces; p += 2) {
+                    float v[16];
+                    tmem_ld16(tcol + 16 * p, v);
+                    const int k0 = n0 + 16 * p;
+                    if (scaled) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] *= (k0 + i < s.L) ? __ldg(srow + k0 + i) : 0.f;
+                    }
+                    if (lane == 0) bulk_wait_read1();
+                    __syncwarp();
+                    float* st = stage0 + ybuf * (kEpiStage / 4);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) st[i * 32 + lane] = v[i];
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tma_store3d(ymap, smem_u32(st), (int)s.po0 + 32 * q, k0, (int)s.pr);
+                    ybuf ^= 1;
+                }
+            } else if (s.form == 1) {
                 // thread = line; for each k the warp's 32 lines are 128 contiguous bytes
                 const long long g0 = s.pr * s.L * s.post + s.po0 + lr;
                 const float* __restrict__ srow = J.scale;
@@ -669,7 +718,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 // its row into the warp's transpose buffer; then lane i handles
                 // lines 8m + i / 4 (m = 0..3), k = 4 (i % 4) .. +3: eight lines
                 // x 64 bytes per memory instruction.
-                float* Ew = reinterpret_cast<float*>(smem_raw + cfg.epi_off) + ew * 32 * kEpiPitch;
+                float* Ew = reinterpret_cast<float*>(smem_raw + cfg.epi_off + ew * kEpiWarpBytes);
                 const int rsub = lane >> 2, csub = 4 * (lane & 3);
                 const float* __restrict__ srow = J.scale;
                 if (PASS == 1) srow = J.scale + (long long)(((s.line0 + lr) / s_between) % F1) * L2s;
@@ -720,6 +769,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             if (lane == 0) mbar_arrive(b_aempty + 8 * a);
             ar.next(cfg.nacc);
         }
+        // TMA tensor stores complete before the CTA's shared memory goes away
+        if (lane == 0) bulk_wait_all();
     }
 
     fence_before();
@@ -756,6 +807,7 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
                                                               double* __restrict__ part, AdmmCheck chk) {
     __shared__ double red[32 * 5];
     __shared__ int last;
+    if (chk.rcount && blockIdx.x == 0 && threadIdx.x < chk.nrcount) chk.rcount[threadIdx.x] = 0;
     const long long blk = blockIdx.x;
     const int jid = find_job(prefix, njobs, blk);
     Job& J = jobs[jid];
@@ -825,12 +877,15 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
     if (threadIdx.x < 5) {
         float v = 0.f;
         for (int w = 0; w < kAdmmThreads / 32; ++w) v += redf[w * 5 + threadIdx.x];
-        if (chk.counters) reinterpret_cast<float*>(part)[blk * 5 + threadIdx.x] = v;
-        else part[blk * 5 + threadIdx.x] = (double)v;
+        if (chk.counters) {
+            reinterpret_cast<float*>(part)[blk * 5 + threadIdx.x] = v;
+            __threadfence();   // the partial set is visible before the block is counted
+        } else {
+            part[blk * 5 + threadIdx.x] = (double)v;
+        }
     }
     if (!chk.counters || !active) return;
     // the last block of the job runs the job's stopping test
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nb = (int)(prefix[jid + 1] - prefix[jid]);
