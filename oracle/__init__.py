@@ -83,7 +83,8 @@ class RefParams(ctypes.Structure):
                 ("alpha", "beta", "gamma", "rho", "eps_abs", "eps_rel", "eta", "eps_obj",
                  "eps_iter", "eps_grad", "gn_rel_grad")] + \
                [(n, ctypes.c_int) for n in
-                ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "nthreads")]
+                ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "nthreads", "adapt_rho")] + \
+               [(n, ctypes.c_double) for n in ("rho_min", "rho_tau", "rho_mu")]
 
 
 @dataclass
@@ -111,6 +112,10 @@ class Params:
     precond: int = 2
     max_gn: int = 10
     nthreads: int = 0
+    adapt_rho: int = 0          # 0 fixed, 1 adaptive (Boyd et al.), 2 adaptive with lower bound
+    rho_min: float = 1e2
+    rho_tau: float = 1.3
+    rho_mu: float = 10.0
 
     def c(self) -> RefParams:
         return RefParams(**{f.name: getattr(self, f.name) for f in fields(self)})

@@ -56,6 +56,8 @@ typedef struct {
     double eps_abs, eps_rel;
     double eta, eps_obj, eps_iter, eps_grad, gn_rel_grad;
     int max_iter, n_sqp, max_pcg, precond, max_gn, nthreads;
+    int adapt_rho;                /* 0 fixed rho, 1 adaptive, 2 adaptive with lower bound */
+    double rho_min, rho_tau, rho_mu;
 } ref_params;
 
 enum { REF_OK = 0, REF_NOTCONV = 1, REF_EINVAL = -1, REF_EINFEASIBLE = -4, REF_ELSFAIL = -7 };
@@ -819,6 +821,17 @@ double ref_max_abs_d1(int nd, const int* m, const double* h, int pe, const doubl
 /* (reading: the k+1 iterates, as in Boyd et al. (3.12)).                    */
 /* hist (optional): 6 doubles per iteration:                                 */
 /*   r_pri, r_dual, eps_pri, eps_dual, rho, J(b^{k+1}).                      */
+/*                                                                           */
+/* Augmentation parameter (Sec. 4.3, last paragraph; Sec. 6, ADMM            */
+/* performance): fixed, or the adaptive choice of Boyd et al. (varying       */
+/* penalty parameter), or that choice kept above a lower bound rho_min.      */
+/* Readings (the paper gives no formula): after an iteration that did not    */
+/* stop, rho <- tau rho when r_pri > mu r_dual, rho <- rho / tau when        */
+/* r_dual > mu r_pri (with the bound: not when rho / tau < rho_min, rho then */
+/* stays), else unchanged; tau = 1.3 (the factor between consecutive rho in  */
+/* the paper's figure), mu = 10 (Boyd's usual value).  On a change the       */
+/* scaled dual is rescaled, u <- u rho_old / rho_new, so that y = rho u is   */
+/* unchanged.                                                                */
 /* info[0] = iterations, info[1] = converged flag, info[2] = capped QPs.     */
 /* ------------------------------------------------------------------------ */
 int ref_admm(int nd, const int* m, const double* h, int pe, const ref_params* prm,
@@ -834,27 +847,41 @@ int ref_admm(int nd, const int* m, const double* h, int pe, const ref_params* pr
     long capped_total = 0;
     int conv = 0;
     long k;
+    ref_params pk = *prm;   /* pk.rho: the current augmentation parameter */
     for (k = 0; k < prm->max_iter; ++k) {
         long stats[3];
-        ref_bstep(nd, m, h, pe, prm, I1, I2, b, z, u, b, stats);
+        ref_bstep(nd, m, h, pe, &pk, I1, I2, b, z, u, b, stats);
         capped_total += stats[0];
         memcpy(zold, z, sizeof(double) * (size_t)n);
-        ref_zstep(nd, m, h, pe, prm, b, u, z);
+        ref_zstep(nd, m, h, pe, &pk, b, u, z);
         for (long f = 0; f < n; ++f) u[f] += b[f] - z[f];
         for (long f = 0; f < n; ++f) tmp[f] = b[f] - z[f];
         double rpri = norm2(n, tmp);
         for (long f = 0; f < n; ++f) tmp[f] = z[f] - zold[f];
-        double rdual = prm->rho * g.hd * norm2(n, tmp);
+        double rdual = pk.rho * g.hd * norm2(n, tmp);
         double nb = norm2(n, b), nz = norm2(n, z), nu = norm2(n, u);
         double epri = sqrt((double)n) * prm->eps_abs + prm->eps_rel * (nb > nz ? nb : nz);
-        double edual = sqrt((double)n) * prm->eps_abs + prm->eps_rel * prm->rho * g.hd * nu;
+        double edual = sqrt((double)n) * prm->eps_abs + prm->eps_rel * pk.rho * g.hd * nu;
         if (hist) {
             double obj[4];
-            ref_objective(nd, m, h, pe, prm, I1, I2, b, obj);
+            ref_objective(nd, m, h, pe, &pk, I1, I2, b, obj);
             double* hk = hist + 6 * k;
-            hk[0] = rpri; hk[1] = rdual; hk[2] = epri; hk[3] = edual; hk[4] = prm->rho; hk[5] = obj[0];
+            hk[0] = rpri; hk[1] = rdual; hk[2] = epri; hk[3] = edual; hk[4] = pk.rho; hk[5] = obj[0];
         }
         if (rpri <= epri && rdual <= edual) { conv = 1; ++k; break; }
+        if (prm->adapt_rho) {
+            double rnew = pk.rho;
+            if (rpri > prm->rho_mu * rdual) {
+                rnew = pk.rho * prm->rho_tau;
+            } else if (rdual > prm->rho_mu * rpri) {
+                rnew = pk.rho / prm->rho_tau;
+                if (prm->adapt_rho == 2 && rnew < prm->rho_min) rnew = pk.rho;
+            }
+            if (rnew != pk.rho) {
+                for (long f = 0; f < n; ++f) u[f] *= pk.rho / rnew;
+                pk.rho = rnew;
+            }
+        }
     }
     free(zold); free(tmp);
     if (info) { info[0] = k; info[1] = conv; info[2] = capped_total; }

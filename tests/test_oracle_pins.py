@@ -477,6 +477,60 @@ def test_admm_dual_equals_regulariser_gradient_after_every_iteration():
                                    atol=1e-11 * np.abs(prm.alpha * lap).max())
 
 
+def _next_rho(prm, rho, rp, rd):
+    # the adaptive rule as stated in the design notes (Boyd et al.'s varying
+    # penalty, optionally bounded below)
+    if rp > prm.rho_mu * rd:
+        return rho * prm.rho_tau
+    if rd > prm.rho_mu * rp:
+        r = rho / prm.rho_tau
+        return rho if (prm.adapt_rho == 2 and r < prm.rho_min) else r
+    return rho
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_adaptive_rho_sequence_and_rescaled_dual(mode):
+    # rho follows the rule from the recorded residuals, and the rescaled dual
+    # keeps y = rho u = alpha (D2^T D2 + D3^T D3) z (Lemma zdescent) through
+    # every change of rho
+    m, pe = (8, 10, 6), 1
+    w = ph.small_workload(m, pe, seed=5)
+    d = ph.make_pair(w)
+    g = oracle.Grid(d["m"], d["h"], d["pe"])
+    Z = np.zeros(m)
+    for k in (1, 3, 12):
+        prm = oracle.Params(alpha=2.0, rho=1e6, max_iter=k, eps_abs=0.0, eps_rel=0.0, adapt_rho=mode,
+                            rho_min=1e5)
+        r = oracle.admm(g, prm, d["I1"], d["I2"], np.zeros(g.face_shape), want_hist=True)
+        hs = r["hist"]
+        rho = prm.rho
+        for it in range(k):
+            assert hs[it, 4] == rho
+            rho = _next_rho(prm, rho, hs[it, 0], hs[it, 1])
+        if mode == 2:
+            assert np.all(hs[:, 4] >= prm.rho_min)
+        lap = oracle.apply(g, prm, "D2tD2", Z, Z, r["z"], r["z"]) + oracle.apply(g, prm, "D3tD3", Z, Z, r["z"], r["z"])
+        np.testing.assert_allclose(rho * r["u"], prm.alpha * lap, rtol=1e-8,
+                                   atol=1e-10 * np.abs(prm.alpha * lap).max())
+    # from rho = 1e6 the primal residual is tiny: rho falls by tau per iteration
+    # (1e6, 769 230.77, ...) until the bound stops it (mode 2)
+    assert hs[1, 4] == pytest.approx(1e6 / 1.3, rel=1e-15)
+    if mode == 2:
+        assert hs[-1, 4] >= 1e5 and hs[-1, 4] / 1.3 < 1e5
+
+
+def test_adaptive_rho_that_never_fires_is_the_fixed_method():
+    m, pe = (8, 10, 6), 1
+    w = ph.small_workload(m, pe, seed=6)
+    d = ph.make_pair(w)
+    g = oracle.Grid(d["m"], d["h"], d["pe"])
+    fixed = oracle.admm(g, oracle.Params(alpha=2.0, rho=50.0, max_iter=6, eps_abs=0.0, eps_rel=0.0),
+                        d["I1"], d["I2"], np.zeros(g.face_shape))
+    never = oracle.admm(g, oracle.Params(alpha=2.0, rho=50.0, max_iter=6, eps_abs=0.0, eps_rel=0.0, adapt_rho=1,
+                                         rho_mu=1e300), d["I1"], d["I2"], np.zeros(g.face_shape))
+    assert np.array_equal(fixed["b"], never["b"]) and np.array_equal(fixed["u"], never["u"])
+
+
 def test_zstep_decreases_augmented_lagrangian():
     # Lemma zdescent: L(b, z^k, y) - L(b, z^{k+1}, y) >= rho h^d / 2 ||z^k - z^{k+1}||^2
     m, pe = (6, 7, 5), 1
