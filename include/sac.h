@@ -104,6 +104,13 @@ typedef struct {
                             (line, segment of 9 or 17 faces) where the PE lines
                             are strided and have at most 272 faces, else one
                             warp per line; 1 always one warp per line */
+    int adapt_rho;       /* augmentation parameter (Sec. 4.3, Sec. 6): 0 fixed rho;
+                            1 adaptive (varying penalty of Boyd et al.): after an
+                            iteration that did not stop, rho *= rho_tau when
+                            r_pri > rho_mu r_dual, rho /= rho_tau when r_dual >
+                            rho_mu r_pri; 2 the same without going below rho_min.
+                            The scaled dual u is rescaled by rho_old / rho_new. */
+    double rho_min, rho_tau, rho_mu;   /* defaults 1e2, 1.3, 10 */
 } sac_params;
 
 void sac_params_default(sac_params* p);

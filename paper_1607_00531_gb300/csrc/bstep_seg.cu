@@ -83,7 +83,8 @@ template <int S, bool kIn>
 __device__ __forceinline__ void forward(const float* __restrict__ rI1, const float* __restrict__ rI2,
                                         const float* __restrict__ rB, const float* __restrict__ rZ,
                                         const float* __restrict__ rU, int m, int s, float inv_h, float ih2,
-                                        float alpha, float rho, float (&A)[S], float (&C)[S], float (&R)[S]) {
+                                        float alpha, float rho, float us, float (&A)[S], float (&C)[S],
+                                        float (&R)[S]) {
     const float bprev = (kIn || s >= 1) ? rB[(s - 1) * kLines] : 0.f;
     float bcur = rB[s * kLines];
     Cell prev = cell<kIn>(rI1, rI2, m, s - 1, bprev, bcur, inv_h);
@@ -95,7 +96,7 @@ __device__ __forceinline__ void forward(const float* __restrict__ rI1, const flo
         float dg = 1.f, sub = 0.f, sup = 0.f, rhs = 0.f;
         if (kIn || i <= m) {
             const float nadj = kIn ? 2.f : (float)((i > 0) + (i < m));
-            const float zu = rU[i * kLines] - rZ[i * kLines];
+            const float zu = us * rU[i * kLines] - rZ[i * kLines];
             dg = prev.Ju * prev.Ju + cur.Jd * cur.Jd + alpha * nadj * ih2 + rho;
             sup = (kIn || i < m) ? cur.Jd * cur.Ju - alpha * ih2 : 0.f;
             sub = (kIn || i > 0) ? prev.Jd * prev.Ju - alpha * ih2 : 0.f;
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
     const long long L = L0 + lane;
     const bool valid = L < nlines;   // rows of lanes past the last line are not staged
     const float h = (float)J.hpe, inv_h = 1.f / h, ih2 = inv_h * inv_h;
-    const float alpha = (float)J.alpha, rho = (float)J.rho;
+    const float alpha = (float)J.alpha, rho = (float)J.rho, us = (float)J.uscale;
     const bool on = gi < G && valid;
     const int s = g * S;
     const float* rI1 = sI1 + lane;
@@ -229,9 +230,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
     float A[S], C[S], R[S];    // eliminated rows of the segment
     if (on) {
         if (s >= 1 && s + S <= m)
-            forward<S, true>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, A, C, R);
+            forward<S, true>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
         else
-            forward<S, false>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, A, C, R);
+            forward<S, false>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
         // rows S-3 .. 1 rewritten as x_k + A_k x_0 + C_k x_{S-1} = R_k
 #pragma unroll
         for (int k = S - 3; k >= 1; --k) {

@@ -153,6 +153,8 @@ int check_params(const sac_params* p) {
     if (!(p->near_bound >= 0)) return SAC_EINVAL;
     if (p->zstep_kernel < 0 || p->zstep_kernel > 1) return SAC_EINVAL;
     if (p->bstep_kernel < 0 || p->bstep_kernel > 1) return SAC_EINVAL;
+    if (p->adapt_rho < 0 || p->adapt_rho > 2) return SAC_EINVAL;
+    if (p->adapt_rho && (!(p->rho_tau > 1.0) || !(p->rho_mu > 0.0) || !(p->rho_min > 0.0))) return SAC_EINVAL;
     return SAC_OK;
 }
 
@@ -236,6 +238,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t o_C2f = take(sizeof(float) * (size_t)L2 * L2);
     size_t o_l1 = take(sizeof(double) * (size_t)L1);
     size_t o_l2 = take(sizeof(double) * (size_t)L2);
+    size_t o_l1f = take(sizeof(float) * (size_t)L1);
+    size_t o_l2f = take(sizeof(float) * (size_t)L2);
     size_t o_scale = take(sizeof(float) * (size_t)L1 * L2);
     size_t o_tc[4];
     for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
@@ -271,6 +275,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->d_C2f = (float*)(base + o_C2f);
     P->d_lam1 = (double*)(base + o_l1);
     P->d_lam2 = (double*)(base + o_l2);
+    P->d_lam1f = (float*)(base + o_l1f);
+    P->d_lam2f = (float*)(base + o_l2f);
     for (int i = 0; i < 10; ++i) P->arr[i] = (double*)(base + o_arr[i]);
     return SAC_OK;
 }
@@ -293,6 +299,8 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     J.C1 = f32 ? (const void*)P->d_C1f : (const void*)P->d_C1;
     J.C2 = f32 ? (const void*)P->d_C2f : (const void*)P->d_C2;
     J.lam1 = P->d_lam1; J.lam2 = P->d_lam2;
+    J.lam1f = P->d_lam1f; J.lam2f = P->d_lam2f;
+    J.uscale = 1.0;
     J.part = P->d_part;
     for (int q = 0; q < 4; ++q) J.Ctc[q] = P->d_Ctc[q];
     for (int q = 0; q < 4; ++q) J.Ctn[q] = P->d_Ctn[q];
@@ -353,6 +361,11 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     SAC_CUDA(cudaMemcpyAsync(P->d_C2f, C2f.data(), C2f.size() * 4, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_lam1, l1.data(), l1.size() * 8, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_lam2, l2.data(), l2.size() * 8, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<float> l1f(l1.begin(), l1.end()), l2f(l2.begin(), l2.end());
+        SAC_CUDA(cudaMemcpyAsync(P->d_lam1f, l1f.data(), l1f.size() * 4, cudaMemcpyHostToDevice, st));
+        SAC_CUDA(cudaMemcpyAsync(P->d_lam2f, l2f.data(), l2f.size() * 4, cudaMemcpyHostToDevice, st));
+    }
     SAC_CUDA(cudaMemsetAsync(P->d_status, 0, 256, st));
     // the host copies above read pageable memory: the runtime has consumed it on return
     return SAC_OK;
@@ -558,6 +571,10 @@ void sac_params_default(sac_params* p) {
     p->check_every = 1;
     p->zstep_kernel = 0;
     p->bstep_kernel = 0;
+    p->adapt_rho = 0;
+    p->rho_min = 1e2;
+    p->rho_tau = 1.3;
+    p->rho_mu = 10.0;
 }
 
 int sac_version(void) { return SAC_VERSION; }
@@ -728,10 +745,11 @@ int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const
     } else {
         SAC_TRY(plan_upload(&P, p, I1, I2, b, zd, ud, P.arr[3], P.arr[4], st));
     }
-    const double sqn = sqrt((double)nf), rhd = p->rho * P.G.hd;
-    const int every = p->check_every > 0 ? p->check_every : 1;
+    // the adaptive augmentation parameter needs the residuals of every iteration
+    const int every = p->adapt_rho ? 1 : (p->check_every > 0 ? p->check_every : 1);
     int k = 0, conv = 0;
-    double rp = 0.0, rd = 0.0;
+    double rp = 0.0, rd = 0.0, rho = p->rho, us_dev = 1.0;
+    char* dj = (char*)P.d_job;
     for (k = 0; k < p->max_iter;) {
         SAC_TRY(bstep_dev(P, p, st));
         SAC_TRY(zstep_passes(P, st));
@@ -739,17 +757,33 @@ int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const
         if (k % every == 0 || k == p->max_iter) {
             double s[5];
             SAC_TRY(read_back(s, P.d_out + 16, sizeof(s), st));
-            rp = sqrt(s[0]);
-            rd = rhd * sqrt(s[1]);
-            const double nb = sqrt(s[2]), nz = sqrt(s[3]), nu = sqrt(s[4]);
-            const double ep = sqn * p->eps_abs + p->eps_rel * (nb > nz ? nb : nz);
-            const double ed = sqn * p->eps_abs + p->eps_rel * rhd * nu;
+            // the batched engine's arithmetic (admm_norms), so that a volume
+            // stops and adapts rho alike alone and in a batch
+            const AdmmNorms nr = admm_norms(s, rho, P.G.hd, nf, p->eps_abs, p->eps_rel);
+            rp = nr.rp;
+            rd = nr.rd;
+            const double ep = nr.ep, ed = nr.ed;
             if (hist) {
                 double* hk = hist + 6 * (k - 1);
-                hk[0] = rp; hk[1] = rd; hk[2] = ep; hk[3] = ed; hk[4] = p->rho; hk[5] = 0.0;
+                hk[0] = rp; hk[1] = rd; hk[2] = ep; hk[3] = ed; hk[4] = rho; hk[5] = 0.0;
             }
             if (!(rp == rp) || !(rd == rd)) return SAC_ENAN;
             if (rp <= ep && rd <= ed) { conv = 1; break; }
+            if (p->adapt_rho) {
+                // next rho; the dual is rescaled lazily by the next iteration's
+                // readers of u (Job::uscale), the z-step scale table rebuilt
+                const double rn = adapt_rho_next(p->adapt_rho, rho, rp, rd, p->rho_min, p->rho_tau, p->rho_mu);
+                const double us = rho / rn;
+                if (us != us_dev) {
+                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, uscale), &us, sizeof(double), cudaMemcpyHostToDevice, st));
+                    us_dev = us;
+                }
+                if (rn != rho) {
+                    rho = rn;
+                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, rho), &rn, sizeof(double), cudaMemcpyHostToDevice, st));
+                    SAC_CUDA(launch_rebuild_scale(P.d_job, st));
+                }
+            }
         }
     }
     if (mixed) {

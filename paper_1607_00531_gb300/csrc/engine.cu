@@ -52,7 +52,7 @@ void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W) {
 // ---------------------------------------------------------------- per-job state block
 struct StateLayout {
     size_t b32, z, u, t1, t2;          // face arrays
-    size_t C1, C2, C1f, C2f, l1, l2, scale, tc[4], tn[4], tmap;
+    size_t C1, C2, C1f, C2f, l1, l2, l1f, l2f, scale, tc[4], tn[4], tmap;
     size_t bytes;
 };
 
@@ -73,6 +73,8 @@ static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
     s.C2f = take(4 * (size_t)L2 * L2);
     s.l1 = take(8 * (size_t)L1);
     s.l2 = take(8 * (size_t)L2);
+    s.l1f = take(4 * (size_t)L1);
+    s.l2f = take(4 * (size_t)L2);
     s.scale = take(4 * (size_t)L1 * L2);
     for (int q = 0; q < 4; ++q)
         s.tc[q] = take(use_tc ? 4 * (size_t)tc_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
@@ -317,6 +319,10 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         J.C2 = (prec == SAC_MIXED) ? (const void*)(s + L.C2f) : (const void*)(s + L.C2);
         J.lam1 = (const double*)(s + L.l1);
         J.lam2 = (const double*)(s + L.l2);
+        J.lam1f = (const float*)(s + L.l1f);
+        J.lam2f = (const float*)(s + L.l2f);
+        if (E.rho0 > 0.0) J.rho = E.rho0;
+        J.uscale = E.uscale0;
         J.scale = (const float*)(s + L.scale);
         for (int q = 0; q < 4; ++q) J.Ctc[q] = use_tc_ ? (const void*)(s + L.tc[q]) : nullptr;
         for (int q = 0; q < 4; ++q)
@@ -341,6 +347,9 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
             neumann_eigs(L1, G.h[G.ax1], l1.data());
             neumann_eigs(L2, G.h[G.ax2], l2.data());
             std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end()), sc((size_t)L1 * L2);
+            std::vector<float> l1f(l1.begin(), l1.end()), l2f(l2.begin(), l2.end());
+            ENG_CUDA(cudaMemcpyAsync(s + L.l1f, l1f.data(), l1f.size() * 4, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.l2f, l2f.data(), l2f.size() * 4, cudaMemcpyHostToDevice, st));
             for (int a = 0; a < L1; ++a)
                 for (int c = 0; c < L2; ++c) sc[(size_t)a * L2 + c] = (float)(p.rho / (p.alpha * (l1[a] + l2[c]) + p.rho));
             ENG_CUDA(cudaMemcpyAsync(s + L.C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
@@ -633,6 +642,8 @@ int Engine::stats(std::vector<EngineStats>* out) {
         S.iters = (int)r[4];
         S.converged = r[5] != 0.0;
         S.done = !hj[i].active;
+        S.rho = hj[i].rho;
+        S.uscale = hj[i].uscale;
     }
     return SAC_OK;
 }

@@ -28,6 +28,8 @@ struct EngineJob {
     int K;               // faces per lane class
     int fresh = 1;       // 1: initialise the state (z = b, u = 0) and the tables
     int iters0 = 0;      // iterations already done (continuing jobs)
+    double rho0 = 0.0;   // continuing jobs: current rho (<= 0: the parameters' rho) and
+    double uscale0 = 1.0;   // the scaled dual's pending rescale factor
     // filled by the engine
     long long nlines;
 };
@@ -37,6 +39,7 @@ struct EngineStats {     // per job, host copy
     int converged;
     int done;
     double r_pri, r_dual, eps_pri, eps_dual;
+    double rho, uscale;  // current augmentation parameter, pending dual rescale factor
 };
 
 class Engine {
@@ -107,6 +110,10 @@ private:
         c.nactive = d_nactive_;
         c.rcount = d_rcount_;
         c.nrcount = kMaxCls;
+        c.adapt = p_.adapt_rho;
+        c.rho_min = p_.rho_min;
+        c.rho_tau = p_.rho_tau;
+        c.rho_mu = p_.rho_mu;
         return c;
     }
     int* d_status_ = nullptr;

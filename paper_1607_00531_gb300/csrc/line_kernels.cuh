@@ -351,7 +351,7 @@ __device__ bool bstep_line(const Job& J, int n_sqp, double near_bound, const S* 
         const int i = lane * K + k;
         if (i <= m) {
             bv[k] = T(rowB[i]);
-            zu[k] = T(rowU[i]) - T(rowZ[i]);   // u - z
+            zu[k] = T(J.uscale) * T(rowU[i]) - T(rowZ[i]);   // u - z (u rescaled after a change of rho)
         } else {
             bv[k] = T(0); zu[k] = T(0);
         }
@@ -435,7 +435,7 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
         const int i = lane * K + k;
         if (i <= m) {
             bv[k] = T(rowB[i]);
-            zu[k] = T(rowU[i]) - T(rowZ[i]);
+            zu[k] = T(J.uscale) * T(rowU[i]) - T(rowZ[i]);
         } else {
             bv[k] = T(0); zu[k] = T(0);
         }

@@ -98,6 +98,7 @@ extern "C" int sac_objective_noalloc(const sac_grid* g, const sac_params* p, con
     J.hd = G.hd; J.hpe = G.hpe;
     J.alpha = p->alpha; J.rho = p->rho; J.beta = p->beta; J.gamma = p->gamma;
     J.I1 = I1; J.I2 = I2; J.b = (void*)b;
+    J.uscale = 1.0;
     J.active = 1;
     const long long pref[4] = {0, P.line_tiles, 0, P.elem_blocks};
     if (cudaMemcpyAsync(P.d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st) != cudaSuccess ||

@@ -64,6 +64,7 @@ struct Plan {
     double* d_part;
     long long n_part;
     double *d_C1, *d_C2, *d_lam1, *d_lam2;
+    float *d_lam1f, *d_lam2f;   // FP32 copies (rebuilding the scale table after a change of rho)
     float *d_C1f, *d_C2f;
     double* arr[10];          // face-sized scratch arrays (8 bytes per face each)
     size_t bytes;             // total workspace bytes used

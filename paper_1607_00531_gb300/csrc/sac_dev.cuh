@@ -52,6 +52,12 @@ struct Job {
     const void* tmaps; // tensor-core z-step: TMA tensor maps of the X sources, [pass][source]
     int tc_tma;        // bit q: pass q loads X with the tensor maps; bit 4 + q: pass q stores with one
     int pad2_;
+    // adaptive augmentation parameter: after rho changes, every reader of the
+    // scaled dual u uses uscale * u (uscale = rho_old / rho_new) for one
+    // iteration, whose dual update stores the rescaled u; 1 otherwise
+    double uscale;
+    const float* lam1f;  // FP32 copies of lam1 / lam2 (the scale table is rebuilt from them)
+    const float* lam2f;
 };
 
 // ---------------------------------------------------------------- job lookup

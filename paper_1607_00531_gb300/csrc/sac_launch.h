@@ -153,6 +153,8 @@ int tc_encode_maps(const int F[3], int ax1, int ax2, const float* b, const float
 // 5 residual partial sums per block (FP32 state) and, when chk.counters is
 // set, the stopping test of each job in its last block; blocks per job:
 long long admm_update_blocks(long long nf);
+// after the host changed a job's rho: rebuild its z-step scale table
+cudaError_t launch_rebuild_scale(Job* job, cudaStream_t st);
 cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, long long total_blocks,
                                double* part, const AdmmCheck& chk, cudaStream_t st);
 void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass);

@@ -85,6 +85,7 @@ struct ServeReq {
     double t_submit = 0, t_admit = 0, t_done = 0;
     int iters = 0, converged = 0;
     double r_pri = 0, r_dual = 0;
+    double rho = 0, uscale = 1;     // adaptive rho: current value and pending dual rescale
     std::vector<double> b;          // result (host)
     bool fresh = true;
 };
@@ -189,6 +190,8 @@ int sac_server_step(struct sac_server_s* S, int iters, int chunk, int* n_running
         E.K = faces_per_lane(R.G.mpe);
         E.fresh = R.fresh ? 1 : 0;
         E.iters0 = R.iters;
+        E.rho0 = R.rho;
+        E.uscale0 = R.uscale;
         return E;
     };
     if (!S->queue.empty() && S->have_tables) {
@@ -257,6 +260,8 @@ int sac_server_step(struct sac_server_s* S, int iters, int chunk, int* n_running
         R.converged = stats[i].converged;
         R.r_pri = stats[i].r_pri;
         R.r_dual = stats[i].r_dual;
+        R.rho = stats[i].rho;
+        R.uscale = stats[i].uscale;
         if (stats[i].done) any_done = true;
     }
     if (any_done) {

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_axis(const Job* __restrict__ jobs, int 
                 if (ld_base[q] >= 0 && j < L) {
                     const long long a = ld_base[q] + (long long)j * post;
                     v = X0[a];
-                    if (X1) v += X1[a];
+                    if (X1) v += T(J.uscale) * X1[a];   // b + u (u rescaled after a change of rho)
                 }
                 Bs[ld_jj[q]][ld_cc[q]] = v;
             }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_axis(const Job* __restrict__ jobs, int 
                     T* __restrict__ U = (T*)J.u;
                     const T* __restrict__ B = (const T*)J.b;
                     const T zo = Z[a], bb = B[a], uu = U[a];
-                    const T un = uu + bb - v;
+                    const T un = T(J.uscale) * uu + bb - v;
                     Z[a] = v;
                     U[a] = un;
                     const T dbz = bb - v, dzz = v - zo;

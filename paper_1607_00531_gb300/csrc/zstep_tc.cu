@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
                                          : (PASS == 2) ? (const float*)J.t2 : (const float*)J.t1;
             const float* __restrict__ X1 = (const float*)J.u;   // pass 0 only
+            const float us = (float)J.uscale;                    // pass 0: b + uscale u
             const bool lv = lr < s.nl;
             const long long gbase = s.form ? s.pr * s.L * s.post + s.po0 + lr : (s.line0 + lr) * s.L;
             const long long js = s.form ? s.post : 1;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                             float4 x = *reinterpret_cast<const float4*>(rb + off);
                             if (NSRC == 2) {
                                 const float4 y = *reinterpret_cast<const float4*>(rb + kRawBytes + off);
-                                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+                                x.x += us * y.x; x.y += us * y.y; x.z += us * y.z; x.w += us * y.w;
                             }
                             v[4 * g] = x.x; v[4 * g + 1] = x.y; v[4 * g + 2] = x.z; v[4 * g + 3] = x.w;
                         }
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         for (int e = 0; e < 16; ++e) {
                             const uint32_t off = (uint32_t)((16 * kh + e) * kTileLines + lr) * 4u;
                             float x = *reinterpret_cast<const float*>(rb + off);
-                            if (NSRC == 2) x += *reinterpret_cast<const float*>(rb + kRawBytes + off);
+                            if (NSRC == 2) x += us * *reinterpret_cast<const float*>(rb + kRawBytes + off);
                             v[e] = x;
                         }
                     }
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         if (lv && j0 + e < s.L) {
                             const long long a = gbase + (long long)(j0 + e) * js;
                             x = __ldg(X0 + a);
-                            if (NSRC == 2) x += __ldg(X1 + a);
+                            if (NSRC == 2) x += us * __ldg(X1 + a);
                         }
                         v[e] = x;
                     }
@@ -818,6 +819,7 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
         const long long e00 = (blk - prefix[jid]) * kAdmmFaces;
         float* __restrict__ z = (float*)J.z;
         float* __restrict__ u = (float*)J.u;
+        const float us = (float)J.uscale;   // u rescaled after a change of rho
         const float* __restrict__ b = (const float*)J.b;
         const float* __restrict__ zn = (const float*)J.t2;
         auto acc = [&](float bb, float zo, float zz, float un) {
@@ -844,8 +846,8 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
                 for (int g = 0; g < kAdmmGroups; ++g) {
                     if (ei[g] >= nf) continue;
                     float4 un;
-                    un.x = vu[g].x + vb[g].x - vn[g].x; un.y = vu[g].y + vb[g].y - vn[g].y;
-                    un.z = vu[g].z + vb[g].z - vn[g].z; un.w = vu[g].w + vb[g].w - vn[g].w;
+                    un.x = us * vu[g].x + vb[g].x - vn[g].x; un.y = us * vu[g].y + vb[g].y - vn[g].y;
+                    un.z = us * vu[g].z + vb[g].z - vn[g].z; un.w = us * vu[g].w + vb[g].w - vn[g].w;
                     acc(vb[g].x, vz[g].x, vn[g].x, un.x);
                     acc(vb[g].y, vz[g].y, vn[g].y, un.y);
                     acc(vb[g].z, vz[g].z, vn[g].z, un.z);
@@ -857,7 +859,7 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
         } else {
             for (long long e = e00 + threadIdx.x; e < e00 + kAdmmFaces && e < nf; e += kAdmmThreads) {
                 const float bb = __ldg(b + e), zo = z[e], uu = u[e], zz = __ldg(zn + e);
-                const float un = uu + bb - zz;
+                const float un = us * uu + bb - zz;
                 acc(bb, zo, zz, un);
                 z[e] = zz;
                 u[e] = un;
@@ -896,6 +898,14 @@ __global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ 
     __threadfence();
     admm_check_job_f32(J, jid, reinterpret_cast<const float*>(part), prefix[jid], prefix[jid + 1], chk, redf);
     if (threadIdx.x == 0) chk.counters[jid] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_rebuild_scale(Job* __restrict__ job) { admm_rebuild_scale(*job); }
+
+cudaError_t launch_rebuild_scale(Job* job, cudaStream_t st) {
+    count_launch();
+    k_rebuild_scale<<<1, 256, 0, st>>>(job);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, long long total_blocks,

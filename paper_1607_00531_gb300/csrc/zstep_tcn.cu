@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
             const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
                                          : (PASS == 2) ? (const float*)J.t2 : (const float*)J.t1;
             const float* __restrict__ X1 = (const float*)J.u;   // pass 0 only
+            const float us = (float)J.uscale;                    // pass 0: b + uscale u
             auto load = [&](int c, float (&v)[16]) {
                 const int j0 = c * kBK + 16 * kh;
                 if (vec) {
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
                             x = __ldg(reinterpret_cast<const float4*>(X0 + base + j0 + 4 * gq));
                             if (NSRC == 2) {
                                 const float4 y = __ldg(reinterpret_cast<const float4*>(X1 + base + j0 + 4 * gq));
-                                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+                                x.x += us * y.x; x.y += us * y.y; x.z += us * y.z; x.w += us * y.w;
                             }
                         }
                         v[4 * gq] = x.x; v[4 * gq + 1] = x.y; v[4 * gq + 2] = x.z; v[4 * gq + 3] = x.w;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
                         if (lv && j0 + e < g.L) {
                             const long long a = base + (long long)(j0 + e) * js;
                             x = __ldg(X0 + a);
-                            if (NSRC == 2) x += __ldg(X1 + a);
+                            if (NSRC == 2) x += us * __ldg(X1 + a);
                         }
                         v[e] = x;
                     }

@@ -34,7 +34,9 @@ class SacParams(ctypes.Structure):
                  "eps_grad", "gn_rel_grad")] + \
                [(n, ctypes.c_int) for n in ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "prec")] + \
                [("near_bound", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("zstep_kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("bstep_kernel", ctypes.c_int)]
+                ("zstep_kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("bstep_kernel", ctypes.c_int),
+                ("adapt_rho", ctypes.c_int), ("rho_min", ctypes.c_double), ("rho_tau", ctypes.c_double),
+                ("rho_mu", ctypes.c_double)]
 
 
 class SacError(RuntimeError):

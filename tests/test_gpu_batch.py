@@ -59,6 +59,29 @@ def test_batch_equals_solo(sac, prec):
         assert diff <= 1e-12 * max(b.abs().max().item(), 1e-30), diff
 
 
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+def test_batch_adaptive_rho_equals_solo(sac, prec):
+    # the batched engine applies the adaptive rule on the device, in the
+    # stopping test of each volume; the single-volume call on the host
+    K = 12
+    vols = volumes()[:4]
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    p = sac.params(alpha=1.0, rho=1e6, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, adapt_rho=2, rho_min=2e4)
+    grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
+    I1s = [cu(d["I1"], dt) for d in vols]
+    I2s = [cu(d["I2"], dt) for d in vols]
+    bs = [torch.zeros(sac.face_shape(g), dtype=torch.float64, device="cuda") for g in grids]
+    bt = sac.Batch(grids, p, I1s, I2s, bs)
+    bt.run(K, chunk=4)
+    bt.finish()
+    bt.close()
+    for g, I1, I2, bb in zip(grids, I1s, I2s, bs):
+        b = torch.zeros_like(bb)
+        sac.admm_solve(g, p, I1, I2, b)
+        diff = (b - bb).abs().max().item()
+        assert diff <= 1e-12 * max(b.abs().max().item(), 1e-30), diff
+
+
 def test_batch_f64_matches_oracle(sac):
     K = 10
     vols = volumes()[:3]

@@ -214,6 +214,34 @@ def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
     assert abs(J_mix - J_ref) <= 1e-6 * abs(J_ref)
 
 
+# ---------------------------------------------------------------- adaptive augmentation parameter
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_admm_adaptive_rho(sac, mode, prec):
+    # rho from 1e6 (the paper's start) with the adaptive rule, optionally
+    # bounded below; the same rho sequence and the same iterate as the oracle
+    m, pe, K = (8, 48, 13), 1, 12
+    w = ph.small_workload(m, pe, seed=3, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    og = oracle.Grid(m, d["h"], pe)
+    kw = dict(alpha=1.0, rho=1e6, max_iter=K, eps_abs=0.0, eps_rel=0.0, adapt_rho=mode, rho_min=2e4)
+    ref = oracle.admm(og, oracle.Params(**kw), d["I1"], d["I2"], np.zeros(og.face_shape), want_hist=True)
+    assert len(set(ref["hist"][:, 4])) > 3          # rho changes several times
+    g = sac.grid(m, d["h"], pe)
+    p = sac.params(prec=prec, **kw)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    b = cu(np.zeros(og.face_shape))
+    res = sac.admm_solve(g, p, cu(d["I1"], dt), cu(d["I2"], dt), b, want_hist=True)
+    assert res["iters"] == K
+    np.testing.assert_allclose(res["hist"][:, 4], ref["hist"][:, 4], rtol=1e-12)
+    bb = b.cpu().numpy()
+    if prec == "f64":
+        assert np.linalg.norm(bb - ref["b"]) <= 1e-9 * np.linalg.norm(ref["b"])
+    else:
+        assert np.max(np.abs(bb - ref["b"])) / d["h"][pe] <= 1e-3
+
+
 # ---------------------------------------------------------------- corrected images, SSD, NCC (Sec. 6)
 
 @pytest.mark.parametrize("m,pe", CASES)
