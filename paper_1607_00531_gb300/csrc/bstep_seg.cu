@@ -1,16 +1,18 @@
 // bstep_seg.cu -- fast path of the ADMM b-step (Sec. 4.2, Eq. admmStep1) with
 // one thread per (line, segment), FP32 storage and arithmetic.
 //
-// A CTA takes NL = 16 neighbouring PE lines and cuts each of them into G
+// A CTA takes NL = kLines neighbouring PE lines and cuts each of them into G
 // segments of S faces; thread (g, l) = (tid / NL, tid % NL) takes segment g of
 // line l.  The lines must be strided (PE axis not the last one): face p of
 // the NL lines is then a run of NL consecutive floats of every face and cell
 // array, and the CTA stages the five arrays of its lines (I1, I2, b, z, u) in
 // shared memory as [p][line] rows with 16-byte asynchronous copies (one
 // round trip; all later reads, including the image values at the displaced
-// points, are shared-memory reads).  A CTA holds about 80 KB for lines of
-// 257 faces, so two CTAs share an SM and one CTA's staging, barriers and
-// serial steps overlap the other's arithmetic.
+// points, are shared-memory reads).  A CTA of 16 lines holds about 80 KB for
+// lines of 257 faces, so two CTAs share an SM and one CTA's staging, barriers
+// and serial steps overlap the other's arithmetic (8 lines per CTA, four CTAs
+// per SM, measured no faster: the warp holding the boundary segments then
+// covers a quarter of the CTA).
 //
 // Per line the step is the first pass of the active-set method with an empty
 // working set (the unconstrained Gauss-Newton step of the b-subproblem):
@@ -56,15 +58,15 @@ struct Cell {
 // residual of cell j between faces j and j+1 (b0, b1) and its two Jacobian
 // entries (Sec. 3); zero outside [0, m) (kIn: j is known to be inside)
 template <bool kIn>
-__device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* __restrict__ I2, int m, int j,
-                                     float b0, float b1, float inv_h) {
+__device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* __restrict__ I2, int m, float mf,
+                                     int j, float jf, float b0, float b1, float inv_h) {
     Cell c{0.f, 0.f, 0.f, 0.f};
     if (kIn || (j >= 0 && j < m)) {
         const float a = 0.5f * (b0 + b1);
         const float d = (b1 - b0) * inv_h;
         float v1, s1, v2, s2;
-        interp(I1, (float)m, (float)j + a * inv_h, v1, s1);
-        interp(I2, (float)m, (float)j - a * inv_h, v2, s2);
+        interp(I1, mf, jf + a * inv_h, v1, s1);
+        interp(I2, mf, jf - a * inv_h, v2, s2);
         const float g1 = s1 * inv_h, g2 = s2 * inv_h;
         c.r = v1 * (1.f + d) - v2 * (1.f - d);
         const float p = 0.5f * (g1 * (1.f + d) + g2 * (1.f - d));
@@ -87,12 +89,13 @@ __device__ __forceinline__ void forward(const float* __restrict__ rI1, const flo
                                         float (&R)[S]) {
     const float bprev = (kIn || s >= 1) ? rB[(s - 1) * kLines] : 0.f;
     float bcur = rB[s * kLines];
-    Cell prev = cell<kIn>(rI1, rI2, m, s - 1, bprev, bcur, inv_h);
+    const float mf = (float)m, sf = (float)s;   // cell positions as floats: sf + k (exact)
+    Cell prev = cell<kIn>(rI1, rI2, m, mf, s - 1, sf - 1.f, bprev, bcur, inv_h);
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const int i = s + k;
         const float bnext = (kIn || i + 1 <= m) ? rB[(i + 1) * kLines] : 0.f;
-        const Cell cur = cell<kIn>(rI1, rI2, m, i, bcur, bnext, inv_h);
+        const Cell cur = cell<kIn>(rI1, rI2, m, mf, i, sf + (float)k, bcur, bnext, inv_h);
         float dg = 1.f, sub = 0.f, sup = 0.f, rhs = 0.f;
         if (kIn || i <= m) {
             const float nadj = kIn ? 2.f : (float)((i > 0) + (i < m));
@@ -158,7 +161,7 @@ __device__ __forceinline__ void stage(float* __restrict__ dst, const float* __re
 size_t smem_bytes(int m) { return sizeof(float) * (size_t)kLines * (size_t)(2 * (m + 4) + 3 * (m + 1)); }
 
 template <int S>
-__global__ void __launch_bounds__(kLines * kMaxSeg, 2)
+__global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     k_bstep_seg(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, float near_bound,
                 unsigned long long* __restrict__ rlist, int* __restrict__ rcount, int rcap,
                 int* __restrict__ status) {
@@ -228,8 +231,11 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
     const float* rI2 = sI2 + lane;
     const float* rB = sB + lane;
     float A[S], C[S], R[S];    // eliminated rows of the segment
+    // interior segments skip the bound tests; a warp that holds a boundary
+    // segment takes the general path for all its threads (no divergence)
+    const bool warp_interior = __all_sync(__activemask(), !on || (s >= 1 && s + S <= m));
     if (on) {
-        if (s >= 1 && s + S <= m)
+        if (warp_interior)
             forward<S, true>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
         else
             forward<S, false>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
@@ -255,15 +261,16 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
         sE[5][g][lane] = R[S - 1];
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 2 * NL) {
         // The line's reduced system: unknown 2q = first of segment q, 2q+1 =
         // its last; row r couples r-1 (a) and r+1 (c), unit diagonal.  Warp
-        // 0 holds the first and the last segment of every line; its lanes
-        // l < 16 eliminate rows 0 .. G-1 downwards, lanes 16 + l rows 2G-1 ..
-        // G upwards (a two-ended Thomas elimination: half the serial chain),
-        // the two meet in a 2 x 2 system and substitute back outwards.
+        // 0 holds the first and the last segment of every line; its threads
+        // l < NL eliminate rows 0 .. G-1 downwards, threads NL + l rows 2G-1
+        // .. G upwards (a two-ended Thomas elimination: half the serial
+        // chain), the two meet in a 2 x 2 system and substitute back outwards.
         constexpr int kC = kMaxSeg * NL;   // stride between components
-        const bool top = threadIdx.x < 16;
+        constexpr unsigned kPair = (2 * NL >= 32) ? 0xffffffffu : ((1u << (2 * NL)) - 1u);
+        const bool top = threadIdx.x < NL;
         const int N = 2 * G, M = G, dir = top ? 1 : -1;
         const int obk = top ? 0 : kC, ofw = top ? kC : 0;   // a / c: towards the done / open side
         float* base = &sE[0][0][lane];
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
             e[2 * kC] = dp;
         }
         // top: x_{M-1} + c' x_M = d'; bottom: a'' x_{M-1} + x_M = d''
-        const float of = __shfl_xor_sync(kFull, fp, 16), od = __shfl_xor_sync(kFull, dp, 16);
+        const float of = __shfl_xor_sync(kPair, fp, NL), od = __shfl_xor_sync(kPair, dp, NL);
         const float ct = top ? fp : of, dt = top ? dp : od, ab = top ? of : fp, db = top ? od : dp;
         const float xm1 = fdiv(dt - ct * db, 1.f - ct * ab);
         float x = top ? xm1 : db - ab * xm1;
@@ -309,21 +316,34 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
         // crosses |D1 b| = 1 (a blocking constraint of the active-set
         // method) exactly where |D1 (b + x)| > 1; the largest |D1 (b + x)|
         // is also the line's distance from the bound
-        bool blocked = false;
-        float dmax = 0.f;
+        // (a NaN anywhere makes the sum NaN: the FP64 method takes the line)
+        float dmax = 0.f, dsum = 0.f;
         float b0 = rB[s * NL];
+        if (s + S <= m) {
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            const int j = s + k;
-            if (j < m) {
-                const float b1 = rB[(j + 1) * NL];
+            for (int k = 0; k < S; ++k) {
+                const float b1 = rB[(s + k + 1) * NL];
                 const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
                 const float dn = fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h);
-                blocked |= !(dn <= 1.f);   // also NaN: the FP64 method takes the line
                 dmax = fmaxf(dmax, dn);
+                dsum += dn;
                 b0 = b1;
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                const int j = s + k;
+                if (j < m) {
+                    const float b1 = rB[(j + 1) * NL];
+                    const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
+                    const float dn = fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h);
+                    dmax = fmaxf(dmax, dn);
+                    dsum += dn;
+                    b0 = b1;
+                }
+            }
         }
+        const bool blocked = !(dmax <= 1.f) || !(dsum == dsum);
         if (blocked) atomicOr(&sFlag[lane], 1);
         if (dmax > 0.f) atomicMax(&sDmax[lane], __float_as_int(dmax));
     }
@@ -333,11 +353,14 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 2)
     if (!queue) {
         if (on) {
             const long long o = L / ni;
-            float* gB = (float*)J.b + o * (long long)(m + 1) * ni + (L - o * ni);
+            float* gB = (float*)J.b + o * (long long)(m + 1) * ni + (L - o * ni) + (long long)s * ni;
+            if (s + S <= m + 1) {
 #pragma unroll
-            for (int k = 0; k < S; ++k) {
-                const int i = s + k;
-                if (i <= m) gB[(long long)i * ni] = rB[i * NL] + xs[k];
+                for (int k = 0; k < S; ++k) gB[(long long)k * ni] = rB[(s + k) * NL] + xs[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+                    if (s + k <= m) gB[(long long)k * ni] = rB[(s + k) * NL] + xs[k];
             }
         }
     } else if (gi == 0) {
@@ -371,7 +394,9 @@ cudaError_t prepare_bstep_seg() {
 cudaError_t launch_bstep_seg(const LineLaunch& L) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.seg_G < 1 || L.seg_G > seg::kMaxSeg) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)L.total_tiles, block = (unsigned)(seg::kLines * L.seg_G);
+    // at least two segments' threads: warp 0 pairs the first and the last
+    // segment of each line in the reduced solve
+    const unsigned grid = (unsigned)L.total_tiles, block = (unsigned)(seg::kLines * (L.seg_G > 2 ? L.seg_G : 2));
     const size_t smem = seg::smem_bytes(L.seg_m);
     const float nb = (float)L.near_bound;
     count_launch();
