@@ -59,6 +59,8 @@ def lib():
             "ref_pcg": g + [P, dp, dp, dp, dp, dp, dp],
             "ref_gnpcg": g + [P, dp, dp, dp, dp, lp, dp, dp],
             "ref_corrected": g + [dp, dp, dp, dp, dp, dp],
+            "ref_restrict": [ctypes.c_int, ip, dp, dp],
+            "ref_prolong": [ctypes.c_int, ip, ctypes.c_int, dp, dp],
         }.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -268,6 +270,74 @@ def corrected(grid, I1, I2, b):
     _check(lib().ref_corrected(*grid.args(), _dp(_f64(I1)), _dp(_f64(I2)), _dp(_f64(b)), _dp(T1), _dp(T2),
                                _dp(out)), "ref_corrected")
     return dict(T1=T1, T2=T2, ssd=out[0], ncc=out[1])
+
+
+def restrict(m, I):
+    """Mean of the 2^d fine cells of every coarse cell (m: fine cells)."""
+    m = tuple(int(x) for x in m)
+    Ic = np.zeros(tuple(x // 2 for x in m))
+    mm = (ctypes.c_int * 3)(*(list(m) + [1] * (3 - len(m))))
+    _check(lib().ref_restrict(len(m), mm, _dp(_f64(I)), _dp(Ic)), "ref_restrict")
+    return Ic
+
+
+def prolong(m, pe, bc):
+    """Fine faces from coarse faces by linear interpolation (m: fine cells)."""
+    m = tuple(int(x) for x in m)
+    bf = np.zeros(tuple(x + (1 if a == pe else 0) for a, x in enumerate(m)))
+    mm = (ctypes.c_int * 3)(*(list(m) + [1] * (3 - len(m))))
+    _check(lib().ref_prolong(len(m), mm, int(pe), _dp(_f64(bc)), _dp(bf)), "ref_prolong")
+    return bf
+
+
+def multilevel_admm(m, h, pe, prm, I1, I2, levels):
+    """Coarse-to-fine ADMM (Sec. 4.4): images restricted level by level, ADMM
+    from b = 0 on the coarsest grid; each finer level starts from b0 = z0 =
+    (P b + P z) / 2 and u0 = 0 (the paper's third strategy), rho carried over
+    (with adaptive rho: the last value of the coarser level)."""
+    m = tuple(int(x) for x in m)
+    h = tuple(float(x) for x in h)
+    ims = [(np.asarray(I1, dtype=float), np.asarray(I2, dtype=float), m, h)]
+    for _ in range(levels - 1):
+        A, B, mm, hh = ims[-1]
+        ims.append((restrict(mm, A), restrict(mm, B), tuple(x // 2 for x in mm), tuple(2 * x for x in hh)))
+    ims.reverse()
+    out = []
+    b = z = None
+    rho = prm.rho
+    for lvl, (A, B, mm, hh) in enumerate(ims):
+        g = Grid(mm, hh, pe)
+        if b is None:
+            b0 = np.zeros(g.face_shape)
+        else:
+            b0 = 0.5 * (prolong(mm, pe, b) + prolong(mm, pe, z))
+        p = Params(**{f.name: getattr(prm, f.name) for f in fields(prm)})
+        p.rho = rho
+        r = admm(g, p, A, B, b0, z0=b0.copy(), u0=np.zeros_like(b0), want_hist=True)
+        b, z = r["b"], r["z"]
+        rho = _rho_after(p, r)
+        out.append(dict(m=mm, h=hh, b=b, z=z, u=r["u"], iters=r["iters"], converged=r["converged"], rho=rho,
+                        hist=r["hist"]))
+    return out
+
+
+def _rho_after(prm, r):
+    # rho after the last iteration: the last recorded rho, adapted once more
+    # unless the level stopped on its test (the rule is applied only to
+    # iterations that did not stop)
+    hs = r["hist"]
+    if len(hs) == 0:
+        return prm.rho
+    rho = hs[-1, 4]
+    if not prm.adapt_rho or r["converged"]:
+        return rho
+    rp, rd = hs[-1, 0], hs[-1, 1]
+    if rp > prm.rho_mu * rd:
+        return rho * prm.rho_tau
+    if rd > prm.rho_mu * rp:
+        nr = rho / prm.rho_tau
+        return rho if (prm.adapt_rho == 2 and nr < prm.rho_min) else nr
+    return rho
 
 
 def max_abs_d1(grid, b):

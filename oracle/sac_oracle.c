@@ -796,6 +796,93 @@ int ref_corrected(int nd, const int* m, const double* h, int pe, const double* I
     return REF_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Multilevel strategy (Sec. 4.4): a coarse-to-fine sequence of grids, each  */
+/* coarse grid with twice the spacing along every axis.  The paper defers    */
+/* the transfer operators to the image registration literature; readings:   */
+/*   restriction of an image: the mean of the 2^d fine cells of a coarse     */
+/*     cell;                                                                 */
+/*   prolongation of b (faces along the PE axis, cells across it): linear   */
+/*     interpolation in every axis at the fine positions, i.e. along the PE  */
+/*     axis fine face 2k = coarse face k and fine face 2k+1 = the mean of    */
+/*     coarse faces k and k+1; across it fine cell 2j = 3/4 coarse cell j +  */
+/*     1/4 cell j-1 and fine cell 2j+1 = 3/4 cell j + 1/4 cell j+1, the      */
+/*     outside neighbour of a boundary cell replaced by the cell itself.     */
+/* With these, D1 of the prolongated field repeats the coarse D1 (and is a   */
+/* convex combination of coarse values across the PE axis), so a feasible    */
+/* coarse field stays feasible.  m are the FINE cells (every axis even).     */
+/* ------------------------------------------------------------------------ */
+int ref_restrict(int nd, const int* m, const double* I, double* Ic) {
+    if (nd != 2 && nd != 3) return REF_EINVAL;
+    long M[3] = {m[0], m[1], nd == 3 ? m[2] : 1};
+    for (int a = 0; a < nd; ++a)
+        if (M[a] % 2) return REF_EINVAL;
+    long C[3] = {M[0] / 2, M[1] / 2, nd == 3 ? M[2] / 2 : 1};
+    double w = 1.0 / (nd == 3 ? 8.0 : 4.0);
+    for (long i = 0; i < C[0]; ++i)
+        for (long j = 0; j < C[1]; ++j)
+            for (long k = 0; k < C[2]; ++k) {
+                double s = 0.0;
+                for (int di = 0; di < 2; ++di)
+                    for (int dj = 0; dj < 2; ++dj)
+                        for (int dk = 0; dk < (nd == 3 ? 2 : 1); ++dk)
+                            s += I[((2 * i + di) * M[1] + (2 * j + dj)) * M[2] + (nd == 3 ? 2 * k + dk : 0)];
+                Ic[(i * C[1] + j) * C[2] + k] = w * s;
+            }
+    return REF_OK;
+}
+
+/* 1D prolongation weights of fine index f along an axis of the coarse
+   length n (faces along PE when face != 0): at most two coarse indices. */
+static int prolong_1d(long f, long n, int face, long* idx, double* wt) {
+    if (face) {
+        if (f % 2 == 0) { idx[0] = f / 2; wt[0] = 1.0; return 1; }
+        idx[0] = (f - 1) / 2; idx[1] = (f + 1) / 2; wt[0] = wt[1] = 0.5;
+        return 2;
+    }
+    long j = f / 2, o = (f % 2 == 0) ? j - 1 : j + 1;
+    if (o < 0) o = 0;
+    if (o > n - 1) o = n - 1;
+    idx[0] = j; wt[0] = 0.75;
+    idx[1] = o; wt[1] = 0.25;
+    return 2;
+}
+
+/* bf (fine faces) = P bc (coarse faces); m are the FINE cells */
+int ref_prolong(int nd, const int* m, int pe, const double* bc, double* bf) {
+    if (nd != 2 && nd != 3) return REF_EINVAL;
+    if (pe < 0 || pe >= nd) return REF_EINVAL;
+    long M[3] = {m[0], m[1], nd == 3 ? m[2] : 1};
+    for (int a = 0; a < nd; ++a)
+        if (M[a] % 2) return REF_EINVAL;
+    long Cc[3], Ff[3], Fc[3];
+    for (int a = 0; a < 3; ++a) {
+        long c = (a < nd) ? M[a] / 2 : 1;
+        Cc[a] = c;
+        Fc[a] = c + (a == pe ? 1 : 0);
+        Ff[a] = M[a] + (a == pe ? 1 : 0);
+    }
+    for (long i = 0; i < Ff[0]; ++i)
+        for (long j = 0; j < Ff[1]; ++j)
+            for (long k = 0; k < Ff[2]; ++k) {
+                long ix[3][2];
+                double wx[3][2];
+                int nx[3];
+                long f[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a) {
+                    if (a >= nd) { nx[a] = 1; ix[a][0] = 0; wx[a][0] = 1.0; continue; }
+                    nx[a] = prolong_1d(f[a], Cc[a], a == pe, ix[a], wx[a]);
+                }
+                double s = 0.0;
+                for (int p = 0; p < nx[0]; ++p)
+                    for (int q = 0; q < nx[1]; ++q)
+                        for (int r = 0; r < nx[2]; ++r)
+                            s += wx[0][p] * wx[1][q] * wx[2][r] * bc[(ix[0][p] * Fc[1] + ix[1][q]) * Fc[2] + ix[2][r]];
+                bf[(i * Ff[1] + j) * Ff[2] + k] = s;
+            }
+    return REF_OK;
+}
+
 /* max |D1 b| over all cells (feasibility of b for the constraint set C) */
 double ref_max_abs_d1(int nd, const int* m, const double* h, int pe, const double* b) {
     grid_t g;

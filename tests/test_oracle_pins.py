@@ -531,6 +531,75 @@ def test_adaptive_rho_that_never_fires_is_the_fixed_method():
     assert np.array_equal(fixed["b"], never["b"]) and np.array_equal(fixed["u"], never["u"])
 
 
+# ---------------------------------------------------------------- multilevel transfer (Sec. 4.4)
+
+@pytest.mark.parametrize("m", [(8, 6), (6, 8, 4)])
+def test_restriction_is_the_block_mean(m):
+    rng = np.random.default_rng(7)
+    Ic = rng.uniform(size=tuple(x // 2 for x in m))
+    blocks = Ic
+    for a in range(len(m)):
+        blocks = np.repeat(blocks, 2, axis=a)
+    assert np.allclose(oracle.restrict(m, blocks), Ic, rtol=1e-15, atol=0)   # piecewise constant at the coarse scale
+    I = rng.uniform(size=m)
+    assert oracle.restrict(m, I).sum() * 2 ** len(m) == pytest.approx(I.sum(), rel=1e-14)
+    assert np.allclose(oracle.restrict(m, np.full(m, 0.37)), 0.37, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("m,pe", [((8, 6), 1), ((6, 8, 4), 1), ((4, 6, 8), 2), ((8, 4, 6), 0)])
+def test_prolongation_keeps_d1_and_linear_fields(m, pe):
+    rng = np.random.default_rng(8)
+    mc = tuple(x // 2 for x in m)
+    gc = oracle.Grid(mc, tuple(0.2 for _ in m), pe)
+    gf = oracle.Grid(m, tuple(0.1 for _ in m), pe)
+    bc = rng.normal(size=gc.face_shape)
+    bf = oracle.prolong(m, pe, bc)
+    # along PE: every fine D1 equals the coarse D1 of its coarse cell, for the
+    # coarse field averaged across the other axes
+    d1c = np.diff(bc, axis=pe) / 0.2
+    d1f = np.diff(bf, axis=pe) / 0.1
+    pair = np.take(d1f, np.arange(0, d1f.shape[pe], 2), axis=pe)
+    assert np.allclose(pair, np.take(d1f, np.arange(1, d1f.shape[pe], 2), axis=pe), rtol=0, atol=1e-12)
+    assert oracle.max_abs_d1(gf, bf) <= oracle.max_abs_d1(gc, bc) + 1e-12
+    # constants stay constants
+    assert np.allclose(oracle.prolong(m, pe, np.full(gc.face_shape, -1.25)), -1.25, rtol=0, atol=1e-15)
+    # a field linear along a non-PE axis (cell centres) is reproduced away from that axis' ends
+    ax = next(a for a in range(len(m)) if a != pe)
+    shape = [1] * len(m); shape[ax] = gc.face_shape[ax]
+    xc = ((np.arange(gc.face_shape[ax]) + 0.5) * 0.2).reshape(shape)
+    shape[ax] = gf.face_shape[ax]
+    xf = ((np.arange(gf.face_shape[ax]) + 0.5) * 0.1).reshape(shape)
+    lin = oracle.prolong(m, pe, np.broadcast_to(3.0 * xc + 1.0, gc.face_shape).copy())
+    ref = np.broadcast_to(3.0 * xf + 1.0, gf.face_shape)
+    inner = [slice(None)] * len(m); inner[ax] = slice(1, -1)
+    assert np.allclose(lin[tuple(inner)], ref[tuple(inner)], rtol=0, atol=1e-12)
+
+
+def test_multilevel_with_one_level_is_plain_admm():
+    m, pe = (8, 10, 6), 1
+    w = ph.small_workload(m, pe, seed=9)
+    d = ph.make_pair(w)
+    prm = oracle.Params(alpha=2.0, rho=50.0, max_iter=5, eps_abs=0.0, eps_rel=0.0)
+    ml = oracle.multilevel_admm(d["m"], d["h"], pe, prm, d["I1"], d["I2"], levels=1)
+    g = oracle.Grid(d["m"], d["h"], pe)
+    r = oracle.admm(g, prm, d["I1"], d["I2"], np.zeros(g.face_shape))
+    assert np.array_equal(ml[-1]["b"], r["b"])
+
+
+def test_multilevel_recovers_the_field_and_stays_feasible():
+    m, pe = (32, 32), 1
+    w = ph.small_workload(m, pe, seed=10, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    prm = oracle.Params(alpha=0.05, rho=1e3, max_iter=150, eps_abs=0.0, eps_rel=1e-5, adapt_rho=2, rho_min=1e2)
+    ml = oracle.multilevel_admm(d["m"], d["h"], pe, prm, d["I1"], d["I2"], levels=3)
+    assert [x["m"] for x in ml] == [(8, 8), (16, 16), (32, 32)]
+    g = oracle.Grid(d["m"], d["h"], pe)
+    assert oracle.max_abs_d1(g, ml[-1]["b"]) <= 1.0
+    D0 = oracle.objective(g, oracle.Params(alpha=0.0), d["I1"], d["I2"], np.zeros(g.face_shape))["D"]
+    D = oracle.objective(g, oracle.Params(alpha=0.0), d["I1"], d["I2"], ml[-1]["b"])["D"]
+    assert D < 0.2 * D0
+
+
 def test_zstep_decreases_augmented_lagrangian():
     # Lemma zdescent: L(b, z^k, y) - L(b, z^{k+1}, y) >= rho h^d / 2 ||z^k - z^{k+1}||^2
     m, pe = (6, 7, 5), 1
