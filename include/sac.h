@@ -161,6 +161,28 @@ int sac_corrected_images(const sac_grid* g, const sac_params* p, const void* I1,
                          const double* b, void* T1, void* T2, double* ssd, double* ncc, void* ws,
                          size_t ws_bytes, void* stream);
 
+/* Multilevel strategy (Sec. 4.4).  Grids coarsen by 2 along every axis (the
+   fine grid's cell counts must be divisible by 2^(levels-1)); spacings double.
+   sac_restrict_image: Ic (coarse cells, image type of p->prec) = the mean of
+   the 2^d fine cells of each coarse cell (`fine` is the fine grid, every axis
+   even).  sac_prolong_field: bf (fine faces, double) = linear interpolation
+   of bc (coarse faces) at the fine positions: along the PE axis fine face 2k =
+   coarse face k and 2k+1 = the mean of faces k and k+1; across it fine cell
+   2j = 3/4 cell j + 1/4 cell j-1, 2j+1 = 3/4 cell j + 1/4 cell j+1 (the outside
+   neighbour of a boundary cell replaced by the cell itself).
+   sac_multilevel_solve: ADMM from b = 0 on the coarsest grid, then on every
+   finer grid from b0 = z0 = (P b + P z) / 2, u0 = 0 (the paper's third
+   strategy; P b when that average is infeasible), rho carried from level to
+   level (with p->adapt_rho: the coarser level's last rho).  I1, I2: the fine
+   images; b (device, double): the fine result; iters (host, may be NULL):
+   ADMM iterations per level, coarsest first; *rho_final (host, may be NULL).
+   Returns SAC_ENOTCONV (a warning) when some level stopped at max_iter. */
+size_t sac_multilevel_workspace_bytes(const sac_grid* g, int levels, const sac_params* p);
+int sac_restrict_image(const sac_grid* fine, const sac_params* p, const void* I, void* Ic, void* stream);
+int sac_prolong_field(const sac_grid* fine, const double* bc, double* bf, void* stream);
+int sac_multilevel_solve(const sac_grid* g, int levels, const sac_params* p, const void* I1, const void* I2,
+                         double* b, int* iters, double* rho_final, void* ws, size_t ws_bytes, void* stream);
+
 /* Gradient of J_GN (Sec. 3: grad D = h^d J_r^T r, grad S = h^d sum_a D_a^T D_a b,
    grad P = beta h^d D1^T phi'(D1 b)) into grad (face array, double). */
 int sac_gradient(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,

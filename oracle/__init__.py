@@ -293,8 +293,9 @@ def prolong(m, pe, bc):
 def multilevel_admm(m, h, pe, prm, I1, I2, levels):
     """Coarse-to-fine ADMM (Sec. 4.4): images restricted level by level, ADMM
     from b = 0 on the coarsest grid; each finer level starts from b0 = z0 =
-    (P b + P z) / 2 and u0 = 0 (the paper's third strategy), rho carried over
-    (with adaptive rho: the last value of the coarser level)."""
+    (P b + P z) / 2 and u0 = 0 (the paper's third strategy; P b when the
+    average is infeasible), rho carried over (with adaptive rho: the last value
+    of the coarser level)."""
     m = tuple(int(x) for x in m)
     h = tuple(float(x) for x in h)
     ims = [(np.asarray(I1, dtype=float), np.asarray(I2, dtype=float), m, h)]
@@ -310,7 +311,7 @@ def multilevel_admm(m, h, pe, prm, I1, I2, levels):
         if b is None:
             b0 = np.zeros(g.face_shape)
         else:
-            b0 = 0.5 * (prolong(mm, pe, b) + prolong(mm, pe, z))
+            b0 = _next_start(g, mm, pe, b, z)
         p = Params(**{f.name: getattr(prm, f.name) for f in fields(prm)})
         p.rho = rho
         r = admm(g, p, A, B, b0, z0=b0.copy(), u0=np.zeros_like(b0), want_hist=True)
@@ -319,6 +320,19 @@ def multilevel_admm(m, h, pe, prm, I1, I2, levels):
         out.append(dict(m=mm, h=hh, b=b, z=z, u=r["u"], iters=r["iters"], converged=r["converged"], rho=rho,
                         hist=r["hist"]))
     return out
+
+
+def _next_start(g, mm, pe, b, z):
+    # the third strategy's start (P b + P z) / 2; z is not constrained, so
+    # when the average leaves |D1 b| <= 1, P b (feasible with b); a start
+    # still outside by rounding is scaled back onto the set
+    b0 = 0.5 * (prolong(mm, pe, b) + prolong(mm, pe, z))
+    if max_abs_d1(g, b0) > 1.0:
+        b0 = prolong(mm, pe, b)
+    mx = max_abs_d1(g, b0)
+    if mx > 1.0:
+        b0 = b0 / mx
+    return b0
 
 
 def _rho_after(prm, r):

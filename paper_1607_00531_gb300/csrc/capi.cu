@@ -715,11 +715,18 @@ int sac_zstep(const sac_grid* g, const sac_params* p, const double* b, const dou
     return status_of(P, st, nullptr);
 }
 
-int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, double* b, double* z,
-                   double* u, int* iters, double* r_pri, double* r_dual, double* hist, void* ws, size_t ws_bytes,
-                   void* stream) {
-    if (!I1 || !I2 || !b) return SAC_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+// ADMM on one volume starting from rho0 (the parameters' rho replaced); on
+// return *rho_out (may be null) holds rho after the last iteration (the
+// adaptive rule applied to every iteration that did not stop)
+static int admm_solve_impl(const sac_grid* g, const sac_params* p0, double rho0, const void* I1, const void* I2,
+                           double* b, double* z, double* u, int* iters, double* r_pri, double* r_dual, double* hist,
+                           void* ws, size_t ws_bytes, cudaStream_t st, double* rho_out) {
+    if (!I1 || !I2 || !b || !p0) return SAC_EINVAL;
+    sac_params q = *p0;
+    q.rho = rho0;
+    const sac_params* p = &q;
     Plan P;
     SAC_TRY(setup(g, p, ws, ws_bytes, &P));
     const long long nf = P.G.nf;
@@ -794,8 +801,148 @@ int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const
     if (iters) *iters = k;
     if (r_pri) *r_pri = rp;
     if (r_dual) *r_dual = rd;
+    if (rho_out) *rho_out = rho;
     SAC_TRY(status_of(P, st, nullptr));
     return conv ? SAC_OK : SAC_ENOTCONV;
+}
+
+// Multilevel layout: level grids (0 coarsest .. levels-1 = g) and the
+// workspace carve: restricted images of the coarser levels, b and z of every
+// level but the finest b (the caller's), then one single-volume workspace
+// (the largest, the finest level's) reused by every level.
+struct MlLayout {
+    sac_grid grid[8];
+    size_t img1[8], img2[8], bl[8], zl[8], solve, solve_bytes, bytes;
+};
+
+static int ml_layout(const sac_grid* g, int levels, const sac_params* p, MlLayout* L) {
+    if (!g || !p || levels < 1 || levels > 8) return SAC_EINVAL;
+    Geometry G0;
+    SAC_TRY(make_geometry(g, &G0));
+    SAC_TRY(check_params(p));
+    const size_t es = (p->prec == SAC_MIXED) ? 4 : 8;
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o = off; off = align256(off + n); return o; };
+    for (int l = 0; l < levels; ++l) {
+        const int f = 1 << (levels - 1 - l);
+        sac_grid& gl = L->grid[l];
+        gl = *g;
+        for (int a = 0; a < g->ndim; ++a) {
+            if (g->m[a] % f) return SAC_EINVAL;
+            gl.m[a] = g->m[a] / f;
+            gl.h[a] = g->h[a] * f;
+        }
+        Geometry Gl;
+        SAC_TRY(make_geometry(&gl, &Gl));
+        const bool finest = (l == levels - 1);
+        L->img1[l] = finest ? 0 : take(es * (size_t)Gl.nc);
+        L->img2[l] = finest ? 0 : take(es * (size_t)Gl.nc);
+        L->bl[l] = finest ? 0 : take(8 * (size_t)Gl.nf);
+        L->zl[l] = take(8 * (size_t)Gl.nf);
+    }
+    L->solve_bytes = sac_workspace_bytes(g, p);
+    if (L->solve_bytes == 0) return SAC_EINVAL;
+    L->solve = take(L->solve_bytes);
+    L->bytes = off;
+    return SAC_OK;
+}
+
+extern "C" {
+
+int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, double* b, double* z,
+                   double* u, int* iters, double* r_pri, double* r_dual, double* hist, void* ws, size_t ws_bytes,
+                   void* stream) {
+    if (!p) return SAC_EINVAL;
+    return admm_solve_impl(g, p, p->rho, I1, I2, b, z, u, iters, r_pri, r_dual, hist, ws, ws_bytes,
+                           (cudaStream_t)stream, nullptr);
+}
+
+size_t sac_multilevel_workspace_bytes(const sac_grid* g, int levels, const sac_params* p) {
+    MlLayout L;
+    return ml_layout(g, levels, p, &L) == SAC_OK ? L.bytes : 0;
+}
+
+int sac_restrict_image(const sac_grid* fine, const sac_params* p, const void* I, void* Ic, void* stream) {
+    Geometry G;
+    if (!p || !I || !Ic) return SAC_EINVAL;
+    SAC_TRY(make_geometry(fine, &G));
+    for (int a = 0; a < G.nd; ++a)
+        if (G.M[a] % 2) return SAC_EINVAL;
+    SAC_CUDA(launch_restrict(G.nd, G.M, p->prec == SAC_MIXED, I, Ic, (cudaStream_t)stream));
+    return SAC_OK;
+}
+
+int sac_prolong_field(const sac_grid* fine, const double* bc, double* bf, void* stream) {
+    Geometry G;
+    if (!bc || !bf) return SAC_EINVAL;
+    SAC_TRY(make_geometry(fine, &G));
+    for (int a = 0; a < G.nd; ++a)
+        if (G.M[a] % 2) return SAC_EINVAL;
+    SAC_CUDA(launch_prolong(G.nd, G.pe, G.M, bc, nullptr, bf, nullptr, nullptr, (cudaStream_t)stream));
+    return SAC_OK;
+}
+
+int sac_multilevel_solve(const sac_grid* g, int levels, const sac_params* p, const void* I1, const void* I2,
+                         double* b, int* iters, double* rho_final, void* ws, size_t ws_bytes, void* stream) {
+    if (!I1 || !I2 || !b || !ws || (((uintptr_t)ws) & 255)) return SAC_EINVAL;
+    MlLayout L;
+    SAC_TRY(ml_layout(g, levels, p, &L));
+    if (ws_bytes < L.bytes) return SAC_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    const bool f32 = (p->prec == SAC_MIXED);
+    const void* im1[8];
+    const void* im2[8];
+    double* bl[8];
+    double* zl[8];
+    for (int l = 0; l < levels; ++l) {
+        const bool finest = (l == levels - 1);
+        im1[l] = finest ? I1 : (const void*)(base + L.img1[l]);
+        im2[l] = finest ? I2 : (const void*)(base + L.img2[l]);
+        bl[l] = finest ? b : (double*)(base + L.bl[l]);
+        zl[l] = (double*)(base + L.zl[l]);
+    }
+    // images, finest to coarsest
+    for (int l = levels - 2; l >= 0; --l) {
+        Geometry Gf;
+        SAC_TRY(make_geometry(&L.grid[l + 1], &Gf));
+        SAC_CUDA(launch_restrict(Gf.nd, Gf.M, f32, im1[l + 1], (void*)im1[l], st));
+        SAC_CUDA(launch_restrict(Gf.nd, Gf.M, f32, im2[l + 1], (void*)im2[l], st));
+    }
+    double rho = p->rho;
+    int result = SAC_OK;
+    for (int l = 0; l < levels; ++l) {
+        Geometry Gl;
+        SAC_TRY(make_geometry(&L.grid[l], &Gl));
+        if (l == 0) {
+            SAC_CUDA(cudaMemsetAsync(bl[0], 0, 8 * (size_t)Gl.nf, st));
+        } else {
+            // start of a finer level (the third strategy): b0 = z0 =
+            // (P b + P z) / 2, u0 = 0; P b when the average leaves the
+            // feasible set (z is not constrained), scaled back onto it when
+            // still outside by rounding
+            Plan P;
+            SAC_TRY(setup(&L.grid[l], p, base + L.solve, L.solve_bytes, &P));
+            SAC_TRY(plan_upload(&P, p, im1[l], im2[l], bl[l], nullptr, nullptr, nullptr, nullptr, st));
+            SAC_CUDA(launch_prolong(Gl.nd, Gl.pe, Gl.M, bl[l - 1], zl[l - 1], bl[l], nullptr, nullptr, st));
+            double mx = 0.0;
+            SAC_TRY(max_abs_d1_dev(P, bl[l], &mx, st));
+            if (!(mx <= 1.0)) {
+                SAC_CUDA(launch_prolong(Gl.nd, Gl.pe, Gl.M, bl[l - 1], nullptr, bl[l], nullptr, nullptr, st));
+                SAC_TRY(max_abs_d1_dev(P, bl[l], &mx, st));
+                if (!(mx <= 1.0)) SAC_CUDA(launch_axpby(Gl.nf, 1.0 / mx, bl[l], 0.0, bl[l], bl[l], st));
+            }
+        }
+        SAC_CUDA(cudaMemcpyAsync(zl[l], bl[l], 8 * (size_t)Gl.nf, cudaMemcpyDeviceToDevice, st));
+        int it = 0;
+        const int s = admm_solve_impl(&L.grid[l], p, rho, im1[l], im2[l], bl[l], zl[l], nullptr, &it, nullptr,
+                                      nullptr, nullptr, base + L.solve, L.solve_bytes, st, &rho);
+        if (s < 0) return s;
+        if (s != SAC_OK) result = s;   // SAC_ENOTCONV on some level: a warning
+        if (iters) iters[l] = it;
+    }
+    if (rho_final) *rho_final = rho;
+    return result;
 }
 
 int sac_hessvec(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,

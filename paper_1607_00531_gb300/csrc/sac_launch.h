@@ -196,6 +196,13 @@ cudaError_t launch_fill(long long n, double v, double* dst, cudaStream_t st);
 int corrected_blocks(long long nc);
 cudaError_t launch_corrected(int prec, const Job* job, long long nc, const double* b, void* T1, void* T2,
                              double* part, cudaStream_t st);
+// multilevel grid transfer (multilevel.cu); M: FINE cells (every used axis
+// even).  Restriction: image type FP32 (f32) or FP64.  Prolongation of the
+// FP64 face arrays: bf = zf = (P bc + P zc) / 2 (zc null: bf = P bc; zf, uf
+// may be null), uf = 0.
+cudaError_t launch_restrict(int nd, const int M[3], bool f32, const void* I, void* Ic, cudaStream_t st);
+cudaError_t launch_prolong(int nd, int pe, const int M[3], const double* bc, const double* zc, double* bf, double* zf,
+                           double* uf, cudaStream_t st);
 cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
                               const double* b, double* part, cudaStream_t st);
 

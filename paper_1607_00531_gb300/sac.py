@@ -65,6 +65,10 @@ def lib():
             "sac_objective": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp, sz, vp]),
             "sac_gradient": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, sz, vp]),
             "sac_corrected_images": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, dp, dp, vp, sz, vp]),
+            "sac_multilevel_workspace_bytes": (sz, [G, ctypes.c_int, P]),
+            "sac_restrict_image": (ctypes.c_int, [G, P, vp, vp, vp]),
+            "sac_prolong_field": (ctypes.c_int, [G, vp, vp, vp]),
+            "sac_multilevel_solve": (ctypes.c_int, [G, ctypes.c_int, P, vp, vp, vp, ip, dp, vp, sz, vp]),
             "sac_objective_noalloc": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp]),
             "sac_objective_noalloc_max_bytes": (sz, []),
             "sac_bstep": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]),
@@ -219,6 +223,37 @@ def corrected_images(g, p, I1, I2, b, T1=None, T2=None, ws=None, stream=None):
                                       _ptr(T2), ctypes.byref(ssd), ctypes.byref(ncc), _ptr(ws), ws.numel(),
                                       _stream(stream)))
     return dict(T1=T1, T2=T2, ssd=ssd.value, ncc=ncc.value)
+
+
+def restrict_image(g_fine, p, I, stream=None):
+    """Coarse image (block means of the fine cells)."""
+    Ic = _torch().empty(tuple(int(x) // 2 for x in I.shape), dtype=I.dtype, device=I.device)
+    _check("sac_restrict_image", lib().sac_restrict_image(ctypes.byref(g_fine), ctypes.byref(p), _ptr(I), _ptr(Ic),
+                                                          _stream(stream)))
+    return Ic
+
+
+def prolong_field(g_fine, bc, stream=None):
+    """Fine face array from a coarse one (linear interpolation, Sec. 4.4)."""
+    bf = _torch().empty(face_shape(g_fine), dtype=_torch().float64, device=bc.device)
+    _check("sac_prolong_field", lib().sac_prolong_field(ctypes.byref(g_fine), _ptr(bc), _ptr(bf), _stream(stream)))
+    return bf
+
+
+def multilevel_solve(g, levels, p, I1, I2, b, ws=None, stream=None):
+    """Coarse-to-fine ADMM; b (fine faces, double) receives the result."""
+    _check_inputs(g, p, I1, I2)
+    n = int(lib().sac_multilevel_workspace_bytes(ctypes.byref(g), int(levels), ctypes.byref(p)))
+    if n == 0:
+        raise SacError("sac_multilevel_workspace_bytes", SAC_EINVAL)
+    ws = _torch().empty(n, dtype=_torch().uint8, device="cuda") if ws is None else ws
+    its = (ctypes.c_int * int(levels))()
+    rho = ctypes.c_double(0)
+    st = lib().sac_multilevel_solve(ctypes.byref(g), int(levels), ctypes.byref(p), _ptr(I1), _ptr(I2), _ptr(b), its,
+                                    ctypes.byref(rho), _ptr(ws), ws.numel(), _stream(stream))
+    if st < 0:
+        raise SacError("sac_multilevel_solve", st)
+    return dict(iters=list(its), rho=rho.value, status=st)
 
 
 def objective_noalloc(g, p, I1, I2, b, stream=None):

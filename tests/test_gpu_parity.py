@@ -242,6 +242,45 @@ def test_admm_adaptive_rho(sac, mode, prec):
         assert np.max(np.abs(bb - ref["b"])) / d["h"][pe] <= 1e-3
 
 
+# ---------------------------------------------------------------- multilevel strategy (Sec. 4.4)
+
+@pytest.mark.parametrize("m,pe", [((8, 12), 1), ((6, 10, 8), 1), ((4, 6, 10), 2), ((10, 4, 6), 0)])
+def test_restriction_and_prolongation(sac, m, pe):
+    rng = np.random.default_rng(11)
+    I = rng.uniform(size=m)
+    g = sac.grid(m, tuple(0.1 for _ in m), pe)
+    for prec, dt, tol in (("f64", torch.float64, 1e-15), ("mixed", torch.float32, 1e-6)):
+        Ic = sac.restrict_image(g, sac.params(prec=prec), cu(I, dt)).double().cpu().numpy()
+        assert rel(Ic, oracle.restrict(m, I)) < tol
+    mc = tuple(x // 2 for x in m)
+    bc = rng.normal(size=tuple(x + (1 if a == pe else 0) for a, x in enumerate(mc)))
+    bf = sac.prolong_field(g, cu(bc)).cpu().numpy()
+    assert rel(bf, oracle.prolong(m, pe, bc)) < 1e-15
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_multilevel_solve(sac, prec):
+    # three levels (8x12x6 -> 16x24x12 -> 32x48x24), a fixed number of
+    # iterations per level, adaptive rho with a lower bound carried across
+    m, pe, K = (32, 48, 24), 1, 8
+    w = ph.small_workload(m, pe, seed=12, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    kw = dict(alpha=1.0, rho=1e5, max_iter=K, eps_abs=0.0, eps_rel=0.0, adapt_rho=2, rho_min=1e3)
+    ref = oracle.multilevel_admm(m, d["h"], pe, oracle.Params(**kw), d["I1"], d["I2"], levels=3)
+    g = sac.grid(m, d["h"], pe)
+    p = sac.params(prec=prec, **kw)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    b = cu(np.zeros(sac.face_shape(g)))
+    res = sac.multilevel_solve(g, 3, p, cu(d["I1"], dt), cu(d["I2"], dt), b)
+    assert res["iters"] == [K, K, K]
+    assert res["rho"] == pytest.approx(ref[-1]["rho"], rel=1e-12)
+    bb = b.cpu().numpy()
+    if prec == "f64":
+        assert np.linalg.norm(bb - ref[-1]["b"]) <= 1e-9 * np.linalg.norm(ref[-1]["b"])
+    else:
+        assert np.max(np.abs(bb - ref[-1]["b"])) / d["h"][pe] <= 1e-3
+
+
 # ---------------------------------------------------------------- corrected images, SSD, NCC (Sec. 6)
 
 @pytest.mark.parametrize("m,pe", CASES)
