@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--workload", default="3d_256x256x80")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--tts-cap", type=int, default=400)
+    ap.add_argument("--tts-cap", type=int, default=2000)
     ap.add_argument("--profile-direct", type=int, default=0, metavar="K",
                     help="only run K mixed ADMM iterations through sac_admm_solve (no CUDA graphs, no "
                          "timing line): the launch sequence for kernel profilers")
@@ -307,9 +307,11 @@ def main():
         return sac.params(alpha=w.alpha, rho=w.rho, prec=prec, max_iter=iters, eps_abs=0.0, eps_rel=eps_rel,
                           check_every=every or max(iters, 1), near_bound=1e-3)
 
-    def batch(prec, I1x, I2x, max_iter, eps_rel=0.0, autotune=1):
+    def batch(prec, I1x, I2x, max_iter, eps_rel=0.0, autotune=1, **kw):
         p = sac.params(alpha=w.alpha, rho=w.rho, prec=prec, max_iter=max_iter, eps_abs=0.0, eps_rel=eps_rel,
                        near_bound=1e-3, autotune=autotune)
+        for k, v in kw.items():
+            setattr(p, k, v)
         bb = torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
         return sac.Batch([g], p, [I1x], [I2x], [bb]), bb
 
@@ -412,7 +414,7 @@ def main():
         tts = {}
         b_by = {}
         for prec, A1, A2 in (("mixed", I1, I2), ("f64", I1d, I2d)):
-            cap = args.tts_cap if prec == "mixed" else min(args.tts_cap, 200)
+            cap = args.tts_cap if prec == "mixed" else min(args.tts_cap, 1000)
             barrier()
             t0 = time.perf_counter()
             btt, bres = batch(prec, A1, A2, cap, eps_rel=1e-4, autotune=0)
@@ -435,6 +437,56 @@ def main():
         bt6.run(kk, chunk=10); bt6.finish(); bt6.close()
         tts["mixed_vs_f64_same_iterations"] = {
             "iterations": kk, "max_abs_db_voxels": float((bm - b6).abs().max().item() / w.h[w.pe])}
+        # the paper's augmentation schedule (Sec. 6): adaptive rho from 1e6,
+        # bounded below by 1e2 (the fixed value above), one level and three
+        # levels (coarse-to-fine, Sec. 4.4), mixed precision
+        cap = args.tts_cap
+        barrier()
+        t0 = time.perf_counter()
+        bta, bra = batch("mixed", I1, I2, cap, eps_rel=1e-4, autotune=0, rho=1e6, adapt_rho=2, rho_min=w.rho)
+        bta.run(cap, chunk=10)
+        st = bta.stats()
+        bta.finish()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        bta.close()
+        tts["mixed_adaptive_rho"] = {"seconds": sec, "iterations": int(st["iters"][0]),
+                                     "converged": bool(st["converged"][0]), "r_pri": float(st["r_pri"][0]),
+                                     "r_dual": float(st["r_dual"][0]), "cap": cap,
+                                     "rho": {"start": 1e6, "min": w.rho, "tau": 1.3, "mu": 10.0}}
+        levels = 3
+        if all(x % (1 << (levels - 1)) == 0 for x in w.m):
+            pml = sac.params(alpha=w.alpha, rho=1e6, prec="mixed", max_iter=cap, eps_abs=0.0, eps_rel=1e-4,
+                             near_bound=1e-3, adapt_rho=2, rho_min=w.rho)
+            bml = torch.zeros(sac.face_shape(g), dtype=torch.float64, device=dev)
+            barrier()
+            t0 = time.perf_counter()
+            rml = sac.multilevel_solve(g, levels, pml, I1, I2, bml)
+            torch.cuda.synchronize()
+            tts["mixed_multilevel"] = {"seconds": time.perf_counter() - t0, "levels": levels,
+                                       "iterations_per_level": rml["iters"], "converged": rml["status"] == 0,
+                                       "rho_final": rml["rho"], "cap_per_level": cap}
+
+    # GN-PCG preconditioners (Sec. 4.1, Sec. 6): Jacobi against block-Jacobi
+    # on the 2D 128 x 128 slice (the paper compares them in 2D), FP64
+    pcg = None
+    if not args.no_tts and rank == 0:
+        wp, dp_ = load_workload("2d_128")
+        gp = sac.grid(wp.m, wp.h, wp.pe)
+        A1 = torch.as_tensor(dp_["I1"], dtype=torch.float64, device=dev)
+        A2 = torch.as_tensor(dp_["I2"], dtype=torch.float64, device=dev)
+        pcg = {"workload": wp.name, "faces": int(np.prod(sac.face_shape(gp))), "prec": "f64",
+               "alpha": wp.alpha, "beta": 10.0, "max_gn": 10, "eta": 0.1, "max_pcg": 500}
+        for name, pc in (("none", 0), ("jacobi", 1), ("block_jacobi", 2)):
+            pp = sac.params(alpha=wp.alpha, beta=10.0, prec="f64", max_gn=10, eta=0.1, precond=pc, max_pcg=500)
+            bp = torch.zeros(sac.face_shape(gp), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rp = sac.gnpcg_solve(gp, pp, A1, A2, bp, want_hist=True)
+            torch.cuda.synchronize()
+            pcg[name] = {"seconds": time.perf_counter() - t0, "gn_iterations": rp["iters"],
+                         "pcg_iterations": int(rp["hist"][:, 2].sum()),
+                         "pcg_per_gn": [int(x) for x in rp["hist"][:, 2]], "J": rp["J"]}
 
     # roofline of the dominant kernel (largest summed device time in the timed region)
     roof, kernels = roofline(prof, w, g, nf, sac)
@@ -457,6 +509,7 @@ def main():
                 "f64_path": {"value": f64_val, "unit": UNIT, "iterations": kf,
                              "mixed_over_f64": value / world / f64_val},
                 "time_to_solution": tts,
+                "gnpcg_preconditioners": pcg,
                 "context": "paper: < 50 s for > 5M dof, three-level ADMM, MATLAB on a laptop CPU"}
         print(json.dumps(line), flush=True)
     if dist:

@@ -195,6 +195,28 @@ def test_gnpcg_f64(sac, m, pe):
     assert res["J"] == pytest.approx(ref["J"], rel=1e-10)
 
 
+def test_gnpcg_jacobi_against_block_jacobi(sac):
+    # Sec. 6, preconditioner comparison: the same GN-PCG with the Jacobi and
+    # the block-Jacobi preconditioner; each matches the oracle's PCG counts,
+    # and block-Jacobi needs fewer PCG iterations in total
+    m, pe = (32, 32), 1
+    w = ph.small_workload(m, pe, seed=5, peak_px=2.0, max_d=0.5)
+    d = ph.make_pair(w)
+    og = oracle.Grid(m, d["h"], pe)
+    g = sac.grid(m, d["h"], pe)
+    total = {}
+    for pc in (1, 2):
+        op = oracle.Params(alpha=200.0, beta=10.0, max_gn=4, eta=0.01, max_pcg=200, precond=pc)
+        ref = oracle.gnpcg(og, op, d["I1"], d["I2"], np.zeros(og.face_shape), want_hist=True)
+        p = sac.params(alpha=200.0, beta=10.0, max_gn=4, eta=0.01, max_pcg=200, precond=pc, prec="f64")
+        b = cu(np.zeros(og.face_shape))
+        res = sac.gnpcg_solve(g, p, cu(d["I1"]), cu(d["I2"]), b, want_hist=True)
+        assert res["iters"] == ref["iters"]
+        np.testing.assert_array_equal(res["hist"][:, 2], ref["hist"][:, 2])
+        total[pc] = int(res["hist"][:, 2].sum())
+    assert total[2] < total[1]
+
+
 @pytest.mark.parametrize("m,pe,K", [((24, 40), 1, 20), ((8, 48, 13), 1, 12)])
 def test_admm_mixed_precision_within_stated_tolerance(sac, m, pe, K):
     w = ph.small_workload(m, pe, seed=3, peak_px=2.0, max_d=0.5)
