@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tts-cap", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="arrival window of the serving run (Poisson, 20 requests/s); 0 skips it")
     ap.add_argument("--profile-direct", type=int, default=0, metavar="K",
                     help="only run K mixed ADMM iterations through sac_admm_solve (no CUDA graphs, no "
                          "timing line): the launch sequence for kernel profilers")
@@ -233,6 +235,78 @@ def ncu_traffic():
     with open(path) as fh:
         d = json.load(fh)
     return {k: v.get("bytes_per_launch") for k, v in d.get("kernels", {}).items()}
+
+
+def serve_run(args, sac, d5, w5, f64_rate):
+    """Requests drawn uniformly from the five serving kinds (2D 128^2 and 256^2,
+    3D 96x96x60, 128x128x64 and 256x256x80), arriving as a Poisson process of
+    20 requests per second for args.serve_seconds; one seeded phantom per kind
+    (the 256x256x80 one is the bench volume).  The server admits requests while
+    its 40 GB pool has room, iterates all admitted ones together and retires
+    them at relative residual 1e-4 (at most 2000 iterations)."""
+    import torch
+    from paper_1607_00531_gb300 import phantoms as ph
+    pairs = []
+    for k in range(len(ph.SERVING_KINDS)):
+        m, pe = ph.SERVING_KINDS[k]
+        if m == tuple(w5.m):
+            pairs.append((sac.grid(w5.m, w5.h, w5.pe), d5["I1"].astype(np.float32), d5["I2"].astype(np.float32)))
+            continue
+        if m == (128, 128, 64):
+            wk, dk = load_workload("3d_128x128x64")
+        else:
+            wk = ph.serving_workload(k, 500 + k)
+            dk = ph.make_pair(wk, dtype=np.float32)
+        pairs.append((sac.grid(wk.m, wk.h, wk.pe), np.asarray(dk["I1"], np.float32), np.asarray(dk["I2"], np.float32)))
+    p = sac.params(alpha=50.0, rho=1e2, prec="mixed", max_iter=2000, eps_abs=0.0, eps_rel=1e-4, near_bound=1e-3)
+    srv = sac.Server(p, pool_bytes=40 << 30, max_jobs=64)
+    rng = np.random.default_rng(5)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / 20.0)
+        if t > args.serve_seconds:
+            break
+        arrivals.append((t, int(rng.integers(len(pairs)))))
+    kinds = {}
+    open_t = {}
+    done = {}
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(arrivals) or open_t:
+        now = time.perf_counter() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            g, A, B = pairs[arrivals[i][1]]
+            tk = srv.submit(g, A, B)
+            open_t[tk] = arrivals[i][1]
+            i += 1
+        if open_t:
+            srv.step(20, chunk=10)
+            for tk in list(open_t):
+                info = srv.poll(tk)
+                if info["state"] == 2:
+                    done[tk] = (open_t.pop(tk), info)
+        elif i < len(arrivals):
+            time.sleep(max(0.0, arrivals[i][0] - (time.perf_counter() - t0)))
+    torch.cuda.synchronize()
+    lat = np.array([inf["t_done"] - inf["t_submit"] for _, inf in done.values()])
+    first = min(inf["t_submit"] for _, inf in done.values())
+    last = max(inf["t_done"] for _, inf in done.values())
+    work = 0
+    for k, inf in done.values():
+        g = pairs[k][0]
+        work += int(np.prod(sac.face_shape(g))) * inf["iters"]
+        kinds.setdefault(str(tuple(ph.SERVING_KINDS[k][0])), []).append(inf["iters"])
+    srv.close()
+    return {"requests": len(done), "arrival_rate_per_s": 20.0, "window_s": args.serve_seconds,
+            "budget_bytes": 40 << 30, "stop": "relative residual 1e-4, at most 2000 iterations",
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "converged": int(sum(1 for _, inf in done.values() if inf["converged"])),
+            "makespan_s": last - first, "value": work / (last - first), "unit": UNIT,
+            "iterations_by_kind": {k: {"n": len(v), "mean": float(np.mean(v))} for k, v in kinds.items()},
+            "fp64_alone_s_estimate": work / f64_rate,
+            "fp64_note": "the same voxel-iterations at the plain FP64 path's measured rate on the bench volume"}
 
 
 def oracle_cpu_baseline(d, w, iters=1, nthreads=0):
@@ -488,6 +562,13 @@ def main():
                          "pcg_iterations": int(rp["hist"][:, 2].sum()),
                          "pcg_per_gn": [int(x) for x in rp["hist"][:, 2]], "J": rp["J"]}
 
+    # serving (continuous batching, Poisson arrivals of mixed-size requests,
+    # 40 GB device budget, stop at relative residual 1e-4): per-request latency
+    # and throughput
+    serving = None
+    if args.serve_seconds > 0 and rank == 0 and world == 1:
+        serving = serve_run(args, sac, d, w, f64_val)
+
     # roofline of the dominant kernel (largest summed device time in the timed region)
     roof, kernels = roofline(prof, w, g, nf, sac)
     cpu = None
@@ -510,6 +591,7 @@ def main():
                              "mixed_over_f64": value / world / f64_val},
                 "time_to_solution": tts,
                 "gnpcg_preconditioners": pcg,
+                "serving": serving,
                 "context": "paper: < 50 s for > 5M dof, three-level ADMM, MATLAB on a laptop CPU"}
         print(json.dumps(line), flush=True)
     if dist:
