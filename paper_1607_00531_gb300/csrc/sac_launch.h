@@ -139,6 +139,8 @@ struct TcCfg {
     int lmax = 0;                    // longest contracted axis of the launch
     int caseB = 0;                   // the contracted axis is the fastest one (first job)
     int tn = 0;                      // 1: the lines-in-N kernel (zstep_tcn.cu), sr = its ring stages
+    int raw_st = 0;                  // lines-in-N kernel: stages of its raw X ring (TMA copies; 0: none)
+    uint32_t raw_off = 0;            // and its shared-memory offset
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
 constexpr int kTcMaps = 12;          // TMA tensor maps per job: [pass][source] X sources, then [pass] outputs

@@ -164,11 +164,23 @@ bool tc_cfg_finish(TcCfg* c) {
         const size_t slot = 2 * 128 * tc::kBK * 4;
         const size_t stage = (c->caseB && (c->lmax & 3) == 0) ? (size_t)128 * c->lmax * 4 : 0;
         const size_t avail = 226 * 1024 - 2 * stage;
-        c->sr = (int)(avail / slot);
+        // split-operand stages, then a ring of raw X chunks (TMA copies of 32
+        // values of j x 128 lines per source) from what is left: at least 3
+        // raw stages, at least 2 split stages
+        c->raw_st = 0;
+        const size_t rslot = c->rslot;
+        if (rslot > 0 && avail >= 2 * slot + 3 * rslot) {
+            c->raw_st = (int)((avail - 2 * slot) / rslot);
+            if (c->raw_st > 4) c->raw_st = 4;
+            c->sr = (int)((avail - (size_t)c->raw_st * rslot) / slot);
+        } else {
+            c->sr = (int)(avail / slot);
+        }
         if (c->sr > 6) c->sr = 6;
         if (c->sr < 2) return false;
-        c->epi_off = (uint32_t)(c->sr * slot);
-        c->smem = c->sr * slot + 2 * stage;
+        c->raw_off = (uint32_t)(c->sr * slot);
+        c->epi_off = (uint32_t)(c->sr * slot + (size_t)c->raw_st * rslot);
+        c->smem = c->epi_off + 2 * stage;
         return true;
     }
     const size_t budget = 226 * 1024 - tc::kEpiBytes;   // rings; 1 KB of static shared memory

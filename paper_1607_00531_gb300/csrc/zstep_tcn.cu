@@ -15,9 +15,12 @@
 // memory traffic saturates the SM; with the DCT resident in TMEM and 128
 // lines per MMA both limits move out of the way.
 //
-// Warps: 0-7 load X from global memory (warp w: lines 32 (w % 4) .. +31,
-// K values 16 (w / 4) .. +15 of each 32-wide chunk), split it and store the
-// K-major operand chunk into a shared-memory ring; 8-15 drain the two
+// Warps: 17 copies the raw X chunks (32 values of j x 128 lines per source)
+// into a shared-memory ring with TMA tensor copies (the tensor maps of
+// zstep_tc.cu), when the job has them and the launch has room for the ring;
+// 0-7 read them (or load X from global memory themselves), warp w taking lines
+// 32 (w % 4) .. +31 and K values 16 (w / 4) .. +15 of each chunk, split them
+// and store the K-major operand chunk into a second ring; 8-15 drain the two
 // accumulator buffers (TMEM lane = k, so for each line the 32 k of a warp are
 // consecutive in memory when the axis is the fastest one); warp 16 owns TMEM
 // and one thread issues the MMAs.  Every wait is bounded (tc_ptx.cuh); a wait
@@ -38,12 +41,15 @@ constexpr int kEpiBar = 1;   // named barrier of the epilogue warps
 constexpr int kConvWarps = 8;
 constexpr int kEpiWarps = 8;
 constexpr int kMmaWarp = kConvWarps + kEpiWarps;
-constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kXWarp = kMmaWarp + 1;            // TMA copies of the raw X chunks
+constexpr int kThreads = (kXWarp + 1) * 32;
 constexpr int kBK = 32;                         // K chunk
 constexpr int kLines = 128;                     // lines per tile (MMA N)
 constexpr uint32_t kHalf = kLines * kBK * 4;    // hi (or lo) half of an X slot (16 KB)
 constexpr uint32_t kSlot = 2 * kHalf;
 constexpr int kMaxStages = 6;
+constexpr int kMaxRaw = 4;                      // raw X ring stages
+constexpr uint32_t kRawBytes = kLines * kBK * 4;   // one source's raw chunk (16 KB)
 constexpr uint32_t kTmemCols = 512;
 // epilogue warps: barrier, and barrier with an AND of a predicate
 __device__ __forceinline__ void epi_bar() {
@@ -117,8 +123,9 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
     using namespace tcn;
     constexpr int NSRC = (PASS == 0) ? 2 : 1;   // X sources (pass 0: b + u)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // barriers: X slot full / empty, accumulator full / empty, drain
-    __shared__ __align__(8) unsigned long long bar[2 * kMaxStages + 5];
+    // barriers: X slot full / empty, accumulator full / empty, drain, raw X
+    // chunk full / empty
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxStages + 5 + 2 * kMaxRaw + 1];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int* abort = &abort_flag;
@@ -128,8 +135,12 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
     const uint32_t b_afull = b_xempty + 8 * kMaxStages;
     const uint32_t b_aempty = b_afull + 16;
     const uint32_t b_drain = b_aempty + 16;
+    const uint32_t b_rfull = b_drain + 8;
+    const uint32_t b_rempty = b_rfull + 8 * kMaxRaw;
+    const uint32_t b_dct = b_rempty + 8 * kMaxRaw;   // the DCT is in TMEM
     const uint32_t s_base = smem_u32(smem_raw);
     const int sx = cfg.sr;                      // X ring stages
+    const int srw = cfg.raw_st;                 // raw X ring stages (0: no TMA copies)
 
     if (tid == 0) {
         for (int i = 0; i < kMaxStages; ++i) {
@@ -141,6 +152,11 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
             mbar_init(b_aempty + 8 * i, kEpiWarps);
         }
         mbar_init(b_drain, 1);
+        for (int i = 0; i < kMaxRaw; ++i) {
+            mbar_init(b_rfull + 8 * i, 1);
+            mbar_init(b_rempty + 8 * i, kConvWarps);
+        }
+        mbar_init(b_dct, kEpiWarps);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -151,33 +167,47 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
     const uint32_t tmem = tmem_slot;
     // every job of the launch has the same geometry: one DCT matrix (that of
     // the job of tile 0), loaded into TMEM columns [0, Kp) (hi) and [Kp, 2 Kp)
-    // (lo) by the epilogue warps
+    // (lo) by the epilogue warps at the start of their role, 48 columns per
+    // round of loads; the MMA warp waits for it on b_dct while the X copies
+    // and conversions of the first chunks are already under way
     const Job& J0 = jobs[find_job(prefix, njobs, 0)];
     const TcPass g0 = tc_pass_geom(J0.F, J0.ax1, J0.ax2, PASS);
     const int Kp = 32 * g0.nch;
     const uint32_t acc0 = (uint32_t)(2 * Kp);   // accumulator buffers at acc0 + 128 a
+    const long long t0 = blockIdx.x, dt = gridDim.x;
     if (warp >= kConvWarps && warp < kMmaWarp) {
         const int q = warp & 3, h = (warp - kConvWarps) >> 2;
         const float* __restrict__ Mt = (const float*)J0.Ctn[PASS] + (size_t)h * kLines * Kp;
         const int k = 32 * q + lane;
-        for (int j0 = 0; j0 < Kp; j0 += 16) {
-            float v[16];
+        for (int j0 = 0; j0 < Kp; j0 += 48) {
+            float v[3][16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = __ldg(Mt + (size_t)(j0 + e) * kLines + k);
-            tmem_st16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * Kp + j0), v);
+            for (int b = 0; b < 3; ++b)
+                if (j0 + 16 * b < Kp) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[b][e] = __ldg(Mt + (size_t)(j0 + 16 * b + e) * kLines + k);
+                }
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                if (j0 + 16 * b < Kp)
+                    tmem_st16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * Kp + j0 + 16 * b), v[b]);
         }
         tmem_st_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(b_dct);
     }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const long long t0 = blockIdx.x, dt = gridDim.x;
 
     if (warp < kConvWarps) {
-        // ------------------------------------------------ X: global -> split operand chunks
+        // ------------------------------------------------ X: raw chunks -> split operand chunks
+        // Where the job's sources have tensor maps and the launch has a raw
+        // ring, the X warp copies each chunk (32 values of j x 128 lines per
+        // source) with TMA and the converters read it from shared memory
+        // (contiguous lines: [line][32] with the 128-byte swizzle; strided:
+        // [32][line]); otherwise they load it from global memory.
         const int q = warp & 3, kh = warp >> 2;
         const int lr = 32 * q + lane;
-        RingPos xr;
+        RingPos xr, rr;
         bool run = true;
         for (long long t = t0; t < total && run; t += dt) {
             const int jid = find_job(prefix, njobs, t);
@@ -201,43 +231,70 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
             }
             const bool lv = lr < nl;
             const bool vec = g.caseB && (g.L & 3) == 0;
+            const bool tma = srw > 0 && ((J.tc_tma >> PASS) & 1);
             const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
                                          : (PASS == 2) ? (const float*)J.t2 : (const float*)J.t1;
             const float* __restrict__ X1 = (const float*)J.u;   // pass 0 only
             const float us = (float)J.uscale;                    // pass 0: b + uscale u
-            auto load = [&](int c, float (&v)[16]) {
-                const int j0 = c * kBK + 16 * kh;
-                if (vec) {
+            for (int c = 0; c < g.nch; ++c) {
+                float v[16];
+                if (tma) {
+                    const int rs = rr.slot;
+                    const bool okr = mbar_wait_ab(b_rfull + 8 * rs, rr.phase, abort);
+                    if (!__all_sync(kFull, okr)) { run = false; break; }
+                    const unsigned char* rb = smem_raw + cfg.raw_off + (size_t)rs * cfg.rslot;
+                    if (g.caseB) {
 #pragma unroll
-                    for (int gq = 0; gq < 4; ++gq) {
-                        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (lv && j0 + 4 * gq < g.L) {
-                            x = __ldg(reinterpret_cast<const float4*>(X0 + base + j0 + 4 * gq));
+                        for (int gq = 0; gq < 4; ++gq) {
+                            const uint32_t off = (uint32_t)lr * 128u + (uint32_t)(((4 * kh + gq) ^ (lr & 7)) << 4);
+                            float4 x = *reinterpret_cast<const float4*>(rb + off);
                             if (NSRC == 2) {
-                                const float4 y = __ldg(reinterpret_cast<const float4*>(X1 + base + j0 + 4 * gq));
+                                const float4 y = *reinterpret_cast<const float4*>(rb + kRawBytes + off);
                                 x.x += us * y.x; x.y += us * y.y; x.z += us * y.z; x.w += us * y.w;
                             }
+                            v[4 * gq] = x.x; v[4 * gq + 1] = x.y; v[4 * gq + 2] = x.z; v[4 * gq + 3] = x.w;
                         }
-                        v[4 * gq] = x.x; v[4 * gq + 1] = x.y; v[4 * gq + 2] = x.z; v[4 * gq + 3] = x.w;
-                    }
-                } else {
+                    } else {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        float x = 0.f;
-                        if (lv && j0 + e < g.L) {
-                            const long long a = base + (long long)(j0 + e) * js;
-                            x = __ldg(X0 + a);
-                            if (NSRC == 2) x += us * __ldg(X1 + a);
+                        for (int e = 0; e < 16; ++e) {
+                            const uint32_t off = (uint32_t)((16 * kh + e) * kLines + lr) * 4u;
+                            float x = *reinterpret_cast<const float*>(rb + off);
+                            if (NSRC == 2) x += us * *reinterpret_cast<const float*>(rb + kRawBytes + off);
+                            v[e] = x;
                         }
-                        v[e] = x;
+                    }
+                    // the raw slot may be refilled once every converter warp has its values
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_rempty + 8 * rs);
+                    rr.next(srw);
+                } else {
+                    const int j0 = c * kBK + 16 * kh;
+                    if (vec) {
+#pragma unroll
+                        for (int gq = 0; gq < 4; ++gq) {
+                            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (lv && j0 + 4 * gq < g.L) {
+                                x = __ldg(reinterpret_cast<const float4*>(X0 + base + j0 + 4 * gq));
+                                if (NSRC == 2) {
+                                    const float4 y = __ldg(reinterpret_cast<const float4*>(X1 + base + j0 + 4 * gq));
+                                    x.x += us * y.x; x.y += us * y.y; x.z += us * y.z; x.w += us * y.w;
+                                }
+                            }
+                            v[4 * gq] = x.x; v[4 * gq + 1] = x.y; v[4 * gq + 2] = x.z; v[4 * gq + 3] = x.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            float x = 0.f;
+                            if (lv && j0 + e < g.L) {
+                                const long long a = base + (long long)(j0 + e) * js;
+                                x = __ldg(X0 + a);
+                                if (NSRC == 2) x += us * __ldg(X1 + a);
+                            }
+                            v[e] = x;
+                        }
                     }
                 }
-            };
-            float v[16];
-            load(0, v);
-            for (int c = 0; c < g.nch; ++c) {
-                float vn[16];
-                if (c + 1 < g.nch) load(c + 1, vn);   // in flight while chunk c is stored
                 const int xs = xr.slot;
                 const bool ok = mbar_wait_ab(b_xempty + 8 * xs, xr.phase ^ 1u, abort);
                 if (!__all_sync(kFull, ok)) { run = false; break; }
@@ -257,18 +314,58 @@ __global__ void __launch_bounds__(tcn::kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_xfull + 8 * xs);
                 xr.next(sx);
-                if (c + 1 < g.nch) {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) v[e] = vn[e];
-                }
             }
+        }
+    } else if (warp == kXWarp) {
+        // ------------------------------------------------ raw X chunks (TMA tensor copies)
+        if (lane == 0 && srw > 0) {
+            long long r_it = 0;
+            RingPos rr;
+            for (long long t = t0; t < total && !*abort; t += dt) {
+                const int jid = find_job(prefix, njobs, t);
+                const Job& J = jobs[jid];
+                if (!J.active || !((J.tc_tma >> PASS) & 1)) continue;
+                const TcPass g = tc_pass_geom(J.F, J.ax1, J.ax2, PASS);
+                const long long local = t - prefix[jid];
+                const char* maps = (const char*)J.tmaps + (size_t)2 * PASS * 128;
+                long long line0 = 0, pr = 0, po0 = 0;
+                if (g.caseB) {
+                    line0 = local * kLines;
+                } else {
+                    const long long tpp = (g.post + kLines - 1) / kLines;
+                    pr = local / tpp;
+                    po0 = (local - pr * tpp) * kLines;
+                }
+                bool ok = true;
+                for (int c = 0; c < g.nch; ++c) {
+                    const int rs = rr.slot;
+                    if (!mbar_wait_ab(b_rempty + 8 * rs, rr.phase ^ 1u, abort)) { ok = false; break; }
+                    const uint32_t dst = s_base + cfg.raw_off + (uint32_t)rs * cfg.rslot;
+                    mbar_expect_tx(b_rfull + 8 * rs, NSRC * kRawBytes);
+#pragma unroll
+                    for (int i = 0; i < NSRC; ++i) {
+                        if (g.caseB)
+                            tma_tile2d(dst + i * kRawBytes, maps + 128 * i, c * kBK, (int)line0, b_rfull + 8 * rs);
+                        else
+                            tma_tile3d(dst + i * kRawBytes, maps + 128 * i, (int)po0, c * kBK, (int)pr, b_rfull + 8 * rs);
+                    }
+                    ++r_it;
+                    rr.next(srw);
+                }
+                if (!ok) break;
+            }
+            // copies still in flight land before the CTA exits
+            for (long long i = (r_it > srw ? r_it - srw : 0); i < r_it; ++i)
+                mbar_wait_drain(b_rfull + 8 * (int)(i % srw), (uint32_t)((i / srw) & 1));
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
             RingPos xr, ar;
             const uint32_t idesc = idesc_tf32(128, kLines);
-            for (long long t = t0; t < total && !*abort; t += dt) {
+            const bool dct_ok = mbar_wait_ab(b_dct, 0, abort);   // the A operand is in TMEM
+            fence_after();
+            for (long long t = t0; t < total && dct_ok && !*abort; t += dt) {
                 const int jid = find_job(prefix, njobs, t);
                 const Job& J = jobs[jid];
                 if (!J.active) continue;
