@@ -803,19 +803,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 // with one set of partial sums per block of
 //   |b - z^{k+1}|^2, |z^{k+1} - z^k|^2, |b|^2, |z^{k+1}|^2, |u^{k+1}|^2
 // (the residuals of the stopping test).  A block covers kAdmmFaces
-// consecutive faces of one job in kAdmmIters rounds of 16 loads per thread
-// (about four blocks per SM for a volume of 5M faces, all resident at once);
+// consecutive faces of one job in kAdmmIters rounds of 8 loads per thread;
+// at most 64 registers let four blocks share an SM, so that the 514 blocks of
+// a volume of 5.26M faces are all resident at once (one wave, no tail);
 // blocks of a stopped job write zeros.  With chk.counters set, the last
 // block of a job to finish (counted with an atomic after a fence) also runs
 // the job's stopping test on the job's partial sums.
 constexpr int kAdmmThreads = 256;
-constexpr int kAdmmGroups = 4;                                  // float4 groups per thread and round
-constexpr int kAdmmIters = 2;
+constexpr int kAdmmGroups = 2;                                  // float4 groups per thread and round
+constexpr int kAdmmIters = 5;
 constexpr long long kAdmmFaces = (long long)kAdmmThreads * kAdmmGroups * 4 * kAdmmIters;
 
 long long admm_update_blocks(long long nf) { return (nf + kAdmmFaces - 1) / kAdmmFaces; }
 
-__global__ void __launch_bounds__(kAdmmThreads) k_admm_update(Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kAdmmThreads, 4) k_admm_update(Job* __restrict__ jobs, int njobs,
                                                               const long long* __restrict__ prefix,
                                                               double* __restrict__ part, AdmmCheck chk) {
     __shared__ double red[32 * 5];
