@@ -6,13 +6,18 @@
 // line l.  The lines must be strided (PE axis not the last one): face p of
 // the NL lines is then a run of NL consecutive floats of every face and cell
 // array, and the CTA stages the five arrays of its lines (I1, I2, b, z, u) in
-// shared memory as [p][line] rows with 16-byte asynchronous copies (one
-// round trip; all later reads, including the image values at the displaced
-// points, are shared-memory reads).  A CTA of 16 lines holds about 80 KB for
-// lines of 257 faces, so two CTAs share an SM and one CTA's staging, barriers
-// and serial steps overlap the other's arithmetic (8 lines per CTA, four CTAs
-// per SM, measured no faster: the warp holding the boundary segments then
-// covers a quarter of the CTA).
+// shared memory as [p][line] rows (all later reads, including the image
+// values at the displaced points, are shared-memory reads): ten TMA tensor
+// copies of 16 lines x half the rows, issued by one warp and completing on an
+// mbarrier, or per-thread asynchronous copies where the rows are not 16-byte
+// aligned.  The CTAs are persistent (two per SM for lines of 257 faces, about
+// 100 KB each) and take tiles strided by the grid; as soon as a tile's forward
+// elimination is done, its images, z and u are dead and the CTA starts the
+// copies of its next tile (b into a second buffer), so that they run under
+// the rest of the tile (reduced solve, back substitution, bound tests,
+// write-back) instead of in a burst with no arithmetic beside it.  (8 lines
+// per CTA and four CTAs per SM measured no faster: the warp holding the
+// boundary segments then covers a quarter of the CTA.)
 //
 // Per line the step is the first pass of the active-set method with an empty
 // working set (the unconstrained Gauss-Newton step of the b-subproblem):
@@ -22,16 +27,23 @@
 // them so that every unknown of the segment depends only on the segment's
 // first and last unknowns (partitioned Thomas elimination); the 2G
 // remaining unknowns of a line form a tridiagonal system with unit diagonal
-// that one thread per line solves by the Thomas algorithm.  As in the
+// that one warp per line solves by parallel cyclic reduction.  As in the
 // warp-per-line kernel (line_kernels.cuh), a line whose step would cross
 // |D1 b| = 1 (a blocking constraint) or, when near_bound > 0, would end
 // within near_bound of the bound keeps b^k and is queued for the full
 // active-set method.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include "sac_dev.cuh"
 #include "sac_launch.h"
+#include "tc_ptx.cuh"
 
 namespace sac {
 namespace seg {
+
+using namespace tcx;
 
 constexpr int kMaxSeg = 16;    // segments per line
 constexpr int kLines = 16;     // lines per CTA (a multiple of 4: 16-byte copies)
@@ -157,13 +169,108 @@ __device__ __forceinline__ void stage(float* __restrict__ dst, const float* __re
     }
 }
 
-// images with two zero rows on each side, then b, z, u
-size_t smem_bytes(int m) { return sizeof(float) * (size_t)kLines * (size_t)(2 * (m + 4) + 3 * (m + 1)); }
+// Rows per TMA box (two boxes per array and tile): images from row -2 to at
+// least row m + 1 (the zero rows are the copies' out-of-range fill), face
+// arrays rows 0 .. m.  Even, so that the second box starts on a 128-byte
+// boundary of shared memory as a tensor copy requires (rows of 64 bytes).
+__host__ __device__ constexpr int img_box_rows(int m) { return ((m + 5) / 2 + 1) & ~1; }
+__host__ __device__ constexpr int face_box_rows(int m) { return ((m + 2) / 2 + 1) & ~1; }
+
+// two b buffers, the two images (from row -2), then z and u; every region
+// sized for the launch's longest line of mmax cells
+size_t smem_bytes(int mmax) {
+    return sizeof(float) * (size_t)kLines * (size_t)(4 * img_box_rows(mmax) + 8 * face_box_rows(mmax));
+}
+
+struct Regions {
+    float *b0, *b1, *I1, *I2, *z, *u;
+    __device__ __forceinline__ float* b(int i) const { return (i & 1) ? b1 : b0; }   // (no indexed array: no stack)
+};
+__device__ __forceinline__ Regions regions(float* sdyn, int mmax) {
+    const int ri = 2 * img_box_rows(mmax) * kLines, rf = 2 * face_box_rows(mmax) * kLines;
+    Regions r;
+    r.b0 = sdyn;
+    r.b1 = r.b0 + rf;
+    r.I1 = r.b1 + rf + 2 * kLines;   // row -2 of I1 is the region's first row
+    r.I2 = r.I1 + ri;
+    r.z = r.I2 - 2 * kLines + ri;
+    r.u = r.z + rf;
+    return r;
+}
+
+// Issues the copies of tile t (nothing for a tile of an inactive job) into the
+// image, z and u regions and the b buffer sB.  With the job's staging maps
+// one thread issues ten TMA tensor copies (two boxes of 16 lines x rows per
+// array) completing on the mbarrier `bar`; otherwise every thread issues
+// 16-byte (4-byte for unaligned rows) asynchronous copies and the images'
+// zero rows are plain stores, completed by cp.async.wait_all.  A CTA barrier
+// follows either.
+__device__ __forceinline__ void stage_tile(const Job* __restrict__ jobs, int njobs,
+                                           const long long* __restrict__ prefix, long long t, const Regions& R,
+                                           float* sB, uint32_t bar) {
+    constexpr int NL = kLines;
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    if (!J.active) return;
+    const int m = J.mpe, ni = J.n_inner;
+    const long long L0 = (t - prefix[jid]) * NL;
+    if (J.seg_tma) {
+        // the last full warp: lane 0 sets the transaction count, lanes 0..9
+        // issue one box each (array i / 2, half i % 2)
+        if ((int)(threadIdx.x >> 5) == (int)(blockDim.x >> 5) - 1) {
+            const int q = threadIdx.x & 31;
+            const int ri = img_box_rows(m), rf = face_box_rows(m);
+            if (q == 0) {
+                bulk_wait_read0();   // the tensor store of the buffer's previous tile has read it
+                mbar_expect_tx(bar, (uint32_t)(sizeof(float) * NL * (4 * ri + 6 * rf)));
+            }
+            __syncwarp();
+            if (q < 10) {
+                // lines L0 .. L0 + 15: inner index x (a multiple of 16:
+                // 64-byte aligned), outer index o
+                const long long o = L0 / ni;
+                const int x = (int)(L0 - o * ni), ai = q >> 1, hf = q & 1;
+                const int rows = (ai < 2) ? ri : rf;
+                float* dst = (ai == 0) ? R.I1 - 2 * NL : (ai == 1) ? R.I2 - 2 * NL : (ai == 2) ? sB : (ai == 3) ? R.z : R.u;
+                const char* map = (const char*)J.tmaps + (size_t)(kSegMap0 + ai) * 128;
+                tma_tile3d(smem_u32(dst + hf * rows * NL), map, x, (ai < 2 ? -2 : 0) + hf * rows, (int)o, bar);
+            }
+        }
+        return;
+    }
+    const long long nlines = (long long)J.n_outer * ni;
+    // with ni a multiple of NL and 16-byte aligned arrays, a tile is one
+    // aligned run of NL floats in every row
+    const uintptr_t any = (uintptr_t)J.I1 | (uintptr_t)J.I2 | (uintptr_t)J.b | (uintptr_t)J.z | (uintptr_t)J.u;
+    const bool vec = (ni % NL) == 0 && (any & 15) == 0;
+    stage(R.I1, (const float*)J.I1, m, ni, L0, nlines, vec);
+    stage(R.I2, (const float*)J.I2, m, ni, L0, nlines, vec);
+    stage(sB, (const float*)J.b, m + 1, ni, L0, nlines, vec);
+    stage(R.z, (const float*)J.z, m + 1, ni, L0, nlines, vec);
+    stage(R.u, (const float*)J.u, m + 1, ni, L0, nlines, vec);
+    for (int e = threadIdx.x; e < 8 * NL; e += blockDim.x) {
+        // zero rows -2, -1, m, m+1 of both images
+        const int r = e / NL, l = e % NL;
+        float* img = (r < 4) ? R.I1 : R.I2;
+        const int row = (r & 3) < 2 ? (r & 3) - 2 : m + (r & 3) - 2;
+        img[row * NL + l] = 0.f;
+    }
+}
+
+// the pending tensor store of a tile's b buffer (two boxes; rows past the
+// line's last face are outside the tensor and not written)
+__device__ __forceinline__ void store_b(const long long* pend, const Regions& R) {
+    const void* map = (const void*)pend[0];
+    const int x = (int)pend[1], z = (int)pend[2], rf = (int)pend[3];
+    const float* src = R.b((int)pend[4]);
+    tma_store3d(map, smem_u32(src), x, 0, z);
+    tma_store3d(map, smem_u32(src + rf * kLines), x, rf, z);
+}
 
 template <int S>
 __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
-    k_bstep_seg(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, float near_bound,
-                unsigned long long* __restrict__ rlist, int* __restrict__ rcount, int rcap,
+    k_bstep_seg(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, int mmax,
+                float near_bound, unsigned long long* __restrict__ rlist, int* __restrict__ rcount, int rcap,
                 int* __restrict__ status) {
     static_assert(S >= 4, "a segment needs at least 4 faces");
     constexpr int NL = kLines;
@@ -174,53 +281,67 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     __shared__ float sX[2][kMaxSeg][NL];
     __shared__ int sFlag[NL];
     __shared__ int sDmax[NL];
-    extern __shared__ __align__(16) float sdyn[];
+    extern __shared__ __align__(128) float sdyn[];   // TMA destinations: 128-byte aligned
     // segment of the thread: the first and the last segment (the ones with
     // boundary rows) share warp 0, the interior ones follow in order
     const int lane = threadIdx.x % NL, gi = threadIdx.x / NL;
-    const long long t = blockIdx.x;
-    if (t >= prefix[njobs]) return;
-    const int jid = find_job(prefix, njobs, t);
-    const Job& J = jobs[jid];
-    if (!J.active) return;
-    const int m = J.mpe, ni = J.n_inner;
-    const int G = (m + S) / S;   // segments of this line: ceil((m + 1) / S)
-    const int g = (gi == 0) ? 0 : (gi == 1) ? G - 1 : gi - 1;
-    if (G * NL > (int)blockDim.x) {   // the host sizes the CTA for the longest line
-        if (threadIdx.x == 0) atomicOr(status, kStTimeout);
-        return;
-    }
-    const long long nlines = (long long)J.n_outer * ni;
-    const long long L0 = (t - prefix[jid]) * NL;
-    float* sI1 = sdyn + 2 * NL;
-    float* sI2 = sI1 + (m + 4) * NL;
-    float* sB = sI2 + (m + 2) * NL;
-    float* sZ = sB + (m + 1) * NL;
-    float* sU = sZ + (m + 1) * NL;
-    {
-        // with ni a multiple of NL and 16-byte aligned arrays, a tile is one
-        // aligned run of NL floats in every row
-        const uintptr_t any = (uintptr_t)J.I1 | (uintptr_t)J.I2 | (uintptr_t)J.b | (uintptr_t)J.z | (uintptr_t)J.u;
-        const bool vec = (ni % NL) == 0 && (any & 15) == 0;
-        stage(sI1, (const float*)J.I1, m, ni, L0, nlines, vec);
-        stage(sI2, (const float*)J.I2, m, ni, L0, nlines, vec);
-        stage(sB, (const float*)J.b, m + 1, ni, L0, nlines, vec);
-        stage(sZ, (const float*)J.z, m + 1, ni, L0, nlines, vec);
-        stage(sU, (const float*)J.u, m + 1, ni, L0, nlines, vec);
-        for (int e = threadIdx.x; e < 8 * NL; e += blockDim.x) {
-            // zero rows -2, -1, m, m+1 of both images
-            const int r = e / NL, l = e % NL;
-            float* img = (r < 4) ? sI1 : sI2;
-            const int row = (r & 3) < 2 ? (r & 3) - 2 : m + (r & 3) - 2;
-            img[row * NL + l] = 0.f;
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    }
-    if (gi == 0) {
-        sFlag[lane] = 0;
-        sDmax[lane] = 0;
+    const Regions Rg = regions(sdyn, mmax);
+    __shared__ __align__(8) unsigned long long sBar;   // TMA staging: one phase per staged tile
+    __shared__ int sAbort;
+    // tensor store of a tile's b^{k+1} from its b buffer, issued at the next
+    // loop top (after a CTA barrier) by the issuing thread: map, x, outer
+    // index, box rows, buffer; valid when sPend[4] >= 0
+    __shared__ long long sPend[5];
+    const bool issuer = threadIdx.x == ((blockDim.x >> 5) - 1) * 32;
+    const uint32_t bar = smem_u32(&sBar);
+    if (issuer) sPend[4] = -1;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        sAbort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const long long total = prefix[njobs];
+    if ((long long)blockIdx.x < total) stage_tile(jobs, njobs, prefix, blockIdx.x, Rg, Rg.b(0), bar);
+    int it = 0;
+    uint32_t nwait = 0;   // TMA-staged tiles consumed (the parity of the next phase)
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+    const int jid = find_job(prefix, njobs, t);
+    const Job& J = jobs[jid];
+    bool lost = false;
+    if (J.active && J.seg_tma) lost = !mbar_wait_ab(bar, (nwait++) & 1u, &sAbort);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // tile t staged; every thread is done with the previous tile
+    if (__syncthreads_or(lost)) {
+        // a copy that never completed (bounded wait): report, wait once more
+        // (bounded) for the copies in flight, leave
+        if (threadIdx.x == 0) {
+            atomicOr(status, kStTimeout);
+            mbar_wait_drain(bar, (nwait - 1) & 1u);
+        }
+        break;
+    }
+    if (issuer && sPend[4] >= 0) {
+        store_b(sPend, Rg);
+        sPend[4] = -1;
+    }
+    const long long tn = t + gridDim.x;
+    float* sB = Rg.b(it);
+    const int m = J.mpe, ni = J.n_inner;
+    const int G = (m + S) / S;   // segments of this line: ceil((m + 1) / S)
+    if (!J.active || G * NL > (int)blockDim.x) {
+        // (the host sizes the CTA for the longest line of the launch)
+        if (J.active && threadIdx.x == 0) atomicOr(status, kStTimeout);
+        if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
+        continue;
+    }
+    const int g = (gi == 0) ? 0 : (gi == 1) ? G - 1 : gi - 1;
+    const long long nlines = (long long)J.n_outer * ni;
+    const long long L0 = (t - prefix[jid]) * NL;
+    const float* sI1 = Rg.I1;
+    const float* sI2 = Rg.I2;
+    const float* sZ = Rg.z;
+    const float* sU = Rg.u;
     const long long L = L0 + lane;
     const bool valid = L < nlines;   // rows of lanes past the last line are not staged
     const float h = (float)J.hpe, inv_h = 1.f / h, ih2 = inv_h * inv_h;
@@ -261,46 +382,43 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         sE[5][g][lane] = R[S - 1];
     }
     __syncthreads();
-    if (threadIdx.x < 2 * NL) {
+    // the images, z, u and the other b buffer are free: copy the next tile
+    if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
+    if (gi == 0) {
+        sFlag[lane] = 0;
+        sDmax[lane] = 0;
+    }
+    {
         // The line's reduced system: unknown 2q = first of segment q, 2q+1 =
-        // its last; row r couples r-1 (a) and r+1 (c), unit diagonal.  Warp
-        // 0 holds the first and the last segment of every line; its threads
-        // l < NL eliminate rows 0 .. G-1 downwards, threads NL + l rows 2G-1
-        // .. G upwards (a two-ended Thomas elimination: half the serial
-        // chain), the two meet in a 2 x 2 system and substitute back outwards.
-        constexpr int kC = kMaxSeg * NL;   // stride between components
-        constexpr unsigned kPair = (2 * NL >= 32) ? 0xffffffffu : ((1u << (2 * NL)) - 1u);
-        const bool top = threadIdx.x < NL;
-        const int N = 2 * G, M = G, dir = top ? 1 : -1;
-        const int obk = top ? 0 : kC, ofw = top ? kC : 0;   // a / c: towards the done / open side
-        float* base = &sE[0][0][lane];
-        auto row = [&](int r) { return base + (r & 1) * 3 * kC + (r >> 1) * NL; };
-        int r = top ? 0 : N - 1;
-        float fp = row(r)[ofw], dp = row(r)[2 * kC];
-#pragma unroll 4
-        for (int k = 1; k < M; ++k) {
-            r += dir;
-            float* e = row(r);
-            const float bk = e[obk], fw = e[ofw], d = e[2 * kC];
-            const float inv = fdiv(1.f, 1.f - bk * fp);
-            fp = fw * inv;
-            dp = (d - bk * dp) * inv;
-            e[ofw] = fp;
-            e[2 * kC] = dp;
-        }
-        // top: x_{M-1} + c' x_M = d'; bottom: a'' x_{M-1} + x_M = d''
-        const float of = __shfl_xor_sync(kPair, fp, NL), od = __shfl_xor_sync(kPair, dp, NL);
-        const float ct = top ? fp : of, dt = top ? dp : od, ab = top ? of : fp, db = top ? od : dp;
-        const float xm1 = fdiv(dt - ct * db, 1.f - ct * ab);
-        float x = top ? xm1 : db - ab * xm1;
-        r = top ? M - 1 : M;
-        sX[r & 1][r >> 1][lane] = x;
-#pragma unroll 4
-        for (int k = 1; k < M; ++k) {
-            r -= dir;
-            const float* e = row(r);
-            x = e[2 * kC] - e[ofw] * x;
-            sX[r & 1][r >> 1][lane] = x;
+        // its last; row r couples r-1 (a) and r+1 (c), unit diagonal; 2G <=
+        // 32 rows, solved by parallel cyclic reduction with one lane per row
+        // (rows 2G .. 31 are identity rows): at stride s every row eliminates
+        // its couplings to rows r -+ s with those rows, then is scaled back
+        // to a unit diagonal, so that after ceil(log2 2G) steps x_r = d_r.
+        // Every full warp of the CTA takes lines warp, warp + nw, ...
+        const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5), q = threadIdx.x & 31, N = 2 * G;
+        for (int l = w; l < NL && w < nw; l += nw) {   // (a partial last warp takes no line)
+            float a = 0.f, c = 0.f, d = 0.f;
+            if (q < N) {
+                const int e = 3 * (q & 1), sg = q >> 1;
+                a = sE[e][sg][l];
+                c = sE[e + 1][sg][l];
+                d = sE[e + 2][sg][l];
+            }
+            for (int st = 1; st < N; st <<= 1) {
+                float am = __shfl_up_sync(0xffffffffu, a, st), cm = __shfl_up_sync(0xffffffffu, c, st);
+                float dm = __shfl_up_sync(0xffffffffu, d, st);
+                float ap = __shfl_down_sync(0xffffffffu, a, st), cp = __shfl_down_sync(0xffffffffu, c, st);
+                float dp = __shfl_down_sync(0xffffffffu, d, st);
+                if (q < st) am = cm = dm = 0.f;          // beyond the first row: identity
+                if (q + st >= 32) ap = cp = dp = 0.f;    // beyond the last lane: identity
+                const float inv = fdiv(1.f, 1.f - a * cm - c * ap);
+                const float dn = (d - a * dm - c * dp) * inv;
+                a = -a * am * inv;
+                c = -c * cp * inv;
+                d = dn;
+            }
+            if (q < N) sX[q & 1][q >> 1][l] = d;
         }
     }
     __syncthreads();
@@ -348,9 +466,29 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         if (dmax > 0.f) atomicMax(&sDmax[lane], __float_as_int(dmax));
     }
     __syncthreads();
-    if (!valid) return;
     const bool queue = sFlag[lane] != 0 || (near_bound > 0.f && (1.f - __int_as_float(sDmax[lane])) < near_bound);
-    if (!queue) {
+    if (J.seg_tma) {
+        // b^{k+1} into the tile's b buffer (queued lines keep b^k there),
+        // copied out by tensor stores after the next CTA barrier
+        if (valid && !queue && on) {
+            float* wB = sB + lane;
+#pragma unroll
+            for (int k = 0; k < S; ++k)
+                if (s + S <= m + 1 || s + k <= m) wB[(s + k) * NL] += xs[k];
+            fence_async_smem();
+        }
+        if (issuer) {
+            const long long o = L0 / ni;
+            sPend[0] = (long long)(const char*)J.tmaps + (long long)(kSegMap0 + 2) * 128;
+            sPend[1] = L0 - o * ni;
+            sPend[2] = o;
+            sPend[3] = face_box_rows(m);
+            sPend[4] = it & 1;
+        }
+    }
+    if (!valid) {
+    } else if (queue) {
+    } else if (!J.seg_tma) {
         if (on) {
             const long long o = L / ni;
             float* gB = (float*)J.b + o * (long long)(m + 1) * ni + (L - o * ni) + (long long)s * ni;
@@ -363,10 +501,18 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
                     if (s + k <= m) gB[(long long)k * ni] = rB[(s + k) * NL] + xs[k];
             }
         }
-    } else if (gi == 0) {
+    }
+    if (valid && queue && gi == 0) {
         const int slot = atomicAdd(rcount, 1);
         if (slot < rcap) rlist[slot] = ((unsigned long long)jid << 40) | (unsigned long long)L;
         else atomicOr(status, kStTimeout);
+    }
+    }
+    // the last tile's store, then every store complete before the CTA ends
+    __syncthreads();
+    if (issuer) {
+        if (sPend[4] >= 0) store_b(sPend, Rg);
+        bulk_wait_all();
     }
 }
 
@@ -381,6 +527,35 @@ int seg_faces(int mpe, int n_inner, int n_sqp, bool mixed, int kernel) {
     return 0;
 }
 
+int seg_encode_maps(int n_outer, int m, int ni, const float* I1, const float* I2, const float* b, const float* z,
+                    const float* u, void* maps) {
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    CUtensorMap* out = (CUtensorMap*)maps + kSegMap0;
+    memset(out, 0, 5 * sizeof(CUtensorMap));
+    auto enc = (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
+    if (!enc || n_outer < 1 || m < 1 || ni < seg::kLines || ni % seg::kLines != 0) return 0;
+    const float* src[5] = {I1, I2, b, z, u};
+    for (int i = 0; i < 5; ++i) {
+        if (!src[i] || ((uintptr_t)src[i] & 15)) return 0;
+        // [n_outer][rows][ni]; box: the tile's 16 lines x half the rows
+        const long long rows = (i < 2) ? m : m + 1;
+        const cuuint64_t dim[3] = {(cuuint64_t)ni, (cuuint64_t)rows, (cuuint64_t)n_outer};
+        const cuuint64_t str[2] = {(cuuint64_t)ni * 4, (cuuint64_t)ni * rows * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)seg::kLines,
+                                   (cuuint32_t)((i < 2) ? seg::img_box_rows(m) : seg::face_box_rows(m)), 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (box[1] > 256) return 0;
+        const CUresult r = enc(&out[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)src[i], dim, str, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            memset(out, 0, 5 * sizeof(CUtensorMap));
+            return 0;
+        }
+    }
+    return 1;
+}
+
 int seg_warps(int mpe, int S) { return S > 0 ? (mpe + S) / S : 0; }
 int seg_lines() { return seg::kLines; }
 size_t seg_smem_bytes(int mpe) { return seg::smem_bytes(mpe); }
@@ -391,27 +566,62 @@ cudaError_t prepare_bstep_seg() {
     return allow_max_dyn_smem((const void*)seg::k_bstep_seg<17>);
 }
 
+namespace {
+// resident CTAs per SM of a variant for a block and shared-memory size (the
+// persistent grid), remembered per configuration
+int seg_resident(const void* k, int S, unsigned block, size_t smem) {
+    struct Entry {
+        int S;
+        unsigned block;
+        size_t smem;
+        int n;
+    };
+    static Entry cache[16];
+    static int used = 0;
+    for (int i = 0; i < used; ++i)
+        if (cache[i].S == S && cache[i].block == block && cache[i].smem == smem) return cache[i].n;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (int)block, smem) != cudaSuccess) return 0;
+    if (used < 16) cache[used++] = Entry{S, block, smem, n};
+    return n;
+}
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+    }
+    return n;
+}
+}  // namespace
+
 cudaError_t launch_bstep_seg(const LineLaunch& L) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.seg_G < 1 || L.seg_G > seg::kMaxSeg) return cudaErrorInvalidValue;
-    // at least two segments' threads: warp 0 pairs the first and the last
-    // segment of each line in the reduced solve
-    const unsigned grid = (unsigned)L.total_tiles, block = (unsigned)(seg::kLines * (L.seg_G > 2 ? L.seg_G : 2));
+    // at least two segments' threads: warp 0 holds the first and the last
+    // segment of every line
+    const unsigned block = (unsigned)(seg::kLines * (L.seg_G > 2 ? L.seg_G : 2));
     const size_t smem = seg::smem_bytes(L.seg_m);
     const float nb = (float)L.near_bound;
-    count_launch();
+    const void* k;
     switch (L.seg_S) {
-        case 9:
-            seg::k_bstep_seg<9><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, nb, L.rlist_out,
-                                                              L.rcount_out, L.rcap, L.status);
-            break;
-        case 17:
-            seg::k_bstep_seg<17><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, nb, L.rlist_out,
-                                                               L.rcount_out, L.rcap, L.status);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+        case 9: k = (const void*)seg::k_bstep_seg<9>; break;
+        case 17: k = (const void*)seg::k_bstep_seg<17>; break;
+        default: return cudaErrorInvalidValue;
     }
+    // persistent: every resident CTA takes the tiles t = blockIdx.x + i * grid
+    const int per_sm = seg_resident(k, L.seg_S, block, smem), sms = sm_count();
+    if (per_sm < 1 || sms < 1) return cudaErrorInvalidConfiguration;
+    const long long cap = (long long)per_sm * sms;
+    const unsigned grid = (unsigned)(L.total_tiles < cap ? L.total_tiles : cap);
+    count_launch();
+    if (L.seg_S == 9)
+        seg::k_bstep_seg<9><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, L.seg_m, nb, L.rlist_out,
+                                                          L.rcount_out, L.rcap, L.status);
+    else
+        seg::k_bstep_seg<17><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, L.seg_m, nb, L.rlist_out,
+                                                           L.rcount_out, L.rcap, L.status);
     return cudaGetLastError();
 }
 

@@ -245,7 +245,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
     size_t o_tn[4];
     for (int q = 0; q < 4; ++q) o_tn[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tn_floats[q] : 0));
-    size_t o_tmap = take(P->use_tc ? tc_map_bytes() : 0);
+    const bool maps = P->use_tc || P->seg_S > 0;   // TMA tensor maps of the z-step passes / the b-step
+    size_t o_tmap = take(maps ? tc_map_bytes() : 0);
     size_t o_arr[10];
     for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
     P->bytes = off;
@@ -263,7 +264,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
     for (int q = 0; q < 4; ++q) P->d_Ctn[q] = (P->use_tc && P->tn_floats[q]) ? (float*)(base + o_tn[q]) : nullptr;
     P->d_scale = (float*)(base + o_scale);
-    P->d_tmaps = P->use_tc ? (void*)(base + o_tmap) : nullptr;
+    P->d_tmaps = maps ? (void*)(base + o_tmap) : nullptr;
     P->d_status = (int*)(base + o_stat);
     P->d_rcount = P->d_status + 1;
     P->d_out = (double*)(base + o_out);
@@ -307,12 +308,19 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
     J.scale = P->d_scale;
     J.active = 1;
-    if (P->use_tc && P->d_tmaps && b && u && t1 && t2) {
-        // TMA tensor maps of the X sources of the tensor-core passes
-        std::vector<unsigned char> maps(tc_map_bytes());
+    const bool tc_maps = P->use_tc && P->d_tmaps && b && u && t1 && t2;
+    const bool seg_maps = P->seg_S > 0 && P->d_tmaps && I1 && I2 && b && z && u;
+    if (tc_maps || seg_maps) {
+        // TMA tensor maps: X sources and outputs of the tensor-core passes,
+        // the b-step's staging copies
+        std::vector<unsigned char> maps(tc_map_bytes(), 0);
         J.tmaps = P->d_tmaps;
-        J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)b, (const float*)u, (const float*)t1,
-                                  (const float*)t2, maps.data());
+        if (tc_maps)
+            J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)b, (const float*)u, (const float*)t1,
+                                      (const float*)t2, maps.data());
+        if (seg_maps)
+            J.seg_tma = seg_encode_maps(G.n_outer, G.mpe, G.n_inner, (const float*)I1, (const float*)I2,
+                                        (const float*)b, (const float*)z, (const float*)u, maps.data());
         SAC_CUDA(cudaMemcpyAsync(P->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
     }
     long long pref[24] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],

@@ -80,7 +80,7 @@ static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
         s.tc[q] = take(use_tc ? 4 * (size_t)tc_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
     for (int q = 0; q < 4; ++q)
         s.tn[q] = take(use_tc ? 4 * (size_t)tcn_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
-    s.tmap = take(use_tc ? tc_map_bytes() : 0);
+    s.tmap = take((use_tc || prec == SAC_MIXED) ? tc_map_bytes() : 0);   // z-step passes, b-step staging
     s.bytes = off;
     return s;
 }
@@ -328,12 +328,17 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         for (int q = 0; q < 4; ++q)
             J.Ctn[q] = (use_tc_ && tcn_matrix_floats(G.F, G.ax1, G.ax2, q)) ? (const void*)(s + L.tn[q]) : nullptr;
         for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
-        if (use_tc_) {
-            // TMA tensor maps of the X sources of the tensor-core passes
-            std::vector<unsigned char> maps(tc_map_bytes());
+        if (use_tc_ || prec == SAC_MIXED) {
+            // TMA tensor maps: X sources and outputs of the tensor-core
+            // passes, the segment b-step's staging copies
+            std::vector<unsigned char> maps(tc_map_bytes(), 0);
             J.tmaps = s + L.tmap;
-            J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)J.b, (const float*)J.u, (const float*)J.t1,
-                                      (const float*)J.t2, maps.data());
+            if (use_tc_)
+                J.tc_tma = tc_encode_maps(G.F, G.ax1, G.ax2, (const float*)J.b, (const float*)J.u,
+                                          (const float*)J.t1, (const float*)J.t2, maps.data());
+            if (prec == SAC_MIXED)
+                J.seg_tma = seg_encode_maps(G.n_outer, G.mpe, G.n_inner, (const float*)J.I1, (const float*)J.I2,
+                                            (const float*)J.b, (const float*)J.z, (const float*)J.u, maps.data());
             ENG_CUDA(cudaMemcpyAsync(s + L.tmap, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
         }
         J.part = d_part_;

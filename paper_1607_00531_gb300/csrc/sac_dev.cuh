@@ -49,9 +49,9 @@ struct Job {
     int active;        // 0: tiles of this job return at once
     int pad_;
     int tc_T[4];       // tensor-core z-step: lines per tile of each pass
-    const void* tmaps; // tensor-core z-step: TMA tensor maps of the X sources, [pass][source]
+    const void* tmaps; // TMA tensor maps: tensor-core z-step X sources [pass][source], outputs [pass]; b-step rows
     int tc_tma;        // bit q: pass q loads X with the tensor maps; bit 4 + q: pass q stores with one
-    int pad2_;
+    int seg_tma;       // 1: the segment b-step copies its tiles with the b-step maps (bstep_seg.cu)
     // adaptive augmentation parameter: after rho changes, every reader of the
     // scaled dual u uses uscale * u (uscale = rho_old / rho_new) for one
     // iteration, whose dual update stores the rescaled u; 1 otherwise

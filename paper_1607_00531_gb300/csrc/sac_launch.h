@@ -95,6 +95,13 @@ inline long long line_tiles(int n_outer, int n_inner, int W) {
 int seg_faces(int mpe, int n_inner, int n_sqp, bool mixed, int kernel);
 int seg_warps(int mpe, int S);
 int seg_lines();   // lines per CTA
+// Host: the b-step's staging maps of a job (FP32 images [n_outer][m][ni] and
+// face arrays [n_outer][m + 1][ni]) into maps kSegMap0 .. kSegMap0 + 4 of the
+// job's map block `maps` (host memory, tc_map_bytes() bytes); returns 1 when
+// all five are encoded (ni a multiple of 16, 16-byte aligned arrays), else 0:
+// the kernel then stages its tiles with per-thread asynchronous copies
+int seg_encode_maps(int n_outer, int m, int ni, const float* I1, const float* I2, const float* b, const float* z,
+                    const float* u, void* maps);
 inline long long seg_tiles(long long nlines) { return (nlines + seg_lines() - 1) / seg_lines(); }
 size_t seg_smem_bytes(int mpe);   // dynamic shared memory of a CTA
 cudaError_t launch_bstep_seg(const LineLaunch& L);
@@ -143,8 +150,13 @@ struct TcCfg {
     uint32_t raw_off = 0;            // and its shared-memory offset
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
-constexpr int kTcMaps = 12;          // TMA tensor maps per job: [pass][source] X sources, then [pass] outputs
+// TMA tensor maps per job: [pass][source] X sources and [pass] outputs of the
+// tensor-core z-step, then the five staging maps of the segment b-step
+constexpr int kTcMaps = 17;
+constexpr int kSegMap0 = 12;
 size_t tc_map_bytes();
+// cuTensorMapEncodeTiled from the driver (null if unavailable)
+void* tensor_map_encoder();
 // Host: encode the tensor maps of a job (FP32 device arrays b, u, t1, t2)
 // into `out` (tc_map_bytes() bytes, host memory); returns a mask: bit q, pass
 // q loads X with the maps; bit 4 + q, pass q (strided axis) writes its output

@@ -109,8 +109,9 @@ __device__ __forceinline__ void tma_store3d(const void* map, uint32_t src, int x
                  :: "l"(map), "r"(src), "r"(x), "r"(y), "r"(z) : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-// at most one bulk group still reading shared memory / every bulk group complete
+// at most one / no bulk group still reading shared memory; every bulk group complete
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {

@@ -251,6 +251,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
     return fn;
 }
 
+void* tensor_map_encoder() { return (void*)tc_encode_fn(); }
+
 size_t tc_map_bytes() { return (size_t)kTcMaps * sizeof(CUtensorMap); }
 
 // Host: tensor maps of the X sources of every pass of one job into `out`
