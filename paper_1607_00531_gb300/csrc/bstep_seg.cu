@@ -68,55 +68,66 @@ struct Cell {
 };
 
 // residual of cell j between faces j and j+1 (b0, b1) and its two Jacobian
-// entries (Sec. 3); zero outside [0, m) (kIn: j is known to be inside)
-template <bool kIn>
+// entries (Sec. 3); zero outside [0, m).  No branch: the value is computed for
+// any j (finite b0, b1; interp clamps its position) and then selected, so
+// that the compiler can schedule the shared-memory loads of all faces of a
+// segment ahead.
 __device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* __restrict__ I2, int m, float mf,
                                      int j, float jf, float b0, float b1, float inv_h) {
-    Cell c{0.f, 0.f, 0.f, 0.f};
-    if (kIn || (j >= 0 && j < m)) {
-        const float a = 0.5f * (b0 + b1);
-        const float d = (b1 - b0) * inv_h;
-        float v1, s1, v2, s2;
-        interp(I1, mf, jf + a * inv_h, v1, s1);
-        interp(I2, mf, jf - a * inv_h, v2, s2);
-        const float g1 = s1 * inv_h, g2 = s2 * inv_h;
-        c.r = v1 * (1.f + d) - v2 * (1.f - d);
-        const float p = 0.5f * (g1 * (1.f + d) + g2 * (1.f - d));
-        const float q = (v1 + v2) * inv_h;
-        c.Jd = p - q;
-        c.Ju = p + q;
-        c.d = d;
-    }
+    Cell c;
+    const float a = 0.5f * (b0 + b1);
+    const float d = (b1 - b0) * inv_h;
+    float v1, s1, v2, s2;
+    interp(I1, mf, jf + a * inv_h, v1, s1);
+    interp(I2, mf, jf - a * inv_h, v2, s2);
+    const float g1 = s1 * inv_h, g2 = s2 * inv_h;
+    c.r = v1 * (1.f + d) - v2 * (1.f - d);
+    const float p = 0.5f * (g1 * (1.f + d) + g2 * (1.f - d));
+    const float q = (v1 + v2) * inv_h;
+    c.Jd = p - q;
+    c.Ju = p + q;
+    c.d = d;
+    const bool in = (unsigned)j < (unsigned)m;
+    c.r = in ? c.r : 0.f;
+    c.Jd = in ? c.Jd : 0.f;
+    c.Ju = in ? c.Ju : 0.f;
+    c.d = in ? c.d : 0.f;
     return c;
 }
 
 // Rows s .. s+S-1 of the line's system, assembled and eliminated (see the
-// kernel); kIn: the segment is interior (1 <= s and s + S <= m), so that every
-// face and cell it touches is inside the line
-template <int S, bool kIn>
+// kernel).  Every segment takes this one path, boundary segments included:
+// rows are read clamped to [0, m] and the boundary terms selected (faces
+// outside [0, m] are zero and their rows identity rows).  (A second, test-free
+// variant for interior segments measured slower overall: the warp holding the
+// boundary segments then ran other code than the rest of the CTA, missing in
+// the instruction cache, and held every CTA barrier.)
+template <int S>
 __device__ __forceinline__ void forward(const float* __restrict__ rI1, const float* __restrict__ rI2,
                                         const float* __restrict__ rB, const float* __restrict__ rZ,
                                         const float* __restrict__ rU, int m, int s, float inv_h, float ih2,
                                         float alpha, float rho, float us, float (&A)[S], float (&C)[S],
                                         float (&R)[S]) {
-    const float bprev = (kIn || s >= 1) ? rB[(s - 1) * kLines] : 0.f;
-    float bcur = rB[s * kLines];
+    const float bp = rB[max(s - 1, 0) * kLines];
+    const float bprev = (s >= 1) ? bp : 0.f;
+    float bcur = rB[s * kLines];   // (s <= m for every segment of the line)
     const float mf = (float)m, sf = (float)s;   // cell positions as floats: sf + k (exact)
-    Cell prev = cell<kIn>(rI1, rI2, m, mf, s - 1, sf - 1.f, bprev, bcur, inv_h);
+    Cell prev = cell(rI1, rI2, m, mf, s - 1, sf - 1.f, bprev, bcur, inv_h);
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const int i = s + k;
-        const float bnext = (kIn || i + 1 <= m) ? rB[(i + 1) * kLines] : 0.f;
-        const Cell cur = cell<kIn>(rI1, rI2, m, mf, i, sf + (float)k, bcur, bnext, inv_h);
-        float dg = 1.f, sub = 0.f, sup = 0.f, rhs = 0.f;
-        if (kIn || i <= m) {
-            const float nadj = kIn ? 2.f : (float)((i > 0) + (i < m));
-            const float zu = us * rU[i * kLines] - rZ[i * kLines];
-            dg = prev.Ju * prev.Ju + cur.Jd * cur.Jd + alpha * nadj * ih2 + rho;
-            sup = (kIn || i < m) ? cur.Jd * cur.Ju - alpha * ih2 : 0.f;
-            sub = (kIn || i > 0) ? prev.Jd * prev.Ju - alpha * ih2 : 0.f;
-            rhs = -(prev.Ju * prev.r + cur.Jd * cur.r + alpha * (prev.d - cur.d) * inv_h + rho * (bcur + zu));
-        }
+        const float bn = rB[min(i + 1, m) * kLines];
+        const float bnext = (i + 1 <= m) ? bn : 0.f;
+        const Cell cur = cell(rI1, rI2, m, mf, i, sf + (float)k, bcur, bnext, inv_h);
+        const int ic = min(i, m);
+        const float nadj = (float)((i > 0) + (i < m));
+        const float zu = us * rU[ic * kLines] - rZ[ic * kLines];
+        const bool face = i <= m;
+        const float dg = face ? prev.Ju * prev.Ju + cur.Jd * cur.Jd + alpha * nadj * ih2 + rho : 1.f;
+        const float sup = (face && i < m) ? cur.Jd * cur.Ju - alpha * ih2 : 0.f;
+        const float sub = (face && i > 0) ? prev.Jd * prev.Ju - alpha * ih2 : 0.f;
+        const float rhs =
+            face ? -(prev.Ju * prev.r + cur.Jd * cur.r + alpha * (prev.d - cur.d) * inv_h + rho * (bcur + zu)) : 0.f;
         // rows 0 and 1 normalised; row k >= 2 rewritten as
         // x_k + A_k x_0 + C_k x_{k+1} = R_k (row 0: A_0 multiplies the
         // previous segment's last unknown)
@@ -282,9 +293,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     __shared__ int sFlag[NL];
     __shared__ int sDmax[NL];
     extern __shared__ __align__(128) float sdyn[];   // TMA destinations: 128-byte aligned
-    // segment of the thread: the first and the last segment (the ones with
-    // boundary rows) share warp 0, the interior ones follow in order
-    const int lane = threadIdx.x % NL, gi = threadIdx.x / NL;
+    // thread (g, lane): segment g of line lane; the two half-warps of a warp
+    // read rows S (odd) apart, in different shared-memory banks
+    const int lane = threadIdx.x % NL, g = threadIdx.x / NL;
     const Regions Rg = regions(sdyn, mmax);
     __shared__ __align__(8) unsigned long long sBar;   // TMA staging: one phase per staged tile
     __shared__ int sAbort;
@@ -335,7 +346,6 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
         continue;
     }
-    const int g = (gi == 0) ? 0 : (gi == 1) ? G - 1 : gi - 1;
     const long long nlines = (long long)J.n_outer * ni;
     const long long L0 = (t - prefix[jid]) * NL;
     const float* sI1 = Rg.I1;
@@ -346,20 +356,14 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     const bool valid = L < nlines;   // rows of lanes past the last line are not staged
     const float h = (float)J.hpe, inv_h = 1.f / h, ih2 = inv_h * inv_h;
     const float alpha = (float)J.alpha, rho = (float)J.rho, us = (float)J.uscale;
-    const bool on = gi < G && valid;
+    const bool on = g < G && valid;
     const int s = g * S;
     const float* rI1 = sI1 + lane;
     const float* rI2 = sI2 + lane;
     const float* rB = sB + lane;
     float A[S], C[S], R[S];    // eliminated rows of the segment
-    // interior segments skip the bound tests; a warp that holds a boundary
-    // segment takes the general path for all its threads (no divergence)
-    const bool warp_interior = __all_sync(__activemask(), !on || (s >= 1 && s + S <= m));
     if (on) {
-        if (warp_interior)
-            forward<S, true>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
-        else
-            forward<S, false>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
+        forward<S>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
         // rows S-3 .. 1 rewritten as x_k + A_k x_0 + C_k x_{S-1} = R_k
 #pragma unroll
         for (int k = S - 3; k >= 1; --k) {
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     __syncthreads();
     // the images, z, u and the other b buffer are free: copy the next tile
     if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
-    if (gi == 0) {
+    if (g == 0) {
         sFlag[lane] = 0;
         sDmax[lane] = 0;
     }
@@ -437,28 +441,17 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         // (a NaN anywhere makes the sum NaN: the FP64 method takes the line)
         float dmax = 0.f, dsum = 0.f;
         float b0 = rB[s * NL];
-        if (s + S <= m) {
+        {
 #pragma unroll
             for (int k = 0; k < S; ++k) {
-                const float b1 = rB[(s + k + 1) * NL];
+                // (clamped row, then selected: no branch around the loads)
+                const int j = s + k;
+                const float b1 = rB[min(j + 1, m) * NL];
                 const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
-                const float dn = fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h);
+                const float dn = (j < m) ? fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h) : 0.f;
                 dmax = fmaxf(dmax, dn);
                 dsum += dn;
                 b0 = b1;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < S; ++k) {
-                const int j = s + k;
-                if (j < m) {
-                    const float b1 = rB[(j + 1) * NL];
-                    const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
-                    const float dn = fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h);
-                    dmax = fmaxf(dmax, dn);
-                    dsum += dn;
-                    b0 = b1;
-                }
             }
         }
         const bool blocked = !(dmax <= 1.f) || !(dsum == dsum);
@@ -502,7 +495,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
             }
         }
     }
-    if (valid && queue && gi == 0) {
+    if (valid && queue && g == 0) {
         const int slot = atomicAdd(rcount, 1);
         if (slot < rcap) rlist[slot] = ((unsigned long long)jid << 40) | (unsigned long long)L;
         else atomicOr(status, kStTimeout);
@@ -599,8 +592,7 @@ int sm_count() {
 cudaError_t launch_bstep_seg(const LineLaunch& L) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.seg_G < 1 || L.seg_G > seg::kMaxSeg) return cudaErrorInvalidValue;
-    // at least two segments' threads: warp 0 holds the first and the last
-    // segment of every line
+    // at least one full warp (the reduced systems are solved by full warps)
     const unsigned block = (unsigned)(seg::kLines * (L.seg_G > 2 ? L.seg_G : 2));
     const size_t smem = seg::smem_bytes(L.seg_m);
     const float nb = (float)L.near_bound;
