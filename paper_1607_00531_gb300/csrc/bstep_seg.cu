@@ -107,7 +107,7 @@ __device__ __forceinline__ void forward(const float* __restrict__ rI1, const flo
                                         const float* __restrict__ rB, const float* __restrict__ rZ,
                                         const float* __restrict__ rU, int m, int s, float inv_h, float ih2,
                                         float alpha, float rho, float us, float (&A)[S], float (&C)[S],
-                                        float (&R)[S]) {
+                                        float (&R)[S], float& b_end) {
     const float bp = rB[max(s - 1, 0) * kLines];
     const float bprev = (s >= 1) ? bp : 0.f;
     float bcur = rB[s * kLines];   // (s <= m for every segment of the line)
@@ -118,6 +118,7 @@ __device__ __forceinline__ void forward(const float* __restrict__ rI1, const flo
         const int i = s + k;
         const float bn = rB[min(i + 1, m) * kLines];
         const float bnext = (i + 1 <= m) ? bn : 0.f;
+        if (k == S - 1) b_end = bn;   // b of row min(s + S, m): the bound test's last read
         const Cell cur = cell(rI1, rI2, m, mf, i, sf + (float)k, bcur, bnext, inv_h);
         const int ic = min(i, m);
         const float nadj = (float)((i > 0) + (i < m));
@@ -291,7 +292,6 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     __shared__ float sE[6][kMaxSeg][NL];
     __shared__ float sX[2][kMaxSeg][NL];
     __shared__ int sFlag[NL];
-    __shared__ int sDmax[NL];
     extern __shared__ __align__(128) float sdyn[];   // TMA destinations: 128-byte aligned
     // thread (g, lane): segment g of line lane; the two half-warps of a warp
     // read rows S (odd) apart, in different shared-memory banks
@@ -361,9 +361,11 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     const float* rI1 = sI1 + lane;
     const float* rI2 = sI2 + lane;
     const float* rB = sB + lane;
+    float* const wB = sB + lane;
     float A[S], C[S], R[S];    // eliminated rows of the segment
+    float b_end = 0.f;
     if (on) {
-        forward<S>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R);
+        forward<S>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R, b_end);
         // rows S-3 .. 1 rewritten as x_k + A_k x_0 + C_k x_{S-1} = R_k
 #pragma unroll
         for (int k = S - 3; k >= 1; --k) {
@@ -388,10 +390,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     __syncthreads();
     // the images, z, u and the other b buffer are free: copy the next tile
     if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
-    if (g == 0) {
-        sFlag[lane] = 0;
-        sDmax[lane] = 0;
-    }
+    if (g == 0) sFlag[lane] = 0;
     {
         // The line's reduced system: unknown 2q = first of segment q, 2q+1 =
         // its last; row r couples r-1 (a) and r+1 (c), unit diagonal; 2G <=
@@ -401,28 +400,42 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         // to a unit diagonal, so that after ceil(log2 2G) steps x_r = d_r.
         // Every full warp of the CTA takes lines warp, warp + nw, ...
         const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5), q = threadIdx.x & 31, N = 2 * G;
-        for (int l = w; l < NL && w < nw; l += nw) {   // (a partial last warp takes no line)
-            float a = 0.f, c = 0.f, d = 0.f;
+        // Two lines per pass (l, l + nw) as independent chains for latency.
+        for (int l = w; l < NL && w < nw; l += 2 * nw) {   // (a partial last warp takes no line)
+            const int l1 = l + nw;
+            const bool two = l1 < NL;
+            float a[2] = {0.f, 0.f}, c[2] = {0.f, 0.f}, d[2] = {0.f, 0.f};
             if (q < N) {
                 const int e = 3 * (q & 1), sg = q >> 1;
-                a = sE[e][sg][l];
-                c = sE[e + 1][sg][l];
-                d = sE[e + 2][sg][l];
+                a[0] = sE[e][sg][l];
+                c[0] = sE[e + 1][sg][l];
+                d[0] = sE[e + 2][sg][l];
+                if (two) {
+                    a[1] = sE[e][sg][l1];
+                    c[1] = sE[e + 1][sg][l1];
+                    d[1] = sE[e + 2][sg][l1];
+                }
             }
             for (int st = 1; st < N; st <<= 1) {
-                float am = __shfl_up_sync(0xffffffffu, a, st), cm = __shfl_up_sync(0xffffffffu, c, st);
-                float dm = __shfl_up_sync(0xffffffffu, d, st);
-                float ap = __shfl_down_sync(0xffffffffu, a, st), cp = __shfl_down_sync(0xffffffffu, c, st);
-                float dp = __shfl_down_sync(0xffffffffu, d, st);
-                if (q < st) am = cm = dm = 0.f;          // beyond the first row: identity
-                if (q + st >= 32) ap = cp = dp = 0.f;    // beyond the last lane: identity
-                const float inv = fdiv(1.f, 1.f - a * cm - c * ap);
-                const float dn = (d - a * dm - c * dp) * inv;
-                a = -a * am * inv;
-                c = -c * cp * inv;
-                d = dn;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    float am = __shfl_up_sync(0xffffffffu, a[i], st), cm = __shfl_up_sync(0xffffffffu, c[i], st);
+                    float dm = __shfl_up_sync(0xffffffffu, d[i], st);
+                    float ap = __shfl_down_sync(0xffffffffu, a[i], st), cp = __shfl_down_sync(0xffffffffu, c[i], st);
+                    float dp = __shfl_down_sync(0xffffffffu, d[i], st);
+                    if (q < st) am = cm = dm = 0.f;          // beyond the first row: identity
+                    if (q + st >= 32) ap = cp = dp = 0.f;    // beyond the last lane: identity
+                    const float inv = fdiv(1.f, 1.f - a[i] * cm - c[i] * ap);
+                    const float dn = (d[i] - a[i] * dm - c[i] * dp) * inv;
+                    a[i] = -a[i] * am * inv;
+                    c[i] = -c[i] * cp * inv;
+                    d[i] = dn;
+                }
             }
-            if (q < N) sX[q & 1][q >> 1][l] = d;
+            if (q < N) {
+                sX[q & 1][q >> 1][l] = d[0];
+                if (two) sX[q & 1][q >> 1][l1] = d[1];
+            }
         }
     }
     __syncthreads();
@@ -438,38 +451,45 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         // crosses |D1 b| = 1 (a blocking constraint of the active-set
         // method) exactly where |D1 (b + x)| > 1; the largest |D1 (b + x)|
         // is also the line's distance from the bound
-        // (a NaN anywhere makes the sum NaN: the FP64 method takes the line)
+        // (a NaN anywhere makes the sum NaN: the FP64 method takes the line).
+        // b + x replaces b in the tile's buffer row by row (each row is read
+        // before it is written; the next segment's first row was read during
+        // the forward elimination, before any thread wrote).  A line is
+        // queued when some segment crosses the bound or, with near_bound,
+        // ends within near_bound of it (monotone in |D1 (b + x)|: the test of
+        // each segment's largest value decides for the line).
         float dmax = 0.f, dsum = 0.f;
         float b0 = rB[s * NL];
-        {
 #pragma unroll
-            for (int k = 0; k < S; ++k) {
-                // (clamped row, then selected: no branch around the loads)
-                const int j = s + k;
-                const float b1 = rB[min(j + 1, m) * NL];
-                const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
-                const float dn = (j < m) ? fabsf(((b1 + x1) - (b0 + xs[k])) * inv_h) : 0.f;
-                dmax = fmaxf(dmax, dn);
-                dsum += dn;
-                b0 = b1;
-            }
+        for (int k = 0; k < S; ++k) {
+            // (clamped row, then selected: no branch around the loads)
+            const int j = s + k;
+            const float b1 = (k + 1 < S) ? rB[min(j + 1, m) * NL] : b_end;
+            const float x1 = (k + 1 < S) ? xs[k + 1] : xr;
+            const float bx0 = b0 + xs[k];
+            const float dn = (j < m) ? fabsf(((b1 + x1) - bx0) * inv_h) : 0.f;
+            if (j <= m) wB[j * NL] = bx0;
+            dmax = fmaxf(dmax, dn);
+            dsum += dn;
+            b0 = b1;
         }
-        const bool blocked = !(dmax <= 1.f) || !(dsum == dsum);
-        if (blocked) atomicOr(&sFlag[lane], 1);
-        if (dmax > 0.f) atomicMax(&sDmax[lane], __float_as_int(dmax));
+        const bool flag = !(dmax <= 1.f) || !(dsum == dsum) || (near_bound > 0.f && (1.f - dmax) < near_bound);
+        if (flag) atomicOr(&sFlag[lane], 1);
     }
     __syncthreads();
-    const bool queue = sFlag[lane] != 0 || (near_bound > 0.f && (1.f - __int_as_float(sDmax[lane])) < near_bound);
+    const bool queue = sFlag[lane] != 0;
     if (J.seg_tma) {
-        // b^{k+1} into the tile's b buffer (queued lines keep b^k there),
-        // copied out by tensor stores after the next CTA barrier
-        if (valid && !queue && on) {
-            float* wB = sB + lane;
+        // the tile's b buffer holds b^{k+1}; a queued line keeps b^k (still
+        // in global memory: the buffer is copied out after the next CTA
+        // barrier by tensor stores)
+        if (valid && queue && on) {
+            const long long o = L / ni;
+            const float* gB = (const float*)J.b + o * (long long)(m + 1) * ni + (L - o * ni) + (long long)s * ni;
 #pragma unroll
             for (int k = 0; k < S; ++k)
-                if (s + S <= m + 1 || s + k <= m) wB[(s + k) * NL] += xs[k];
-            fence_async_smem();
+                if (s + k <= m) wB[(s + k) * NL] = gB[(long long)k * ni];
         }
+        fence_async_smem();
         if (issuer) {
             const long long o = L0 / ni;
             sPend[0] = (long long)(const char*)J.tmaps + (long long)(kSegMap0 + 2) * 128;
@@ -485,14 +505,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         if (on) {
             const long long o = L / ni;
             float* gB = (float*)J.b + o * (long long)(m + 1) * ni + (L - o * ni) + (long long)s * ni;
-            if (s + S <= m + 1) {
 #pragma unroll
-                for (int k = 0; k < S; ++k) gB[(long long)k * ni] = rB[(s + k) * NL] + xs[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < S; ++k)
-                    if (s + k <= m) gB[(long long)k * ni] = rB[(s + k) * NL] + xs[k];
-            }
+            for (int k = 0; k < S; ++k)
+                if (s + k <= m) gB[(long long)k * ni] = rB[(s + k) * NL];   // b + x
         }
     }
     if (valid && queue && g == 0) {
