@@ -213,6 +213,15 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
         tc_cfg_add(&P->tc_cfg[q], G.F, G.ax1, G.ax2, q);
         if (!tc_cfg_finish(&P->tc_cfg[q])) P->use_tc = 0;
     }
+    P->fuse12 = 0;
+    if (P->use_tc) {
+        TcCfg f;
+        tc_cfg_add(&f, G.F, G.ax1, G.ax2, 1);
+        if (tc_cfg_fuse12(&f)) {
+            P->tc_cfg12 = f;
+            P->fuse12 = 1;
+        }
+    }
     const long long nlines = (long long)G.n_outer * G.n_inner;
     P->rcap = (int)nlines;
     long long np = 4 * P->line_tiles;
@@ -491,6 +500,7 @@ static int max_abs_d1_dev(Plan& P, const double* b, double* out, cudaStream_t st
 static int zstep_passes(Plan& P, cudaStream_t st) {
     const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
     for (int q = 0; q < 4; ++q) {
+        if (P.use_tc && P.fuse12 && q == 2) continue;   // done with pass 1
         PhaseScope ps(2 + q, st);
         AxisLaunch A;
         A.jobs = P.d_job;
@@ -503,7 +513,7 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
         if (P.use_tc) {
             A.prefix = P.d_pref_tc[q];
             A.total_tiles = P.tc_tiles[q];
-            SAC_CUDA(launch_axis_pass_tc(A, P.tc_cfg[q]));
+            SAC_CUDA(launch_axis_pass_tc(A, (P.fuse12 && q == 1) ? P.tc_cfg12 : P.tc_cfg[q]));
         } else {
             A.prefix = P.d_pref_pass[q];
             A.total_tiles = P.pass_tiles[q];

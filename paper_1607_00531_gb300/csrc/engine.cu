@@ -272,6 +272,7 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         zpref_.assign(4 * ngeo_, nullptr);
         ztiles_.assign(4 * ngeo_, 0);
         zcfg_.assign(4 * ngeo_, TcCfg());
+        zcfg12_.assign(ngeo_, TcCfg());
         for (int q = 0; q < 4; ++q)
             for (int gr = 0; gr < ngeo_; ++gr) {
                 const int z = q * ngeo_ + gr;
@@ -283,6 +284,12 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
                     if (gid[i] == gr) tc_cfg_add(&zcfg_[z], G.F, G.ax1, G.ax2, q);
                 }
                 ztiles_[z] = h[nj];
+                if (q == 1 && use_tc_) {
+                    // the fused layout from the same jobs' pass-1 geometry
+                    TcCfg f = zcfg_[z];
+                    if (!tc_cfg_fuse12(&f)) f = TcCfg();
+                    zcfg12_[gr] = f;
+                }
                 if (use_tc_ && !tc_cfg_finish(&zcfg_[z])) return SAC_EINVAL;
             }
         ENG_CUDA(cudaMemcpyAsync(zp, hz.data(), hz.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -468,9 +475,11 @@ int Engine::enqueue_iteration(int slot) {
             for (int gr = 0; gr < ngeo_; ++gr) {
                 const int z = q * ngeo_ + gr;
                 if (ztiles_[z] == 0) continue;
+                const bool fused = zcfg12_[gr].fused != 0;
+                if (fused && q == 2) continue;   // done with pass 1
                 A.prefix = zpref_[z];
                 A.total_tiles = ztiles_[z];
-                ENG_CUDA(launch_axis_pass_tc(A, zcfg_[z]));
+                ENG_CUDA(launch_axis_pass_tc(A, (fused && q == 1) ? zcfg12_[gr] : zcfg_[z]));
             }
         } else {
             A.prefix = d_pref_ax_[q];

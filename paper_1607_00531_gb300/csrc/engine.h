@@ -93,6 +93,7 @@ private:
     std::vector<long long*> zpref_;
     std::vector<long long> ztiles_;
     std::vector<TcCfg> zcfg_;
+    std::vector<TcCfg> zcfg12_;       // per geometry group: passes 1 and 2 in one launch (fused = 1)
     long long* d_pref_ax_[4] = {nullptr, nullptr, nullptr, nullptr};
     long long ax_tiles_[4] = {0, 0, 0, 0};
     long long* d_pref_admm_ = nullptr;   // ADMM update blocks per job (tensor-core z-step)

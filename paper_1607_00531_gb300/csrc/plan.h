@@ -44,6 +44,8 @@ struct Plan {
     long long tc_floats[4];
     long long tn_floats[4];    // tensor-memory DCT operands (axes of at most 128 faces)
     TcCfg tc_cfg[4];           // ring / accumulator layout of each tensor-core pass
+    TcCfg tc_cfg12;            // passes 1 and 2 in one launch (valid when fuse12)
+    int fuse12;
     int rcap;
     // device pointers inside ws
     Job* d_job;

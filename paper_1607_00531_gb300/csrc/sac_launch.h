@@ -138,6 +138,7 @@ struct TcCfg {
     uint32_t dslot = 0, rslot = 0;   // bytes of one DCT / raw X ring slot (shared memory)
     int acc_need = 0;                // TMEM columns of one tile's accumulator
     int sd = 0, sr = 0, st = 0;      // ring stages: DCT, raw X, split X (tensor memory)
+    int st2 = 0;                     // fused passes 1 + 2: stages of the second split ring (D2's operand)
     int nacc = 0;                    // accumulator buffers (2 when both fit in TMEM)
     uint32_t acc_cols = 0;           // TMEM columns per accumulator buffer
     uint32_t epi_off = 0;            // shared-memory offset of the epilogue transpose buffers
@@ -148,6 +149,7 @@ struct TcCfg {
     int tn = 0;                      // 1: the lines-in-N kernel (zstep_tcn.cu), sr = its ring stages
     int raw_st = 0;                  // lines-in-N kernel: stages of its raw X ring (TMA copies; 0: none)
     uint32_t raw_off = 0;            // and its shared-memory offset
+    int fused = 0;                   // 1: passes 1 and 2 in one launch (lines-in-M kernel, tc_cfg_fuse12)
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
 // TMA tensor maps per job: [pass][source] X sources and [pass] outputs of the
@@ -173,6 +175,12 @@ cudaError_t launch_admm_update(Job* jobs, int njobs, const long long* prefix, lo
                                double* part, const AdmmCheck& chk, cudaStream_t st);
 void tc_cfg_add(TcCfg* c, const int F[3], int ax1, int ax2, int pass);
 bool tc_cfg_finish(TcCfg* c);
+// Layout of the fused launch of passes 1 and 2 (both along ax2) from a
+// configuration that has seen tc_cfg_add(pass 1) for every job: one geometry,
+// both DCT matrices resident in shared memory, D1 beside the accumulators in
+// tensor memory; false when it does not fit (then the passes run apart).
+// Launched as pass 1 (its prefix and tiles); writes pass 2's output.
+bool tc_cfg_fuse12(TcCfg* c);
 cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg);
 int tc_tile_lines(const int F[3], int ax1, int ax2, int pass);
 long long tc_pass_tiles(const int F[3], int ax1, int ax2, int pass);

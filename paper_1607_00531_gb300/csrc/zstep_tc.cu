@@ -78,7 +78,7 @@ constexpr int kThreads = (kXWarp + 1) * 32;
 constexpr int kBK = 32;                            // K chunk
 constexpr int kTileLines = 128;                    // lines per tile (MMA M)
 constexpr uint32_t kRawBytes = kTileLines * kBK * 4;   // one source's raw chunk (16 KB)
-constexpr int kMaxDStages = 4, kMaxRStages = 6, kMaxTStages = 4;
+constexpr int kMaxDStages = 8, kMaxRStages = 6, kMaxTStages = 4;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kXCols = 2 * kBK;               // TMEM columns of an X chunk slot
 constexpr int kEpiPitch = 20;                      // floats per row of an epilogue transpose buffer
@@ -199,6 +199,35 @@ bool tc_cfg_finish(TcCfg* c) {
     c->epi_off = (uint32_t)need();
     c->smem = need() + tc::kEpiBytes;
     // more than half of the SM's shared memory: one CTA per SM, which owns all of TMEM
+    if (c->smem < 120 * 1024) c->smem = 120 * 1024;
+    return true;
+}
+
+bool tc_cfg_fuse12(TcCfg* c) {
+    if (c->dslot == 0 || c->geom[0] < 0 || c->acc_need > 256) return false;
+    c->tn = 0;
+    c->fused = 1;
+    c->sd = 2 * c->nch;   // C2 in slots 0 .. nch - 1, C2^T after it, resident
+    if (c->sd > tc::kMaxDStages) return false;
+    const size_t budget = 226 * 1024 - tc::kEpiBytes;
+    c->sr = 2;
+    auto need = [&]() { return (size_t)c->sd * c->dslot + (size_t)c->sr * c->rslot; };
+    if (need() > budget) return false;
+    while (c->sr < tc::kMaxRStages && need() + c->rslot <= budget) c->sr++;
+    c->acc_cols = (uint32_t)((c->acc_need + 31) & ~31);
+    // the accumulators, D1, then at least two X slots
+    // one accumulator, D1, then ring A (at least two slots) and ring B (at
+    // least one).  The tile period is set by the chain D1 -> ring B -> D2 ->
+    // D1 free, so the columns of a second accumulator serve better as ring
+    // slots (the epilogue of tile t ends before D2 of tile t + 1 starts)
+    c->nacc = 1;
+    const int slots = (int)((tc::kTmemCols - 2 * c->acc_cols) / tc::kXCols);
+    if (slots < 3) return false;
+    c->st2 = (slots >= 4) ? 2 : 1;
+    c->st = slots - c->st2 > tc::kMaxTStages ? tc::kMaxTStages : slots - c->st2;
+    c->resident = 1;
+    c->epi_off = (uint32_t)need();
+    c->smem = need() + tc::kEpiBytes;
     if (c->smem < 120 * 1024) c->smem = 120 * 1024;
     return true;
 }
@@ -393,16 +422,24 @@ __device__ __forceinline__ void tc_unit_cols(long long u, long long nfull, int N
     nN = second ? Np - h0 : h0;
 }
 
+// PASS 0..3: one pass.  PASS 4: passes 1 and 2 fused (both contract ax2):
+// per tile, D1 = C2 X into a second accumulator; the converters read D1 back,
+// scale it (row k1 of the table), split it and feed it through the X ring
+// as the operand of D2 = C2^T (scaled D1), which the epilogue writes as
+// pass 2's output.  Both DCT matrices stay resident in shared memory.
 template <int PASS>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_axis_tc(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, long long total,
               long long nfull, TcCfg cfg, int* __restrict__ status) {
     using namespace tc;
-    constexpr int NSRC = (PASS == 0) ? 2 : 1;   // X sources (pass 0: b + u)
+    constexpr bool FUSED = (PASS == 4);
+    constexpr int PIN = FUSED ? 1 : PASS;    // the pass whose input, tiles and DCT the kernel reads
+    constexpr int POUT = FUSED ? 2 : PASS;   // the pass whose output it writes
+    constexpr int NSRC = (PIN == 0) ? 2 : 1;   // X sources (pass 0: b + u)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // barriers: DCT full / empty, raw X full / empty, TMEM X full / empty,
-    // accumulator full / empty, drain
-    __shared__ __align__(8) unsigned long long bar[2 * kMaxDStages + 2 * kMaxRStages + 2 * kMaxTStages + 5];
+    // accumulator full / empty, drain; fused: D1 full / empty
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxDStages + 2 * kMaxRStages + 4 * kMaxTStages + 7];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int* abort = &abort_flag;
@@ -416,6 +453,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const uint32_t b_afull = b_tempty + 8 * kMaxTStages;
     const uint32_t b_aempty = b_afull + 16;
     const uint32_t b_drain = b_aempty + 16;
+    const uint32_t b_d1full = b_drain + 8;
+    const uint32_t b_d1empty = b_d1full + 8;
+    const uint32_t b_t2full = b_d1empty + 8;   // fused: ring B (D2's operand)
+    const uint32_t b_t2empty = b_t2full + 8 * kMaxTStages;
     const uint32_t s_base = smem_u32(smem_raw);
     const uint32_t s_raw = s_base + (uint32_t)cfg.sd * cfg.dslot;   // raw X ring after the DCT ring
 
@@ -424,19 +465,25 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             mbar_init(b_dfull + 8 * i, 1);
             mbar_init(b_dempty + 8 * i, 1);
         }
+        // (fused: four converter warps per ring)
+        constexpr int kConvArrive = FUSED ? 4 : kConvWarps;
         for (int i = 0; i < kMaxRStages; ++i) {
             mbar_init(b_rfull + 8 * i, 1);
-            mbar_init(b_rempty + 8 * i, kConvWarps);
+            mbar_init(b_rempty + 8 * i, kConvArrive);
         }
         for (int i = 0; i < kMaxTStages; ++i) {
-            mbar_init(b_tfull + 8 * i, kConvWarps);
+            mbar_init(b_tfull + 8 * i, kConvArrive);
             mbar_init(b_tempty + 8 * i, 1);
+            mbar_init(b_t2full + 8 * i, 4);
+            mbar_init(b_t2empty + 8 * i, 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(b_afull + 8 * i, 1);
             mbar_init(b_aempty + 8 * i, kEpiWarps);
         }
         mbar_init(b_drain, 1);
+        mbar_init(b_d1full, 1);
+        mbar_init(b_d1empty, 4);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -445,10 +492,140 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t xcol0 = (uint32_t)cfg.nacc * cfg.acc_cols;   // first TMEM column of the X slots
+    // TMEM columns: the accumulators, (fused) D1, then the X slots
+    const uint32_t d1col = (uint32_t)cfg.nacc * cfg.acc_cols;
+    const uint32_t xcol0 = d1col + (FUSED ? cfg.acc_cols : 0u);
     const long long t0 = blockIdx.x, dt = gridDim.x;
 
-    if (warp < kConvWarps) {
+    if (FUSED && warp < kConvWarps) {
+        // ------------------------------------------------ fused: two converter groups
+        // warps 0-3 (group A): X chunks of pass 1 (32 values of j per line and
+        // chunk) into ring A; warps 4-7 (group B): D1 read back, scaled by row
+        // k1 of the table, split, into ring B for D2 = C2^T (scaled D1).  The
+        // groups run side by side: group A converts tile t + 1 while group B
+        // converts tile t.  Warp w reaches TMEM lanes 32 (w % 4) .. + 31.
+        const int q = warp & 3;
+        const bool grpB = warp >= 4;
+        const int lr = 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t colA = xcol0, colB = xcol0 + (uint32_t)cfg.st * kXCols;
+        RingPos rr, tr;
+        uint32_t d1_phase = 0;
+        for (long long t = t0; t < total; t += dt) {
+            const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
+            if (!s.active) continue;
+            const Job& J = *s.J;
+            bool ok = true;
+            if (!grpB) {
+                const float* __restrict__ X0 = (const float*)J.t1;
+                const bool lv = lr < s.nl;
+                const long long gbase = s.form ? s.pr * s.L * s.post + s.po0 + lr : (s.line0 + lr) * s.L;
+                const long long js = s.form ? s.post : 1;
+                for (int c = 0; c < s.nch && ok; ++c) {
+                    const int rs = rr.slot;
+                    ok = __all_sync(kFull, mbar_wait_ab(b_rfull + 8 * rs, rr.phase, abort));
+                    if (!ok) break;
+                    float v[32];
+                    if (s.tma) {
+                        const unsigned char* rb = smem_raw + (size_t)cfg.sd * cfg.dslot + (size_t)rs * cfg.rslot;
+                        if (s.form == 0) {
+#pragma unroll
+                            for (int g = 0; g < 8; ++g) {
+                                const uint32_t off = (uint32_t)lr * 128u + (uint32_t)((g ^ (lr & 7)) << 4);
+                                const float4 x = *reinterpret_cast<const float4*>(rb + off);
+                                v[4 * g] = x.x; v[4 * g + 1] = x.y; v[4 * g + 2] = x.z; v[4 * g + 3] = x.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 32; ++e)
+                                v[e] = *reinterpret_cast<const float*>(rb + (uint32_t)(e * kTileLines + lr) * 4u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int j = c * kBK + e;
+                            v[e] = (lv && j < s.L) ? __ldg(X0 + gbase + (long long)j * js) : 0.f;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_rempty + 8 * rs);
+                    rr.next(cfg.sr);
+                    const int ts = tr.slot;
+                    ok = __all_sync(kFull, mbar_wait_ab(b_tempty + 8 * ts, tr.phase ^ 1u, abort));
+                    if (!ok) break;
+                    fence_after();
+                    float hi[16], lo[16];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            hi[e] = tf32_round(v[16 * hh + e]);
+                            lo[e] = v[16 * hh + e] - hi[e];
+                        }
+                        const uint32_t col = colA + (uint32_t)ts * kXCols + 16u * hh;
+                        tmem_st16(tl + col, hi);
+                        tmem_st16(tl + col + kBK, lo);
+                    }
+                    tmem_st_wait();
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_tfull + 8 * ts);
+                    tr.next(cfg.st);
+                }
+            } else {
+                ok = __all_sync(kFull, mbar_wait_ab(b_d1full, d1_phase, abort));
+                if (!ok) break;
+                d1_phase ^= 1u;
+                fence_after();
+                const int L2s = J.F[J.ax2];
+                long long s_between = 1;
+                for (int ax = J.ax1 + 1; ax < J.ax2; ++ax) s_between *= J.F[ax];
+                const int F1 = J.F[J.ax1];
+                const long long k1 = (s.form == 0) ? ((s.line0 + lr) / s_between) % F1 : (s.pr / s_between) % F1;
+                const float* __restrict__ srow = J.scale + k1 * L2s;
+                for (int c = 0; c < s.nch && ok; ++c) {
+                    float sc[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int k = kBK * c + e;
+                        sc[e] = (k < s.L) ? __ldg(srow + k) : 0.f;
+                    }
+                    float va[16], vb[16];
+                    tmem_ld16(tl + d1col + (uint32_t)(kBK * c), va);
+                    tmem_ld16(tl + d1col + (uint32_t)(kBK * c + 16), vb);
+                    if (c == s.nch - 1) {
+                        // D1 is read: the next tile's first product may overwrite it
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(b_d1empty);
+                    }
+                    const int ts = tr.slot;
+                    ok = __all_sync(kFull, mbar_wait_ab(b_t2empty + 8 * ts, tr.phase ^ 1u, abort));
+                    if (!ok) break;
+                    fence_after();
+                    float hi[16], lo[16];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float x = (hh ? vb[e] : va[e]) * sc[16 * hh + e];
+                            hi[e] = tf32_round(x);
+                            lo[e] = x - hi[e];
+                        }
+                        const uint32_t col = colB + (uint32_t)ts * kXCols + 16u * hh;
+                        tmem_st16(tl + col, hi);
+                        tmem_st16(tl + col + kBK, lo);
+                    }
+                    tmem_st_wait();
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_t2full + 8 * ts);
+                    tr.next(cfg.st2);
+                }
+            }
+            if (!ok) break;
+        }
+    } else if (warp < kConvWarps) {
         // ------------------------------------------------ X converters
         const int q = warp & 3, kh = warp >> 2;
         const int lr = 32 * q + lane;              // line of the tile (TMEM lane)
@@ -456,11 +633,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         RingPos rr, tr;
         bool run = true;
         for (long long t = t0; t < total && run; t += dt) {
-            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
+            const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
             if (!s.active) continue;
             const Job& J = *s.J;
-            const float* __restrict__ X0 = (PASS == 0) ? (const float*)J.b
-                                         : (PASS == 2) ? (const float*)J.t2 : (const float*)J.t1;
+            const float* __restrict__ X0 = (PIN == 0) ? (const float*)J.b
+                                         : (PIN == 2) ? (const float*)J.t2 : (const float*)J.t1;
             const float* __restrict__ X1 = (const float*)J.u;   // pass 0 only
             const float us = (float)J.uscale;                    // pass 0: b + uscale u
             const bool lv = lr < s.nl;
@@ -537,9 +714,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             long long r_it = 0;
             RingPos rr;
             for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
+                const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
-                const char* maps = (const char*)s.J->tmaps + (size_t)2 * PASS * 128;
+                const char* maps = (const char*)s.J->tmaps + (size_t)2 * PIN * 128;
                 bool ok = true;
                 for (int c = 0; c < s.nch; ++c) {
                     const int rs = rr.slot;
@@ -572,18 +749,28 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             long long d_it = 0;
             RingPos dr;
             for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
+                const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
-                const float* Mpre = (const float*)s.J->Ctc[PASS];
+                const float* Mpre = (const float*)s.J->Ctc[PIN];
                 const uint32_t db = 2u * (uint32_t)s.Np * 128u;
                 bool ok = true;
                 if (cfg.resident) {
                     // every tile uses the same matrix: chunk c stays in slot c
+                    // (fused: pass 2's matrix in slots nch .. 2 nch - 1)
                     for (int c = 0; c < s.nch; ++c) {
                         mbar_expect_tx(b_dfull + 8 * c, db);
                         tma_bulk_g2s(s_base + (uint32_t)c * cfg.dslot, Mpre + (long long)c * (db / 4), db, b_dfull + 8 * c);
                     }
                     d_it = s.nch;
+                    if (FUSED) {
+                        const float* M2 = (const float*)s.J->Ctc[2];
+                        for (int c = 0; c < s.nch; ++c) {
+                            const int sl = s.nch + c;
+                            mbar_expect_tx(b_dfull + 8 * sl, db);
+                            tma_bulk_g2s(s_base + (uint32_t)sl * cfg.dslot, M2 + (long long)c * (db / 4), db, b_dfull + 8 * sl);
+                        }
+                        d_it = 2 * s.nch;
+                    }
                     break;
                 }
                 for (int c = 0; c < s.nch; ++c) {
@@ -603,34 +790,30 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
-            RingPos dr, tr, ar;
-            for (long long t = t0; t < total && !*abort; t += dt) {
-                const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
-                if (!s.active) continue;
-                const int a = ar.slot;
-                if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
-                fence_after();
-                const uint32_t dacc = tmem + (uint32_t)a * cfg.acc_cols;
-                int n0, nN;
-                tc_unit_cols(t, nfull, s.Np, n0, nN);
+            RingPos dr, tr, tr2, ar;
+            uint32_t d1_phase = 0;
+            // one product of a tile: its nch X chunks from ring A (or, fused
+            // D2, ring B) against the DCT chunks (resident: slots dbase + c;
+            // else the DCT ring)
+            auto product = [&](uint32_t dacc, int dbase, int nch, int Np, int n0, int nN, bool ringB) -> bool {
                 const uint32_t idesc = idesc_tf32(kTileLines, nN);
-                bool ok = true;
-                for (int c = 0; c < s.nch; ++c) {
-                    const int ds = cfg.resident ? c : dr.slot, ts = tr.slot;
+                RingPos& xr = ringB ? tr2 : tr;
+                const uint32_t fb = ringB ? b_t2full : b_tfull, eb = ringB ? b_t2empty : b_tempty;
+                const uint32_t xc0 = ringB ? xcol0 + (uint32_t)cfg.st * kXCols : xcol0;
+                for (int c = 0; c < nch; ++c) {
+                    const int ds = cfg.resident ? dbase + c : dr.slot, ts = xr.slot;
                     const uint32_t dpar = cfg.resident ? 0u : dr.phase;
                     if (!mbar_wait_ab(b_dfull + 8 * ds, dpar, abort) ||
-                        !mbar_wait_ab(b_tfull + 8 * ts, tr.phase, abort)) {
-                        ok = false;
-                        break;
-                    }
+                        !mbar_wait_ab(fb + 8 * ts, xr.phase, abort))
+                        return false;
                     fence_after();
                     // B: the DCT chunk [hi: Np rows][lo: Np rows]; a K step of 8
                     // adds 256 bytes (16 in descriptor units).  A: TMEM columns
                     // of the X slot, hi then lo; a K step adds 8 columns.
                     // rows n0.. of the chunk: 8-row groups are 1024 bytes apart
                     const uint64_t ch = sdesc(s_base + (uint32_t)ds * cfg.dslot + (uint32_t)(n0 / 8) * 1024u, 128, 1024);
-                    const uint64_t cl = ch + (uint32_t)s.Np * 8u;
-                    const uint32_t xh = tmem + xcol0 + (uint32_t)ts * kXCols, xl = xh + kBK;
+                    const uint64_t cl = ch + (uint32_t)Np * 8u;
+                    const uint32_t xh = tmem + xc0 + (uint32_t)ts * kXCols, xl = xh + kBK;
                     const uint32_t en = (c > 0) ? 1u : 0u;   // the tile's first K step overwrites
                     // product by product (hi x hi over the chunk's K steps, then
                     // hi x lo, then lo x hi): consecutive MMAs walk along K, which
@@ -643,11 +826,29 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 #pragma unroll
                     for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xl + 8 * ks, ch + 16u * ks, idesc, 1u);
                     if (!cfg.resident) mma_commit(b_dempty + 8 * ds);
-                    mma_commit(b_tempty + 8 * ts);
+                    mma_commit(eb + 8 * ts);
                     dr.next(cfg.sd);
-                    tr.next(cfg.st);
+                    xr.next(ringB ? cfg.st2 : cfg.st);
                 }
-                if (!ok) break;
+                return true;
+            };
+            for (long long t = t0; t < total && !*abort; t += dt) {
+                const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
+                if (!s.active) continue;
+                int n0, nN;
+                tc_unit_cols(t, nfull, s.Np, n0, nN);
+                if (FUSED) {
+                    // D1 = C2 X, once the converters have read the previous tile's D1
+                    if (!mbar_wait_ab(b_d1empty, d1_phase ^ 1u, abort)) break;
+                    fence_after();
+                    if (!product(tmem + d1col, 0, s.nch, s.Np, n0, nN, false)) break;
+                    mma_commit(b_d1full);
+                    d1_phase ^= 1u;
+                }
+                const int a = ar.slot;
+                if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
+                fence_after();
+                if (!product(tmem + (uint32_t)a * cfg.acc_cols, FUSED ? s.nch : 0, s.nch, s.Np, n0, nN, FUSED)) break;
                 mma_commit(b_afull + 8 * a);
                 ar.next(cfg.nacc);
             }
@@ -665,15 +866,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         int ybuf = 0;                       // staging buffer of the next TMA tensor store
         RingPos ar;
         for (long long t = t0; t < total && !*abort; t += dt) {
-            const TcTile s = tc_tile(jobs, njobs, prefix, PASS, tc_unit_tile(t, nfull));
+            const TcTile s = tc_tile(jobs, njobs, prefix, POUT, tc_unit_tile(t, nfull));
             if (!s.active) continue;
             const Job& J = *s.J;
             const int a = ar.slot;
             const bool ok = mbar_wait_ab(b_afull + 8 * a, ar.phase, abort);
             if (!__all_sync(kFull, ok)) break;
             fence_after();
-            float* __restrict__ Y = (PASS == 0 || PASS == 2) ? (float*)J.t1 : (float*)J.t2;
-            const bool scaled = (PASS == 1) || (PASS == 0 && J.F[J.ax2] < 2);
+            float* __restrict__ Y = (POUT == 0 || POUT == 2) ? (float*)J.t1 : (float*)J.t2;
+            const bool scaled = (POUT == 1) || (POUT == 0 && J.F[J.ax2] < 2);
             const int L2s = J.F[J.ax2];
             long long s_between = 1;
             for (int ax = J.ax1 + 1; ax < J.ax2; ++ax) s_between *= J.F[ax];
@@ -689,9 +890,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 // by one TMA tensor store (box 32 x 16 x 1); two staging
                 // buffers per warp, a buffer is rewritten once the store
                 // issued from it two pieces earlier has read it
-                const char* ymap = (const char*)J.tmaps + (size_t)(8 + PASS) * 128;
+                const char* ymap = (const char*)J.tmaps + (size_t)(8 + POUT) * 128;
                 const float* __restrict__ srow = J.scale;
-                if (PASS == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
+                if (POUT == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
                 float* stage0 = reinterpret_cast<float*>(smem_raw + cfg.epi_off + ew * kEpiWarpBytes);
                 for (int p = h; p < npieces; p += 2) {
                     float v[16];
@@ -715,7 +916,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 // thread = line; for each k the warp's 32 lines are 128 contiguous bytes
                 const long long g0 = s.pr * s.L * s.post + s.po0 + lr;
                 const float* __restrict__ srow = J.scale;
-                if (PASS == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
+                if (POUT == 1) srow = J.scale + ((s.pr / s_between) % F1) * L2s;
                 for (int p = h; p < npieces; p += 2) {
                     float v[16];
                     tmem_ld16(tcol + 16 * p, v);
@@ -736,7 +937,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 float* Ew = reinterpret_cast<float*>(smem_raw + cfg.epi_off + ew * kEpiWarpBytes);
                 const int rsub = lane >> 2, csub = 4 * (lane & 3);
                 const float* __restrict__ srow = J.scale;
-                if (PASS == 1) srow = J.scale + (long long)(((s.line0 + lr) / s_between) % F1) * L2s;
+                if (POUT == 1) srow = J.scale + (long long)(((s.line0 + lr) / s_between) % F1) * L2s;
                 const long long rbase0 = (s.line0 + 32 * q + rsub) * s.L, rstep = 8LL * s.L;
                 unsigned rok = 0;
 #pragma unroll
@@ -943,13 +1144,18 @@ cudaError_t launch_axis_pass_tc(const AxisLaunch& A, const TcCfg& cfg) {
     // most half of the SMs as two column halves each (one geometry, N >= 32)
     const long long T = A.total_tiles;
     long long nfull = T;
-    if (cfg.geom[0] >= 0 && cfg.acc_need >= 32) {
+    if (!cfg.fused && cfg.geom[0] >= 0 && cfg.acc_need >= 32) {
         const long long extra = (T <= nsm) ? T : T % nsm;
         if (extra > 0 && 2 * extra <= nsm) nfull = T - extra;
     }
     const long long units = nfull + 2 * (T - nfull);
     const unsigned grid = (unsigned)(units < nsm ? units : nsm);
     count_launch();
+    if (cfg.fused) {
+        if (A.pass != 1) return cudaErrorInvalidValue;
+        k_axis_tc<4><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status);
+        return cudaGetLastError();
+    }
     switch (A.pass) {
         case 0: k_axis_tc<0><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
         case 1: k_axis_tc<1><<<grid, tc::kThreads, cfg.smem, A.stream>>>(A.jobs, A.njobs, A.prefix, units, nfull, cfg, A.status); break;
@@ -965,6 +1171,7 @@ cudaError_t prepare_axis_tc() {
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<0>)) != cudaSuccess) return e;
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<1>)) != cudaSuccess) return e;
     if ((e = allow_max_dyn_smem((const void*)k_axis_tc<2>)) != cudaSuccess) return e;
+    if ((e = allow_max_dyn_smem((const void*)k_axis_tc<4>)) != cudaSuccess) return e;
     return allow_max_dyn_smem((const void*)k_axis_tc<3>);
 }
 
