@@ -590,9 +590,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         const int k = kBK * c + e;
                         sc[e] = (k < s.L) ? __ldg(srow + k) : 0.f;
                     }
-                    float va[16], vb[16];
-                    tmem_ld16(tl + d1col + (uint32_t)(kBK * c), va);
-                    tmem_ld16(tl + d1col + (uint32_t)(kBK * c + 16), vb);
+                    float vd[32];
+                    tmem_ld32(tl + d1col + (uint32_t)(kBK * c), vd);
                     if (c == s.nch - 1) {
                         // D1 is read: the next tile's first product may overwrite it
                         fence_before();
@@ -608,7 +607,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
-                            const float x = (hh ? vb[e] : va[e]) * sc[16 * hh + e];
+                            const float x = vd[16 * hh + e] * sc[16 * hh + e];
                             hi[e] = tf32_round(x);
                             lo[e] = x - hi[e];
                         }
@@ -792,6 +791,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         if (lane == 0) {
             RingPos dr, tr, tr2, ar;
             uint32_t d1_phase = 0;
+            uint32_t dct_seen = 0;   // resident DCT slots whose copy has been waited for
             // one product of a tile: its nch X chunks from ring A (or, fused
             // D2, ring B) against the DCT chunks (resident: slots dbase + c;
             // else the DCT ring)
@@ -803,9 +803,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 for (int c = 0; c < nch; ++c) {
                     const int ds = cfg.resident ? dbase + c : dr.slot, ts = xr.slot;
                     const uint32_t dpar = cfg.resident ? 0u : dr.phase;
-                    if (!mbar_wait_ab(b_dfull + 8 * ds, dpar, abort) ||
+                    const bool dwait = !cfg.resident || !((dct_seen >> ds) & 1u);
+                    if ((dwait && !mbar_wait_ab(b_dfull + 8 * ds, dpar, abort)) ||
                         !mbar_wait_ab(fb + 8 * ts, xr.phase, abort))
                         return false;
+                    if (cfg.resident) dct_seen |= 1u << ds;
                     fence_after();
                     // B: the DCT chunk [hi: Np rows][lo: Np rows]; a K step of 8
                     // adds 256 bytes (16 in descriptor units).  A: TMEM columns
