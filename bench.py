@@ -146,6 +146,20 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def fused12(L):
+    """Whether the library runs z-step passes 1 and 2 (axis of L faces) as one
+    launch: the same fit test as its fused layout (both split DCT matrices
+    resident beside two raw X stages and the epilogue buffers; one
+    accumulator, D1 and three operand slots in 512 tensor-memory columns)."""
+    if L < 2:
+        return False
+    npad, nch = (L + 15) // 16 * 16, (L + 31) // 32
+    dslot, rslot, epi = 2 * npad * 128, 128 * 32 * 4, 8 * 4096
+    acc = (npad + 31) // 32 * 32
+    return (2 * nch <= 8 and 2 * nch * dslot + 2 * rslot <= 226 * 1024 - epi
+            and (512 - 2 * acc) // 64 >= 3)
+
+
 def roofline(prof, w, g, nf, sac):
     """Per phase: algorithmic HBM bytes and algorithmic flops per launch over
     the measured average launch time; the binding roof (larger fraction) of
@@ -167,7 +181,11 @@ def roofline(prof, w, g, nf, sac):
     # one array in, one out; the update reads b, u, t2, z and writes u, z
     per_face_bytes = {"zpass0": 12, "zpass1": 8, "zpass2": 8, "zpass3": 8, "admm_update": 24}
     flops = {"zpass0": 2 * L1 * nf, "zpass3": 2 * L1 * nf, "zpass1": 2 * L2 * nf, "zpass2": 2 * L2 * nf}
-    nphase = {k: v for k, v in prof.items() if v[1] > 0}
+    fused = fused12(L2)
+    if fused:
+        # passes 1 and 2 in one launch (phase 1): one array in, one out, both products
+        flops["zpass1"] = 4 * L2 * nf
+    nphase = {k: v for k, v in prof.items() if v[1] > 0 and not (fused and k == "zpass2")}
     tot_ms = sum(v[0] for v in nphase.values())
     kernels = {}
     for k, (ms, n) in nphase.items():
@@ -205,7 +223,7 @@ def roofline(prof, w, g, nf, sac):
     else:
         bname = f"k_bstep<float,float,{kpl}>"
     names = {"bstep": bname, "bstep_refine": f"k_bstep_list<double,float,{kpl}>",
-             "zpass0": zk(L1, 0), "zpass1": zk(L2, 1), "zpass2": zk(L2, 2),
+             "zpass0": zk(L1, 0), "zpass1": "k_axis_tc<4>" if fused else zk(L2, 1), "zpass2": zk(L2, 2),
              "zpass3": zk(L1, 3), "admm_update": "k_admm_update"}
     for k in kernels:
         kernels[k]["kernel"] = names.get(k, k)
