@@ -150,14 +150,15 @@ def fused12(L):
     """Whether the library runs z-step passes 1 and 2 (axis of L faces) as one
     launch: the same fit test as its fused layout (both split DCT matrices
     resident beside two raw X stages and the epilogue buffers; one
-    accumulator, D1 and three operand slots in 512 tensor-memory columns)."""
+    accumulator, two D1 buffers and three operand slots in 512 tensor-memory
+    columns)."""
     if L < 2:
         return False
     npad, nch = (L + 15) // 16 * 16, (L + 31) // 32
     dslot, rslot, epi = 2 * npad * 128, 128 * 32 * 4, 8 * 4096
     acc = (npad + 31) // 32 * 32
     return (2 * nch <= 8 and 2 * nch * dslot + 2 * rslot <= 226 * 1024 - epi
-            and (512 - 2 * acc) // 64 >= 3)
+            and (512 - 3 * acc) // 64 >= 3)
 
 
 def roofline(prof, w, g, nf, sac):

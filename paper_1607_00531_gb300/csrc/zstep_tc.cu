@@ -216,12 +216,11 @@ bool tc_cfg_fuse12(TcCfg* c) {
     while (c->sr < tc::kMaxRStages && need() + c->rslot <= budget) c->sr++;
     c->acc_cols = (uint32_t)((c->acc_need + 31) & ~31);
     // the accumulators, D1, then at least two X slots
-    // one accumulator, D1, then ring A (at least two slots) and ring B (at
-    // least one).  The tile period is set by the chain D1 -> ring B -> D2 ->
-    // D1 free, so the columns of a second accumulator serve better as ring
-    // slots (the epilogue of tile t ends before D2 of tile t + 1 starts)
+    // one accumulator (D2), two D1 buffers (the next tile's first product
+    // runs while group B converts this tile's D1), then ring A (at least two
+    // slots) and ring B (at least one)
     c->nacc = 1;
-    const int slots = (int)((tc::kTmemCols - 2 * c->acc_cols) / tc::kXCols);
+    const int slots = (int)((tc::kTmemCols - 3 * c->acc_cols) / tc::kXCols);   // D2, two D1
     if (slots < 3) return false;
     c->st2 = (slots >= 4) ? 2 : 1;
     c->st = slots - c->st2 > tc::kMaxTStages ? tc::kMaxTStages : slots - c->st2;
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // barriers: DCT full / empty, raw X full / empty, TMEM X full / empty,
     // accumulator full / empty, drain; fused: D1 full / empty
-    __shared__ __align__(8) unsigned long long bar[2 * kMaxDStages + 2 * kMaxRStages + 4 * kMaxTStages + 7];
+    __shared__ __align__(8) unsigned long long bar[2 * kMaxDStages + 2 * kMaxRStages + 4 * kMaxTStages + 9];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int* abort = &abort_flag;
@@ -453,9 +452,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const uint32_t b_afull = b_tempty + 8 * kMaxTStages;
     const uint32_t b_aempty = b_afull + 16;
     const uint32_t b_drain = b_aempty + 16;
-    const uint32_t b_d1full = b_drain + 8;
-    const uint32_t b_d1empty = b_d1full + 8;
-    const uint32_t b_t2full = b_d1empty + 8;   // fused: ring B (D2's operand)
+    const uint32_t b_d1full = b_drain + 8;      // fused: two D1 buffers
+    const uint32_t b_d1empty = b_d1full + 16;
+    const uint32_t b_t2full = b_d1empty + 16;   // fused: ring B (D2's operand)
     const uint32_t b_t2empty = b_t2full + 8 * kMaxTStages;
     const uint32_t s_base = smem_u32(smem_raw);
     const uint32_t s_raw = s_base + (uint32_t)cfg.sd * cfg.dslot;   // raw X ring after the DCT ring
@@ -482,8 +481,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             mbar_init(b_aempty + 8 * i, kEpiWarps);
         }
         mbar_init(b_drain, 1);
-        mbar_init(b_d1full, 1);
-        mbar_init(b_d1empty, 4);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b_d1full + 8 * i, 1);
+            mbar_init(b_d1empty + 8 * i, 4);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -492,9 +493,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_slot;
-    // TMEM columns: the accumulators, (fused) D1, then the X slots
+    // TMEM columns: the accumulators, (fused) two D1 buffers, then the X slots
     const uint32_t d1col = (uint32_t)cfg.nacc * cfg.acc_cols;
-    const uint32_t xcol0 = d1col + (FUSED ? cfg.acc_cols : 0u);
+    const uint32_t xcol0 = d1col + (FUSED ? 2u * cfg.acc_cols : 0u);
     const long long t0 = blockIdx.x, dt = gridDim.x;
 
     if (FUSED && warp < kConvWarps) {
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         const uint32_t colA = xcol0, colB = xcol0 + (uint32_t)cfg.st * kXCols;
         RingPos rr, tr;
-        uint32_t d1_phase = 0;
+        uint32_t nd1 = 0;   // group B: D1 buffers consumed (buffer nd1 & 1, parity (nd1 >> 1) & 1)
         for (long long t = t0; t < total; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
             if (!s.active) continue;
@@ -573,9 +574,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     tr.next(cfg.st);
                 }
             } else {
-                ok = __all_sync(kFull, mbar_wait_ab(b_d1full, d1_phase, abort));
+                const uint32_t d1b = nd1 & 1u;
+                ok = __all_sync(kFull, mbar_wait_ab(b_d1full + 8 * d1b, (nd1 >> 1) & 1u, abort));
                 if (!ok) break;
-                d1_phase ^= 1u;
+                ++nd1;
                 fence_after();
                 const int L2s = J.F[J.ax2];
                 long long s_between = 1;
@@ -591,12 +593,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         sc[e] = (k < s.L) ? __ldg(srow + k) : 0.f;
                     }
                     float vd[32];
-                    tmem_ld32(tl + d1col + (uint32_t)(kBK * c), vd);
+                    tmem_ld32(tl + d1col + d1b * cfg.acc_cols + (uint32_t)(kBK * c), vd);
                     if (c == s.nch - 1) {
                         // D1 is read: the next tile's first product may overwrite it
                         fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(b_d1empty);
+                        if (lane == 0) mbar_arrive(b_d1empty + 8 * d1b);
                     }
                     const int ts = tr.slot;
                     ok = __all_sync(kFull, mbar_wait_ab(b_t2empty + 8 * ts, tr.phase ^ 1u, abort));
@@ -790,7 +792,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
             RingPos dr, tr, tr2, ar;
-            uint32_t d1_phase = 0;
             uint32_t dct_seen = 0;   // resident DCT slots whose copy has been waited for
             // one product of a tile: its nch X chunks from ring A (or, fused
             // D2, ring B) against the DCT chunks (resident: slots dbase + c;
@@ -834,23 +835,67 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 }
                 return true;
             };
-            for (long long t = t0; t < total && !*abort; t += dt) {
+            if (FUSED) {
+                // D1 of tile t (two buffers) is issued before D2 of the
+                // previous tile, so that the tensor pipe works on the next
+                // tile while converter group B turns D1 into D2's operand
+                uint32_t n1 = 0;       // D1 products issued (buffer n1 & 1)
+                bool pending = false;  // a tile whose D2 is still to do
+                int pnch = 0, pNp = 0;
+                for (long long t = t0;; t += dt) {
+                    const bool more = t < total && !*abort;
+                    bool have = false;
+                    int nch = 0, Np = 0;
+                    if (more) {
+                        const TcTile s = tc_tile(jobs, njobs, prefix, PIN, t);
+                        have = s.active;
+                        nch = s.nch;
+                        Np = s.Np;
+                    }
+                    bool ok = true;
+                    if (have) {
+                        const uint32_t b = n1 & 1u;
+                        ok = mbar_wait_ab(b_d1empty + 8 * b, ((n1 >> 1) & 1u) ^ 1u, abort);
+                        if (ok) {
+                            fence_after();
+                            ok = product(tmem + d1col + b * cfg.acc_cols, 0, nch, Np, 0, Np, false);
+                        }
+                        if (ok) {
+                            mma_commit(b_d1full + 8 * b);
+                            ++n1;
+                        }
+                    }
+                    if (ok && pending) {
+                        const int a = ar.slot;
+                        ok = mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort);
+                        if (ok) {
+                            fence_after();
+                            ok = product(tmem + (uint32_t)a * cfg.acc_cols, pnch, pnch, pNp, 0, pNp, true);
+                        }
+                        if (ok) {
+                            mma_commit(b_afull + 8 * a);
+                            ar.next(cfg.nacc);
+                        }
+                        pending = false;
+                    }
+                    if (!ok) break;
+                    if (have) {
+                        pending = true;
+                        pnch = nch;
+                        pNp = Np;
+                    }
+                    if (!more && !pending) break;
+                }
+            }
+            for (long long t = t0; !FUSED && t < total && !*abort; t += dt) {
                 const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
                 if (!s.active) continue;
                 int n0, nN;
                 tc_unit_cols(t, nfull, s.Np, n0, nN);
-                if (FUSED) {
-                    // D1 = C2 X, once the converters have read the previous tile's D1
-                    if (!mbar_wait_ab(b_d1empty, d1_phase ^ 1u, abort)) break;
-                    fence_after();
-                    if (!product(tmem + d1col, 0, s.nch, s.Np, n0, nN, false)) break;
-                    mma_commit(b_d1full);
-                    d1_phase ^= 1u;
-                }
                 const int a = ar.slot;
                 if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
                 fence_after();
-                if (!product(tmem + (uint32_t)a * cfg.acc_cols, FUSED ? s.nch : 0, s.nch, s.Np, n0, nN, FUSED)) break;
+                if (!product(tmem + (uint32_t)a * cfg.acc_cols, 0, s.nch, s.Np, n0, nN, false)) break;
                 mma_commit(b_afull + 8 * a);
                 ar.next(cfg.nacc);
             }
