@@ -356,6 +356,10 @@ SEG_CASES = [
     ((4, 145, 10), 1),      # 146 faces: 9 segments of 17
     ((5, 256, 11), 1),      # 257 faces: 16 segments of 17, 55 lines
     ((2, 271, 17), 1),      # 272 faces: exactly 16 segments of 17
+    # lines a multiple of 16 apart (aligned rows): tiles staged by TMA tensor copies
+    ((9, 70, 32), 1),       # 71 faces, 18 tiles
+    ((24, 143, 256), 1),    # 144 faces, 384 tiles: more tiles than resident CTAs (next tile prefetched)
+    ((20, 256, 256), 1),    # 257 faces, 320 tiles: the same with segments of 17
 ]
 
 
@@ -377,8 +381,10 @@ def test_bstep_mixed_segment_kernel(sac, m, pe):
     assert np.max(np.abs(outs[0] - outs[1])) / h[pe] <= 1e-4
 
 
-@pytest.mark.parametrize("m,pe", [((9, 70, 21), 1), ((5, 256, 11), 1)])
+@pytest.mark.parametrize("m,pe", [((9, 70, 21), 1), ((5, 256, 11), 1), ((9, 70, 32), 1), ((3, 256, 32), 1)])
 def test_bstep_mixed_segment_kernel_queues_blocked_lines(sac, m, pe):
+    # (the last two: TMA-staged tiles, queued lines restored in the tile's
+    # shared-memory buffer before its tensor store)
     # steep targets: many lines' unconstrained steps cross |D1 b| = 1; the
     # segment kernel leaves them to the FP64 active-set method
     h, I1, I2, b, _, u = case_data(m, pe, seed=40, max_d=0.8)
