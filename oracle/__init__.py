@@ -86,7 +86,8 @@ class RefParams(ctypes.Structure):
                  "eps_iter", "eps_grad", "gn_rel_grad")] + \
                [(n, ctypes.c_int) for n in
                 ("max_iter", "n_sqp", "max_pcg", "precond", "max_gn", "nthreads", "adapt_rho")] + \
-               [(n, ctypes.c_double) for n in ("rho_min", "rho_tau", "rho_mu")]
+               [(n, ctypes.c_double) for n in ("rho_min", "rho_tau", "rho_mu")] + \
+               [("knot32", ctypes.c_int)]
 
 
 @dataclass
@@ -118,6 +119,10 @@ class Params:
     rho_min: float = 1e2
     rho_tau: float = 1.3
     rho_mu: float = 10.0
+    # 1: interpolation positions formed in FP32 as the single-precision
+    # kernels form them (the model's interval is an integer decided in
+    # floating point; tests of FP32 kernels take that decision in FP32)
+    knot32: int = 0
 
     def c(self) -> RefParams:
         return RefParams(**{f.name: getattr(self, f.name) for f in fields(self)})

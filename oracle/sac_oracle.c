@@ -58,6 +58,7 @@ typedef struct {
     int max_iter, n_sqp, max_pcg, precond, max_gn, nthreads;
     int adapt_rho;                /* 0 fixed rho, 1 adaptive, 2 adaptive with lower bound */
     double rho_min, rho_tau, rho_mu;
+    int knot32;                   /* 1: interpolation positions formed in FP32 (see line_cells) */
 } ref_params;
 
 enum { REF_OK = 0, REF_NOTCONV = 1, REF_EINVAL = -1, REF_EINFEASIBLE = -4, REF_ELSFAIL = -7 };
@@ -157,16 +158,29 @@ static void interp_line(const double* I, long stride, long m, double t, double* 
 typedef struct { double r, d, Jd, Ju; } cellq;
 
 static void line_cells(const grid_t* g, const double* I1, const double* I2, long cstride,
-                       const double* bl, long sb, cellq* q) {
+                       const double* bl, long sb, cellq* q, int knot32) {
     long m = g->mpe;
     double h = g->h[g->pe];
     for (long j = 0; j < m; ++j) {
         double b0 = bl[j * sb], b1 = bl[(j + 1) * sb];
         double a = 0.5 * (b0 + b1);       /* A1 b: displacement at the cell centre */
         double d = (b1 - b0) / h;         /* D1 b: derivative along PE */
+        double t1 = (double)j + a / h, t2 = (double)j - a / h;
+        if (knot32) {
+            /* The interval of the piecewise-linear model (an integer) is decided
+               by a floating-point position; its slope jumps at the knots, so a
+               position that rounds across one changes the Jacobian, not just
+               its last digits.  For comparison with single-precision kernels the
+               position is formed as they form it: A1 b and 1/h rounded to FP32,
+               then one fused multiply-add with the cell index. */
+            const float af = 0.5f * ((float)b0 + (float)b1);
+            const float invh = (float)(1.0 / h);
+            t1 = (double)fmaf(af, invh, (float)j);
+            t2 = (double)fmaf(-af, invh, (float)j);
+        }
         double v1, s1, v2, s2;
-        interp_line(I1, cstride, m, (double)j + a / h, &v1, &s1);   /* I_v(x + A b)  */
-        interp_line(I2, cstride, m, (double)j - a / h, &v2, &s2);   /* I_-v(x - A b) */
+        interp_line(I1, cstride, m, t1, &v1, &s1);   /* I_v(x + A b)  */
+        interp_line(I2, cstride, m, t2, &v2, &s2);   /* I_-v(x - A b) */
         double g1 = s1 / h, g2 = s2 / h;  /* spatial derivatives d/dx */
         q[j].r = v1 * (1.0 + d) - v2 * (1.0 - d);
         q[j].d = d;
@@ -249,7 +263,7 @@ int ref_objective(int nd, const int* m, const double* h, int pe, const ref_param
 #pragma omp for schedule(static)
         for (long l = 0; l < L; ++l) {
             line_cells(&g, I1 + line_cell0(&g, l), I2 + line_cell0(&g, l), g.n_inner,
-                       b + line_face0(&g, l), g.n_inner, q);
+                       b + line_face0(&g, l), g.n_inner, q, prm->knot32);
             double sD = 0.0, sP = 0.0, sS = 0.0;
             for (long j = 0; j < g.mpe; ++j) {
                 sD += q[j].r * q[j].r;
@@ -287,7 +301,7 @@ int ref_residual(int nd, const int* m, const double* h, int pe,
 #pragma omp for schedule(static)
         for (long l = 0; l < L; ++l) {
             long c0 = line_cell0(&g, l);
-            line_cells(&g, I1 + c0, I2 + c0, g.n_inner, b + line_face0(&g, l), g.n_inner, q);
+            line_cells(&g, I1 + c0, I2 + c0, g.n_inner, b + line_face0(&g, l), g.n_inner, q, 0);
             for (long j = 0; j < g.mpe; ++j) r[c0 + j * g.n_inner] = q[j].r;
         }
         free(q);
@@ -313,7 +327,7 @@ int ref_gradient(int nd, const int* m, const double* h, int pe, const ref_params
 #pragma omp for schedule(static)
         for (long l = 0; l < L; ++l) {
             long f0 = line_face0(&g, l), c0 = line_cell0(&g, l), s = g.n_inner;
-            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q);
+            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q, prm->knot32);
             for (long i = 0; i <= g.mpe; ++i) {
                 double gi = 0.0;
                 if (i > 0) gi += q[i - 1].Ju * q[i - 1].r;
@@ -389,7 +403,7 @@ int ref_apply(int nd, const int* m, const double* h, int pe, const ref_params* p
 #pragma omp for schedule(static)
         for (long l = 0; l < L; ++l) {
             long f0 = line_face0(&g, l), c0 = line_cell0(&g, l), s = g.n_inner;
-            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q);
+            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q, prm->knot32);
             for (long j = 0; j < g.mpe; ++j) {
                 w[j] = q[j].Jd * v[f0 + j * s] + q[j].Ju * v[f0 + (j + 1) * s];   /* J_r v */
                 e[j] = (v[f0 + (j + 1) * s] - v[f0 + j * s]) / hpe;               /* D1 v */
@@ -634,7 +648,7 @@ int ref_bstep(int nd, const int* m, const double* h, int pe, const ref_params* p
             long f0 = line_face0(&g, l), c0 = line_cell0(&g, l), s = g.n_inner;
             for (long i = 0; i < n; ++i) bl[i] = b_out[f0 + i * s];
             for (int it = 0; it < prm->n_sqp; ++it) {
-                line_cells(&g, I1 + c0, I2 + c0, s, bl, 1, q);
+                line_cells(&g, I1 + c0, I2 + c0, s, bl, 1, q, prm->knot32);
                 for (long i = 0; i < n; ++i) {
                     double Jup = (i > 0) ? q[i - 1].Ju : 0.0, rup = (i > 0) ? q[i - 1].r : 0.0;
                     double Jdn = (i < mp) ? q[i].Jd : 0.0, rdn = (i < mp) ? q[i].r : 0.0;
@@ -1006,7 +1020,7 @@ int ref_precond_solve(int nd, const int* m, const double* h, int pe, const ref_p
 #pragma omp for schedule(static)
         for (long l = 0; l < L; ++l) {
             long f0 = line_face0(&g, l), c0 = line_cell0(&g, l), s = g.n_inner;
-            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q);
+            line_cells(&g, I1 + c0, I2 + c0, s, b + f0, s, q, prm->knot32);
             for (long i = 0; i < n; ++i) {
                 double Jup = (i > 0) ? q[i - 1].Ju : 0.0, Jdn = (i < mp) ? q[i].Jd : 0.0;
                 double nadj = (double)((i > 0) + (i < mp));

@@ -78,8 +78,11 @@ __device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* 
     const float a = 0.5f * (b0 + b1);
     const float d = (b1 - b0) * inv_h;
     float v1, s1, v2, s2;
-    interp(I1, mf, jf + a * inv_h, v1, s1);
-    interp(I2, mf, jf - a * inv_h, v2, s2);
+    // positions with one rounding each (explicit fused multiply-add): the
+    // model's interval is decided from them, and the FP32 oracle forms them
+    // the same way
+    interp(I1, mf, __fmaf_rn(a, inv_h, jf), v1, s1);
+    interp(I2, mf, __fmaf_rn(-a, inv_h, jf), v2, s2);
     const float g1 = s1 * inv_h, g2 = s2 * inv_h;
     c.r = v1 * (1.f + d) - v2 * (1.f - d);
     const float p = 0.5f * (g1 * (1.f + d) + g2 * (1.f - d));
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     const float* sU = Rg.u;
     const long long L = L0 + lane;
     const bool valid = L < nlines;   // rows of lanes past the last line are not staged
-    const float h = (float)J.hpe, inv_h = 1.f / h, ih2 = inv_h * inv_h;
+    const float inv_h = (float)(1.0 / J.hpe), ih2 = inv_h * inv_h;   // (1/h rounded once, as in the warp kernels)
     const float alpha = (float)J.alpha, rho = (float)J.rho, us = (float)J.uscale;
     const bool on = g < G && valid;
     const int s = g * S;

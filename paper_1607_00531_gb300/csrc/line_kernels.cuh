@@ -103,6 +103,17 @@ __device__ __forceinline__ void warp_load_line(S* __restrict__ s, const S* __res
     for (int p = threadIdx.x & 31; p < len; p += 32) s[p] = g[base + (long long)p * stride];
 }
 
+// Position j + a / h of a displaced cell centre in index units.  The model's
+// interval is an integer decided from this value, so every kernel of a
+// precision forms it the same way: with FP32 storage (the FP32 and mixed
+// paths, FP64 arithmetic included) a and 1/h rounded to FP32 and one fused
+// multiply-add, as the FP32 oracle (knot32) does; with FP64 storage in FP64.
+template <typename S, typename T>
+__device__ __forceinline__ T cell_pos(T a, T inv_h, int j) {
+    if constexpr (sizeof(S) == 4) return (T)__fmaf_rn((float)a, (float)inv_h, (float)j);
+    else return (T)j + a * inv_h;
+}
+
 // Per-cell quantities of the lane's K cells j = lane*K + k at field values
 // bv (faces lane*K + k) and bnext (face lane*K + K, from the next lane):
 // r = I1(x + A1 b)(1 + D1 b) - I2(x - A1 b)(1 - D1 b); Jd = dr_j/db_j,
@@ -120,8 +131,8 @@ __device__ __forceinline__ void lane_cells(const S* __restrict__ rowI1, const S*
             T a = T(0.5) * (b0 + b1);
             T d = (b1 - b0) * inv_h;
             T v1, s1, v2, s2;
-            interp_line<T, S>(rowI1, m, T(j) + a * inv_h, v1, s1);
-            interp_line<T, S>(rowI2, m, T(j) - a * inv_h, v2, s2);
+            interp_line<T, S>(rowI1, m, cell_pos<S>(a, inv_h, j), v1, s1);
+            interp_line<T, S>(rowI2, m, cell_pos<S>(-a, inv_h, j), v2, s2);
             T g1 = s1 * inv_h, g2 = s2 * inv_h;
             r[k] = v1 * (T(1) + d) - v2 * (T(1) - d);
             T p = T(0.5) * (g1 * (T(1) + d) + g2 * (T(1) - d));

@@ -45,6 +45,11 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def f32(a):
+    """FP32 rounding of an array, kept in FP64 (the values FP32 storage holds)."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
 def case_data(m, pe, seed=0, max_d=0.5):
     h = tuple(1.0 / m[0] for _ in m)
     I1 = ph.random_images(m, seed + 1)
@@ -369,7 +374,11 @@ def test_bstep_mixed_segment_kernel(sac, m, pe):
     # (1e-3 voxel) and against the warp-per-line FP32 kernel
     h, I1, I2, b, z, u = case_data(m, pe, seed=30)
     og = oracle.Grid(m, h, pe)
-    b_ref, st = oracle.bstep(og, oracle.Params(alpha=0.5, rho=100.0), I1, I2, b, z, u)
+    # the model's interval at a displaced position is an integer decided in
+    # floating point: the oracle takes it in FP32 as the kernels do, on the
+    # FP32-rounded inputs they see (knot32); the rest of it runs in FP64
+    b_ref, st = oracle.bstep(og, oracle.Params(alpha=0.5, rho=100.0, knot32=1), f32(I1), f32(I2), f32(b), f32(z),
+                             f32(u))
     g = sac.grid(m, h, pe)
     outs = []
     for kern in (0, 1):
@@ -391,7 +400,8 @@ def test_bstep_mixed_segment_kernel_queues_blocked_lines(sac, m, pe):
     rng = np.random.default_rng(6)
     z = b + 3.0 * h[pe] * rng.normal(size=b.shape)
     og = oracle.Grid(m, h, pe)
-    b_ref, st = oracle.bstep(og, oracle.Params(alpha=1e-3, rho=1e5), I1, I2, b, z, u)
+    b_ref, st = oracle.bstep(og, oracle.Params(alpha=1e-3, rho=1e5, knot32=1), f32(I1), f32(I2), f32(b), f32(z),
+                             f32(u))
     assert st["active"] > 0 and st["capped"] == 0
     g = sac.grid(m, h, pe)
     p = sac.params(alpha=1e-3, rho=1e5, prec="mixed", bstep_kernel=0)

@@ -710,3 +710,31 @@ def test_pcg_meets_the_forcing_condition_and_gn_descends():
     Js = r["hist"][:, 0]
     assert np.all(np.diff(Js) <= 0) and Js[0] < oracle.objective(g, prm, d["I1"], d["I2"], b)["J"]
     assert oracle.max_abs_d1(g, r["b"]) < 1
+
+
+def test_knot32_takes_the_interval_decision_in_fp32():
+    # Sec. 3's piecewise-linear image model has a slope that jumps at the
+    # knots.  A displacement just below a whole cell in FP64 (1 - 1e-9 cells)
+    # rounds to the knot itself in FP32: with knot32 the oracle must then use
+    # the interval right of the knot, as it does in FP64 for an exact knot;
+    # without it, the interval left of the knot (a different gradient).
+    m, pe = (8, 2), 0
+    h = (1.0 / 8, 1.0 / 8)
+    g = oracle.Grid(m, h, pe)
+    rng = np.random.default_rng(11)
+    I1 = rng.uniform(0.2, 1.0, size=m)
+    I2 = rng.uniform(0.2, 1.0, size=m)
+    below = np.full((9, 2), (1.0 - 1e-9) * h[0])   # positions j + 1 - 1e-9
+    at = np.full((9, 2), 1.0 * h[0])               # positions exactly j + 1
+    p64 = oracle.Params(alpha=0.3)
+    p32 = oracle.Params(alpha=0.3, knot32=1)
+    g_at = oracle.gradient(g, p64, I1, I2, at)
+    g_below64 = oracle.gradient(g, p64, I1, I2, below)
+    g_below32 = oracle.gradient(g, p32, I1, I2, below)
+    scale = np.abs(g_at).max()
+    assert np.abs(g_below32 - g_at).max() <= 1e-6 * scale
+    assert np.abs(g_below64 - g_at).max() >= 1e-2 * scale
+    # away from knots the two forms agree to FP32 position rounding
+    mid = np.full((9, 2), 0.37 * h[0])
+    assert np.allclose(oracle.gradient(g, p32, I1, I2, mid), oracle.gradient(g, p64, I1, I2, mid), rtol=1e-5,
+                       atol=1e-6 * scale)
