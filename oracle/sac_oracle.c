@@ -22,7 +22,10 @@
  * boundary, units of b, the D1^T in the b-step gradient and in grad P, gamma
  * in P_block, the step form of the QP, the active-set start, the number of SQP
  * passes, the DCT type, the line search) are the ones listed in the design
- * notes; each is restated at the place it is used.
+ * notes; each is restated at the place it is used.  One option serves the
+ * comparison with single-precision kernels only: with knot32 the position at
+ * which the image model is evaluated is formed in FP32 as they form it (the
+ * model's interval is an integer decided in floating point), all else FP64.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py.
  */
