@@ -59,8 +59,8 @@ __device__ __forceinline__ void interp(const float* __restrict__ row, float mf, 
     const int k = (int)fl;
     const float f = tc - fl;
     const float left = row[k * kLines], right = row[(k + 1) * kLines];
-    v = (1.f - f) * left + f * right;
     dv = right - left;
+    v = fmaf(f, dv, left);   // (1 - f) left + f right
 }
 
 struct Cell {
@@ -83,10 +83,13 @@ __device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* 
     // the same way
     interp(I1, mf, __fmaf_rn(a, inv_h, jf), v1, s1);
     interp(I2, mf, __fmaf_rn(-a, inv_h, jf), v2, s2);
-    const float g1 = s1 * inv_h, g2 = s2 * inv_h;
-    c.r = v1 * (1.f + d) - v2 * (1.f - d);
-    const float p = 0.5f * (g1 * (1.f + d) + g2 * (1.f - d));
-    const float q = (v1 + v2) * inv_h;
+    // r = v1 (1 + d) - v2 (1 - d); with g = s / h the slopes in x:
+    // p = (g1 (1 + d) + g2 (1 - d)) / 2, q = (v1 + v2) / h (fewer operations
+    // in this arrangement)
+    const float sv = v1 + v2;
+    c.r = fmaf(d, sv, v1 - v2);
+    const float p = (0.5f * inv_h) * fmaf(d, s1 - s2, s1 + s2);
+    const float q = sv * inv_h;
     c.Jd = p - q;
     c.Ju = p + q;
     c.d = d;
