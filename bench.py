@@ -146,6 +146,23 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def max_over_ranks(t_ms, dist_mod, device):
+    """The slowest rank's time: every rank takes part (any backend); one rank
+    or no process group returns its own."""
+    if not dist_mod:
+        return t_ms
+    import torch
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(tt, op=dist_mod.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world, units_per_rank, steps, t_ms):
+    """Whole-job throughput: the units of every rank (replicas of the same
+    volume) over the slowest rank's time."""
+    return world * units_per_rank * steps / (t_ms / 1e3)
+
+
 def fused12(L):
     """Whether the library runs z-step passes 1 and 2 (axis of L faces) as one
     launch: the same fit test as its fused layout (both split DCT matrices
@@ -447,11 +464,8 @@ def main():
     assert int(bt.stats()["iters"][0]) == args.warmup + args.steps
     bt.finish()
     bt.close()
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * nf * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, dist, dev)
+    value = job_value(world, nf, args.steps, t_ms)
     clocks = clk.summary()
     if args.only_mixed:
         if rank == 0:
