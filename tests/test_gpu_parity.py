@@ -460,3 +460,31 @@ def test_zstep_mixed_tensor_cores(sac, m, pe):
         np.testing.assert_allclose(nr[:3], ref, rtol=1e-4)
     assert rel(outs[0], outs[1]) < TC_TOL
     assert rel(outs[0], z_ref) < 2 * TC_TOL
+
+
+# ---------------------------------------------------------------- the benchmark's volume
+
+@pytest.mark.xfail(strict=True, reason=(
+    "mixed b-step at the benchmark's grid (h = 1/256, alpha = 50): 1.06e-3 voxel max against the 1e-3 bar; "
+    "the per-line GN system has condition ~1e5 (4 alpha / h^2 against rho + J^2) and its FP32 elimination "
+    "carries ~4e-5 of a step of ~20 voxels (FP32 assembly alone: 3e-6 voxel)"))
+def test_full_size_bstep_matches_the_oracle(sac):
+    # the 256 x 256 x 80 volume of the benchmark (5.26M faces) with its
+    # parameters and b-step kernel: the persistent TMA-staged segment kernel
+    # over 1280 tiles of 16 lines (synthetic images of that size; the oracle
+    # takes the model's interval decisions in FP32 on the FP32-rounded inputs,
+    # as for the smaller cases)
+    m, pe = (256, 256, 80), 1
+    h = tuple(1.0 / x for x in m)
+    I1, I2 = ph.random_images(m, 1), ph.random_images(m, 2)
+    b = f32(ph.random_field(m, pe, h, 3, max_d=0.5))
+    rng = np.random.default_rng(4)
+    z = f32(b + 0.05 * h[pe] * rng.normal(size=b.shape))
+    u = f32(0.05 * h[pe] * rng.normal(size=b.shape))
+    og = oracle.Grid(m, h, pe)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=50.0, rho=100.0, prec="mixed", near_bound=1e-3)
+    out, capped = sac.bstep(g, p, cu(I1, torch.float32), cu(I2, torch.float32), cu(b), cu(z), cu(u))
+    assert not capped
+    b_ref, _ = oracle.bstep(og, oracle.Params(alpha=50.0, rho=100.0, knot32=1), f32(I1), f32(I2), b, z, u)
+    assert np.max(np.abs(out.cpu().numpy() - b_ref)) / h[pe] <= 1e-3
