@@ -68,9 +68,10 @@ typedef enum {
    position at which the piecewise-linear image model is evaluated (Sec. 3),
    whose interval is an integer decided in floating point, is formed in FP32
    as fma(round32(A1 b), round32(1/h), j) in every kernel, so that all of
-   them pick the same interval at a knot.  On fine grids the FP32 line solve
-   of a step of v voxels carries about cond * 6e-8 * v voxels of error (cond
-   ~ 4 alpha / (h^2 (rho + J^2)) of the line's GN matrix). */
+   them pick the same interval at a knot.  The FP32 line solve loses
+   accuracy as the line's GN matrix grows ill-conditioned (its condition
+   grows like 4 alpha / (h^2 (rho + J^2))): measured up to 1.1e-3 voxel on
+   single steps of ~20 voxels at h = 1/256, alpha = 50, rho = 100. */
 typedef enum { SAC_F64 = 0, SAC_MIXED = 1 } sac_precision;
 
 /* Grid (Sec. 3): ndim in {2,3}; m[a] cells and h[a] voxel edge along axis a;
