@@ -163,21 +163,6 @@ def job_value(world, units_per_rank, steps, t_ms):
     return world * units_per_rank * steps / (t_ms / 1e3)
 
 
-def fused12(L):
-    """Whether the library runs z-step passes 1 and 2 (axis of L faces) as one
-    launch: the same fit test as its fused layout (both split DCT matrices
-    resident beside two raw X stages and the epilogue buffers; one
-    accumulator, two D1 buffers and three operand slots in 512 tensor-memory
-    columns)."""
-    if L < 2:
-        return False
-    npad, nch = (L + 15) // 16 * 16, (L + 31) // 32
-    dslot, rslot, epi = 2 * npad * 128, 128 * 32 * 4, 8 * 4096
-    acc = (npad + 31) // 32 * 32
-    return (2 * nch <= 8 and 2 * nch * dslot + 2 * rslot <= 226 * 1024 - epi
-            and (512 - 3 * acc) // 64 >= 3)
-
-
 def roofline(prof, w, g, nf, sac):
     """Per phase: algorithmic HBM bytes and algorithmic flops per launch over
     the measured average launch time; the binding roof (larger fraction) of
@@ -199,7 +184,7 @@ def roofline(prof, w, g, nf, sac):
     # one array in, one out; the update reads b, u, t2, z and writes u, z
     per_face_bytes = {"zpass0": 12, "zpass1": 8, "zpass2": 8, "zpass3": 8, "admm_update": 24}
     flops = {"zpass0": 2 * L1 * nf, "zpass3": 2 * L1 * nf, "zpass1": 2 * L2 * nf, "zpass2": 2 * L2 * nf}
-    fused = fused12(L2)
+    fused = sac.zstep_fused(g, sac.params(alpha=w.alpha, rho=w.rho, prec="mixed"))
     if fused:
         # passes 1 and 2 in one launch (phase 1): one array in, one out, both products
         flops["zpass1"] = 4 * L2 * nf

@@ -130,6 +130,13 @@ const char* sac_status_string(int status);
 /* Workspace for the single-volume entry points below. */
 size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p);
 
+/* Host only (no device needed): 1 when the z-step of this grid and these
+   parameters runs its second-axis DCT, spectral scale and inverse DCT
+   (passes 1 and 2, Sec. 4.2 Eq. dctdiag) as one tensor-core launch, 0 when
+   it runs them as separate launches or on the SIMT path, SAC_EINVAL for an
+   invalid grid or parameters. */
+int sac_zstep_fused(const sac_grid* g, const sac_params* p);
+
 /* Objective (Sec. 3, Eqs. D, S, P, JGN): out[0..3] = {J_GN, D, S, P} with
    J_GN = D + alpha S + P; P = 0 when beta == 0 and +inf when beta > 0 and
    some |D1 b| >= 1.  b: face array (double). */

@@ -637,6 +637,12 @@ size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p) {
     return P.bytes;
 }
 
+int sac_zstep_fused(const sac_grid* g, const sac_params* p) {
+    Plan P;
+    if (plan_layout(g, p, nullptr, &P) != SAC_OK) return SAC_EINVAL;
+    return (P.use_tc && P.fuse12) ? 1 : 0;
+}
+
 int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const void* I2, const double* b,
                   double* out4, void* ws, size_t ws_bytes, void* stream) {
     if (!I1 || !I2 || !b || !out4) return SAC_EINVAL;

@@ -62,6 +62,7 @@ def lib():
             "sac_version": (ctypes.c_int, []),
             "sac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "sac_workspace_bytes": (sz, [G, P]),
+            "sac_zstep_fused": (ctypes.c_int, [G, P]),
             "sac_objective": (ctypes.c_int, [G, P, vp, vp, vp, dp, vp, sz, vp]),
             "sac_gradient": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, sz, vp]),
             "sac_corrected_images": (ctypes.c_int, [G, P, vp, vp, vp, vp, vp, dp, dp, vp, sz, vp]),
@@ -153,6 +154,14 @@ def workspace_bytes(g, p):
 def _torch():
     import torch
     return torch
+
+
+def zstep_fused(g, p):
+    """Whether the z-step runs passes 1 and 2 as one launch (host only)."""
+    r = int(lib().sac_zstep_fused(ctypes.byref(g), ctypes.byref(p)))
+    if r < 0:
+        raise SacError("sac_zstep_fused", r)
+    return bool(r)
 
 
 def workspace(g, p, device="cuda"):

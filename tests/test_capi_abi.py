@@ -51,3 +51,20 @@ def test_entry_points_reject_null_arrays(L):
     assert L.sac_admm_solve(ctypes.byref(g), ctypes.byref(p), None, None, None, None, None, None, None, None, None,
                             None, 0, None) == sac.SAC_EINVAL
     assert L.sac_status_string(-4).decode() == "infeasible starting field"
+
+
+def test_zstep_fusion_decision_needs_no_device(L):
+    # passes 1 and 2 run as one launch when both DCT matrices of the second
+    # non-PE axis fit beside the rings (axes up to 96 faces), only on the
+    # tensor-core path of the mixed precision
+    def fused(m, pe, prec):
+        g = sac.grid(m, tuple(1.0 / x for x in m), pe)
+        return sac.zstep_fused(g, sac.params(prec=prec))
+    assert fused((256, 256, 80), 1, "mixed")
+    assert fused((64, 60, 96), 1, "mixed")
+    assert not fused((64, 60, 112), 1, "mixed")
+    assert not fused((64, 60, 128), 1, "mixed")
+    assert not fused((256, 256, 80), 1, "f64")
+    assert not fused((128, 128), 1, "mixed")          # 2D: no second axis to fuse
+    with pytest.raises(sac.SacError):
+        sac.zstep_fused(sac.grid((16, 12), (0.1, 0.1), 2), sac.params())
