@@ -64,7 +64,7 @@ __device__ __forceinline__ void interp(const float* __restrict__ row, float mf, 
 }
 
 struct Cell {
-    float r, Jd, Ju, d;   // residual, dr/db_j, dr/db_{j+1}, D1 b
+    float r, Jd, Ju, d, p2;   // residual, dr/db_j, dr/db_{j+1}, D1 b, dr/db_j + dr/db_{j+1}
 };
 
 // residual of cell j between faces j and j+1 (b0, b1) and its two Jacobian
@@ -93,11 +93,13 @@ __device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* 
     c.Jd = p - q;
     c.Ju = p + q;
     c.d = d;
+    c.p2 = p + p;   // Jd + Ju without the cancellation of q
     const bool in = (unsigned)j < (unsigned)m;
     c.r = in ? c.r : 0.f;
     c.Jd = in ? c.Jd : 0.f;
     c.Ju = in ? c.Ju : 0.f;
     c.d = in ? c.d : 0.f;
+    c.p2 = in ? c.p2 : 0.f;
     return c;
 }
 
@@ -108,17 +110,34 @@ __device__ __forceinline__ Cell cell(const float* __restrict__ I1, const float* 
 // variant for interior segments measured slower overall: the warp holding the
 // boundary segments then ran other code than the rest of the CTA, missing in
 // the instruction cache, and held every CTA barrier.)
+//
+// Row sums.  On fine grids the rows are dominated by the regulariser:
+// alpha/h^2 ~ 3e6 on the diagonal's off-diagonal neighbours against a row sum
+// rho + (J_r^T J_r row sum) of ~1e2 .. 1e5, so forming the diagonal (or an
+// eliminated pivot d_k - sub_k C_{k-1}) in FP32 loses the row sum, which is
+// what sets the smooth part of the solution.  Each row is therefore given by
+// its off-diagonals and its row sum
+//   sigma_i = rho + Ju_{i-1} (Jd_{i-1} + Ju_{i-1}) + Jd_i (Jd_i + Ju_i)
+// (the alpha h^-2 D1^T D1 part sums to zero; the diagonal is sigma - sub - sup,
+// the same matrix), and every eliminated row carries its row sum T along: a
+// pivot is then a sum of terms of one sign (row sum, minus the off-diagonals
+// it still couples) instead of a difference of two ~alpha/h^2 numbers.  T0 is
+// row 0's row sum, Tl row S-1's, T1 the row sum of row 1 after the backward
+// pass (x_1 + A_1 x_0 + C_1 x_{S-1}), accumulated here from the forward rows:
+// T1 = sum_{k=1}^{S-2} T_k prod_{j=1}^{k-1} (-C_j).
 template <int S>
 __device__ __forceinline__ void forward(const float* __restrict__ rI1, const float* __restrict__ rI2,
                                         const float* __restrict__ rB, const float* __restrict__ rZ,
                                         const float* __restrict__ rU, int m, int s, float inv_h, float ih2,
                                         float alpha, float rho, float us, float (&A)[S], float (&C)[S],
-                                        float (&R)[S], float& b_end) {
+                                        float (&R)[S], float& b_end, float& T0, float& T1, float& Tl) {
     const float bp = rB[max(s - 1, 0) * kLines];
     const float bprev = (s >= 1) ? bp : 0.f;
     float bcur = rB[s * kLines];   // (s <= m for every segment of the line)
     const float mf = (float)m, sf = (float)s;   // cell positions as floats: sf + k (exact)
+    const float aih2 = alpha * ih2;
     Cell prev = cell(rI1, rI2, m, mf, s - 1, sf - 1.f, bprev, bcur, inv_h);
+    float Tp = 0.f, P = 1.f;   // row sum of the previous eliminated row; running product of -C
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const int i = s + k;
@@ -127,28 +146,40 @@ __device__ __forceinline__ void forward(const float* __restrict__ rI1, const flo
         if (k == S - 1) b_end = bn;   // b of row min(s + S, m): the bound test's last read
         const Cell cur = cell(rI1, rI2, m, mf, i, sf + (float)k, bcur, bnext, inv_h);
         const int ic = min(i, m);
-        const float nadj = (float)((i > 0) + (i < m));
         const float zu = us * rU[ic * kLines] - rZ[ic * kLines];
         const bool face = i <= m;
-        const float dg = face ? prev.Ju * prev.Ju + cur.Jd * cur.Jd + alpha * nadj * ih2 + rho : 1.f;
-        const float sup = (face && i < m) ? cur.Jd * cur.Ju - alpha * ih2 : 0.f;
-        const float sub = (face && i > 0) ? prev.Jd * prev.Ju - alpha * ih2 : 0.f;
+        // (cells outside [0, m) are zero, so the sum needs no boundary test)
+        const float sig = face ? fmaf(prev.Ju, prev.p2, fmaf(cur.Jd, cur.p2, rho)) : 1.f;
+        const float sup = (face && i < m) ? fmaf(cur.Jd, cur.Ju, -aih2) : 0.f;
+        const float sub = (face && i > 0) ? fmaf(prev.Jd, prev.Ju, -aih2) : 0.f;
         const float rhs =
             face ? -(prev.Ju * prev.r + cur.Jd * cur.r + alpha * (prev.d - cur.d) * inv_h + rho * (bcur + zu)) : 0.f;
         // rows 0 and 1 normalised; row k >= 2 rewritten as
         // x_k + A_k x_0 + C_k x_{k+1} = R_k (row 0: A_0 multiplies the
         // previous segment's last unknown)
+        float Tk;
         if (k < 2) {
-            const float inv = fdiv(1.f, dg);
+            const float inv = fdiv(1.f, (sig - sub) - sup);
             A[k] = sub * inv;
             C[k] = sup * inv;
             R[k] = rhs * inv;
+            Tk = sig * inv;
         } else {
-            const float inv = fdiv(1.f, dg - sub * C[k - 1]);
+            // row k minus sub_k times row k-1: row sum sm, pivot = sm minus
+            // the x_0 and x_{k+1} coefficients
+            const float sm = fmaf(-sub, Tp, sig);
+            const float inv = fdiv(1.f, fmaf(sub, A[k - 1], sm) - sup);
             R[k] = (rhs - sub * R[k - 1]) * inv;
             C[k] = sup * inv;
             A[k] = -sub * A[k - 1] * inv;
+            Tk = sm * inv;
         }
+        if (k == 0) T0 = Tk;
+        if (k == 1) T1 = Tk;
+        if (k >= 2 && k <= S - 2) T1 = fmaf(P, Tk, T1);
+        if (k >= 1 && k <= S - 3) P *= -C[k];
+        if (k == S - 1) Tl = Tk;
+        Tp = Tk;
         prev = cur;
         bcur = bnext;
     }
@@ -292,10 +323,10 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
                 int* __restrict__ status) {
     static_assert(S >= 4, "a segment needs at least 4 faces");
     constexpr int NL = kLines;
-    // reduced rows per segment and line: (sub, sup, rhs) of the first and of
-    // the last unknown; then the segment's first / last unknown
+    // reduced rows per segment and line: (sub, sup, rhs, row sum) of the
+    // first and of the last unknown; then the segment's first / last unknown
     // (component-major: the threads of a warp touch consecutive words)
-    __shared__ float sE[6][kMaxSeg][NL];
+    __shared__ float sE[8][kMaxSeg][NL];
     __shared__ float sX[2][kMaxSeg][NL];
     __shared__ int sFlag[NL];
     extern __shared__ __align__(128) float sdyn[];   // TMA destinations: 128-byte aligned
@@ -371,7 +402,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     float A[S], C[S], R[S];    // eliminated rows of the segment
     float b_end = 0.f;
     if (on) {
-        forward<S>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R, b_end);
+        float T0, T1, Tl;      // row sums (see forward)
+        forward<S>(rI1, rI2, rB, sZ + lane, sU + lane, m, s, inv_h, ih2, alpha, rho, us, A, C, R, b_end, T0, T1,
+                   Tl);
         // rows S-3 .. 1 rewritten as x_k + A_k x_0 + C_k x_{S-1} = R_k
 #pragma unroll
         for (int k = S - 3; k >= 1; --k) {
@@ -380,18 +413,23 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
             C[k] = -C[k] * C[k + 1];
         }
         {
-            // row 0: x_0 + A_0 x_prev + C_0 x_{S-1} = R_0
-            const float inv = fdiv(1.f, 1.f - C[0] * A[1]);
+            // row 0: x_0 + A_0 x_prev + C_0 x_{S-1} = R_0; its pivot 1 - C_0 A_1
+            // formed from its row sum T0 - C_0 T1
+            const float t = fmaf(-C[0], T1, T0);
+            const float inv = fdiv(1.f, fmaf(C[0], C[1], t - A[0]));
             R[0] = (R[0] - C[0] * R[1]) * inv;
             C[0] = -C[0] * C[1] * inv;
             A[0] = A[0] * inv;
+            T0 = t * inv;
         }
         sE[0][g][lane] = A[0];
         sE[1][g][lane] = C[0];
         sE[2][g][lane] = R[0];
-        sE[3][g][lane] = A[S - 1];
-        sE[4][g][lane] = C[S - 1];
-        sE[5][g][lane] = R[S - 1];
+        sE[3][g][lane] = T0;
+        sE[4][g][lane] = A[S - 1];
+        sE[5][g][lane] = C[S - 1];
+        sE[6][g][lane] = R[S - 1];
+        sE[7][g][lane] = Tl;
     }
     __syncthreads();
     // the images, z, u and the other b buffer are free: copy the next tile
@@ -399,43 +437,50 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     if (g == 0) sFlag[lane] = 0;
     {
         // The line's reduced system: unknown 2q = first of segment q, 2q+1 =
-        // its last; row r couples r-1 (a) and r+1 (c), unit diagonal; 2G <=
-        // 32 rows, solved by parallel cyclic reduction with one lane per row
-        // (rows 2G .. 31 are identity rows): at stride s every row eliminates
-        // its couplings to rows r -+ s with those rows, then is scaled back
-        // to a unit diagonal, so that after ceil(log2 2G) steps x_r = d_r.
+        // its last; row r couples r-1 (a) and r+1 (c), unit diagonal, row
+        // sum t = 1 + a + c; 2G <= 32 rows, solved by parallel cyclic
+        // reduction with one lane per row (rows 2G .. 31 are identity rows):
+        // at stride s every row eliminates its couplings to rows r -+ s with
+        // those rows, then is scaled back to a unit diagonal, so that after
+        // ceil(log2 2G) steps x_r = d_r.  The new diagonal 1 - a c_- - c a_+
+        // is formed from the new row sum t - a t_- - c t_+ plus a a_- + c c_+
+        // (terms of one sign; see forward).
         // Every full warp of the CTA takes lines warp, warp + nw, ...
         const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5), q = threadIdx.x & 31, N = 2 * G;
         // Two lines per pass (l, l + nw) as independent chains for latency.
         for (int l = w; l < NL && w < nw; l += 2 * nw) {   // (a partial last warp takes no line)
             const int l1 = l + nw;
             const bool two = l1 < NL;
-            float a[2] = {0.f, 0.f}, c[2] = {0.f, 0.f}, d[2] = {0.f, 0.f};
+            float a[2] = {0.f, 0.f}, c[2] = {0.f, 0.f}, d[2] = {0.f, 0.f}, tr[2] = {1.f, 1.f};
             if (q < N) {
-                const int e = 3 * (q & 1), sg = q >> 1;
+                const int e = 4 * (q & 1), sg = q >> 1;
                 a[0] = sE[e][sg][l];
                 c[0] = sE[e + 1][sg][l];
                 d[0] = sE[e + 2][sg][l];
+                tr[0] = sE[e + 3][sg][l];
                 if (two) {
                     a[1] = sE[e][sg][l1];
                     c[1] = sE[e + 1][sg][l1];
                     d[1] = sE[e + 2][sg][l1];
+                    tr[1] = sE[e + 3][sg][l1];
                 }
             }
             for (int st = 1; st < N; st <<= 1) {
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     float am = __shfl_up_sync(0xffffffffu, a[i], st), cm = __shfl_up_sync(0xffffffffu, c[i], st);
-                    float dm = __shfl_up_sync(0xffffffffu, d[i], st);
+                    float dm = __shfl_up_sync(0xffffffffu, d[i], st), tm = __shfl_up_sync(0xffffffffu, tr[i], st);
                     float ap = __shfl_down_sync(0xffffffffu, a[i], st), cp = __shfl_down_sync(0xffffffffu, c[i], st);
-                    float dp = __shfl_down_sync(0xffffffffu, d[i], st);
-                    if (q < st) am = cm = dm = 0.f;          // beyond the first row: identity
-                    if (q + st >= 32) ap = cp = dp = 0.f;    // beyond the last lane: identity
-                    const float inv = fdiv(1.f, 1.f - a[i] * cm - c[i] * ap);
+                    float dp = __shfl_down_sync(0xffffffffu, d[i], st), tp = __shfl_down_sync(0xffffffffu, tr[i], st);
+                    if (q < st) am = cm = dm = tm = 0.f;          // beyond the first row: identity
+                    if (q + st >= 32) ap = cp = dp = tp = 0.f;    // beyond the last lane: identity
+                    const float tn = tr[i] - a[i] * tm - c[i] * tp;
+                    const float inv = fdiv(1.f, fmaf(a[i], am, fmaf(c[i], cp, tn)));
                     const float dn = (d[i] - a[i] * dm - c[i] * dp) * inv;
                     a[i] = -a[i] * am * inv;
                     c[i] = -c[i] * cp * inv;
                     d[i] = dn;
+                    tr[i] = tn * inv;
                 }
             }
             if (q < N) {

@@ -118,10 +118,11 @@ __device__ __forceinline__ T cell_pos(T a, T inv_h, int j) {
 // bv (faces lane*K + k) and bnext (face lane*K + K, from the next lane):
 // r = I1(x + A1 b)(1 + D1 b) - I2(x - A1 b)(1 - D1 b); Jd = dr_j/db_j,
 // Ju = dr_j/db_{j+1} (Sec. 3, Jacobian of the residual); d = D1 b.
+// p2 = Jd + Ju, formed without the cancellation of the image-value terms.
 template <typename T, typename S, int K>
 __device__ __forceinline__ void lane_cells(const S* __restrict__ rowI1, const S* __restrict__ rowI2, int m,
                                            T inv_h, const T (&bv)[K], T bnext, T (&r)[K], T (&Jd)[K],
-                                           T (&Ju)[K], T (&dc)[K]) {
+                                           T (&Ju)[K], T (&dc)[K], T (&p2)[K]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -140,10 +141,18 @@ __device__ __forceinline__ void lane_cells(const S* __restrict__ rowI1, const S*
             Jd[k] = p - q;
             Ju[k] = p + q;
             dc[k] = d;
+            p2[k] = p + p;
         } else {
-            r[k] = T(0); Jd[k] = T(0); Ju[k] = T(0); dc[k] = T(0);
+            r[k] = T(0); Jd[k] = T(0); Ju[k] = T(0); dc[k] = T(0); p2[k] = T(0);
         }
     }
+}
+template <typename T, typename S, int K>
+__device__ __forceinline__ void lane_cells(const S* __restrict__ rowI1, const S* __restrict__ rowI2, int m,
+                                           T inv_h, const T (&bv)[K], T bnext, T (&r)[K], T (&Jd)[K],
+                                           T (&Ju)[K], T (&dc)[K]) {
+    T p2[K];
+    lane_cells<T, S, K>(rowI1, rowI2, m, inv_h, bv, bnext, r, Jd, Ju, dc, p2);
 }
 
 // ------------------------------------------------------------------------
@@ -452,29 +461,33 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
         }
     }
     for (int it = 0; it < n_sqp; ++it) {
-        T r[K], Jd[K], Ju[K], dc[K];
+        T r[K], Jd[K], Ju[K], dc[K], p2[K];
         T bnext = from_next(bv[0]);
-        lane_cells<T, S, K>(rowI1, rowI2, m, inv_h, bv, bnext, r, Jd, Ju, dc);
+        lane_cells<T, S, K>(rowI1, rowI2, m, inv_h, bv, bnext, r, Jd, Ju, dc, p2);
         T Ju_p = from_prev(Ju[K - 1]), r_p = from_prev(r[K - 1]), d_p = from_prev(dc[K - 1]);
-        T aa[K], dd[K], cc[K], xh[K];
+        T p2_p = from_prev(p2[K - 1]);
+        // rows by off-diagonals and row sums (warp_tridiag_solve_rs): the
+        // alpha h^-2 D1^T D1 part has zero row sums, so
+        // sum_i = rho + Ju_{i-1} (Jd_{i-1} + Ju_{i-1}) + Jd_i (Jd_i + Ju_i)
+        T aa[K], sg[K], cc[K], xh[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int i = lane * K + k;
             if (i <= m) {
                 T Jup = k ? Ju[k - 1] : Ju_p, rup = k ? r[k - 1] : r_p, dup = k ? dc[k - 1] : d_p;
-                if (i == 0) { Jup = T(0); rup = T(0); dup = T(0); }
-                T nadj = T((i > 0) + (i < m));
-                dd[k] = Jup * Jup + Jd[k] * Jd[k] + alpha * nadj * ih2 + rho;
+                T pup = k ? p2[k - 1] : p2_p;
+                if (i == 0) { Jup = T(0); rup = T(0); dup = T(0); pup = T(0); }
+                sg[k] = rho + Jup * pup + Jd[k] * p2[k];
                 cc[k] = (i < m) ? (Jd[k] * Ju[k] - alpha * ih2) : T(0);
                 xh[k] = -(Jup * rup + Jd[k] * r[k] + alpha * (dup - dc[k]) * inv_h + rho * (bv[k] + zu[k]));
             } else {
-                dd[k] = T(1); cc[k] = T(0); xh[k] = T(0);
+                sg[k] = T(1); cc[k] = T(0); xh[k] = T(0);
             }
         }
         T cprev = from_prev(cc[K - 1]);
 #pragma unroll
         for (int k = 0; k < K; ++k) aa[k] = k ? cc[k - 1] : cprev;
-        warp_tridiag_solve<T, K>(aa, dd, cc, xh);
+        warp_tridiag_solve_rs<T, K>(aa, cc, sg, xh);
         // ratio test of the full step from x = 0 (line_qp's first pass)
         T sn = from_next(xh[0]);
         bool blocked = false;

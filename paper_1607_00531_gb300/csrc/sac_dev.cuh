@@ -263,6 +263,135 @@ __device__ __forceinline__ void warp_tridiag_solve(T (&a)[K], T (&d)[K], T (&c)[
     for (int i = 1; i < K - 1; ++i) r[i] = r[i] - a[i] * x0 - c[i] * xl;
 }
 
+// The same solve for rows given by their off-diagonals and their row sums:
+// row i is a_i x_{i-1} + (s_i - a_i - c_i) x_i + c_i x_{i+1} = r_i.  For the
+// b-step's rows, dominated by alpha h^-2 D1^T D1 (zero row sums), the row sum
+// s_i is known to full relative precision while the diagonal and every pivot
+// d_i - a_i c_{i-1} of the elimination above are differences of numbers of
+// size alpha/h^2; here every eliminated row carries its row sum, and each
+// pivot is formed from it as a sum of terms of one sign (row sum minus the
+// off-diagonals the row still couples), which keeps the FP32 solve accurate
+// where the elimination above loses the row sum.  The same matrix and the same
+// steps otherwise.  Rows beyond the system: a = c = r = 0, s = 1.
+template <typename T, int K>
+__device__ __forceinline__ void warp_tridiag_solve_rs(T (&a)[K], T (&c)[K], const T (&s)[K], T (&r)[K]) {
+    static_assert(K >= 3, "need at least 3 rows per lane");
+    const int lane = threadIdx.x & 31;
+    // forward: rows 0 and 1 normalised; row i >= 2 rewritten as
+    // x_i + a_i x_0 + c_i x_{i+1} = r_i; t: row sums of the rewritten rows.
+    // t1 collects the row sum of row 1 after the backward pass,
+    // sum_{i=1}^{K-2} t_i prod_{j=1}^{i-1} (-c_j).
+    T t0, t1, tl, tp, P = T(1);
+    {
+        T inv = fdiv(T(1), (s[0] - a[0]) - c[0]);
+        a[0] *= inv; c[0] *= inv; r[0] *= inv;
+        t0 = s[0] * inv;
+        inv = fdiv(T(1), (s[1] - a[1]) - c[1]);
+        a[1] *= inv; c[1] *= inv; r[1] *= inv;
+        t1 = s[1] * inv;
+        tp = t1;
+        tl = t1;
+        if (K >= 4) P = -c[1];
+    }
+#pragma unroll
+    for (int i = 2; i < K; ++i) {
+        const T sm = s[i] - a[i] * tp;
+        const T inv = fdiv(T(1), (sm + a[i] * a[i - 1]) - c[i]);
+        r[i] = (r[i] - a[i] * r[i - 1]) * inv;
+        c[i] = c[i] * inv;
+        a[i] = -a[i] * a[i - 1] * inv;
+        const T ti = sm * inv;
+        if (i <= K - 2) t1 += P * ti;
+        if (i <= K - 3) P *= -c[i];
+        tp = ti;
+        tl = ti;
+    }
+    // backward: rows K-3 .. 1 rewritten as x_i + a_i x_0 + c_i x_{K-1} = r_i
+#pragma unroll
+    for (int i = K - 3; i >= 1; --i) {
+        r[i] -= c[i] * r[i + 1];
+        a[i] -= c[i] * a[i + 1];
+        c[i] = -c[i] * c[i + 1];
+    }
+    // row 0: x_0 + a_0 x_{prev last} + c_0 x_{K-1} = r_0, pivot 1 - c_0 a_1
+    // from the row sum t0 - c_0 t1
+    {
+        const T t = t0 - c[0] * t1;
+        const T inv = fdiv(T(1), (t - a[0]) + c[0] * c[1]);
+        r[0] = (r[0] - c[0] * r[1]) * inv;
+        c[0] = -c[0] * c[1] * inv;
+        a[0] = a[0] * inv;
+        t0 = t * inv;
+    }
+    // reduced system as in warp_tridiag_solve, rows (A, B, C, R) with their
+    // row sums M = A + B + C; a combination of rows combines the row sums, and
+    // the new diagonal is M' - A' - C' (terms of one sign)
+    T eA = a[0], eB = T(1), eC = c[0], eR = r[0], eM = t0;
+    T oA = a[K - 1], oB = T(1), oC = c[K - 1], oR = r[K - 1], oM = tl;
+    {
+        T pA = __shfl_up_sync(kFull, oA, 1), pB = __shfl_up_sync(kFull, oB, 1);
+        T pC = __shfl_up_sync(kFull, oC, 1), pR = __shfl_up_sync(kFull, oR, 1);
+        T pM = __shfl_up_sync(kFull, oM, 1);
+        T nA = __shfl_down_sync(kFull, eA, 1), nB = __shfl_down_sync(kFull, eB, 1);
+        T nC = __shfl_down_sync(kFull, eC, 1), nR = __shfl_down_sync(kFull, eR, 1);
+        T nM = __shfl_down_sync(kFull, eM, 1);
+        if (lane == 0) { pA = 0; pB = 1; pC = 0; pR = 0; pM = 1; }
+        if (lane == 31) { nA = 0; nB = 1; nC = 0; nR = 0; nM = 1; }
+        T k1 = fdiv(eA, pB), k2 = fdiv(eC, oB);
+        T neA = -k1 * pA, neC = -k2 * oC;
+        T neM = eM - k1 * pM - k2 * oM;
+        T neB = (neM + k1 * pA) + k2 * oC;
+        T neR = eR - k1 * pR - k2 * oR;
+        T k3 = fdiv(oA, eB), k4 = fdiv(oC, nB);
+        T noA = -k3 * eA, noC = -k4 * nC;
+        T noM = oM - k3 * eM - k4 * nM;
+        T noB = (noM + k3 * eA) + k4 * nC;
+        T noR = oR - k3 * eR - k4 * nR;
+        eA = neA; eB = neB; eC = neC; eR = neR; eM = neM;
+        oA = noA; oB = noB; oC = noC; oR = noR; oM = noM;
+    }
+#pragma unroll
+    for (int st = 1; st < 32; st <<= 1) {
+        T peA = __shfl_up_sync(kFull, eA, st), peB = __shfl_up_sync(kFull, eB, st);
+        T peC = __shfl_up_sync(kFull, eC, st), peR = __shfl_up_sync(kFull, eR, st);
+        T peM = __shfl_up_sync(kFull, eM, st);
+        T poA = __shfl_up_sync(kFull, oA, st), poB = __shfl_up_sync(kFull, oB, st);
+        T poC = __shfl_up_sync(kFull, oC, st), poR = __shfl_up_sync(kFull, oR, st);
+        T poM = __shfl_up_sync(kFull, oM, st);
+        T neA = __shfl_down_sync(kFull, eA, st), neB = __shfl_down_sync(kFull, eB, st);
+        T neC = __shfl_down_sync(kFull, eC, st), neR = __shfl_down_sync(kFull, eR, st);
+        T neM = __shfl_down_sync(kFull, eM, st);
+        T noA = __shfl_down_sync(kFull, oA, st), noB = __shfl_down_sync(kFull, oB, st);
+        T noC = __shfl_down_sync(kFull, oC, st), noR = __shfl_down_sync(kFull, oR, st);
+        T noM = __shfl_down_sync(kFull, oM, st);
+        if (lane < st) {
+            peA = 0; peB = 1; peC = 0; peR = 0; peM = 1;
+            poA = 0; poB = 1; poC = 0; poR = 0; poM = 1;
+        }
+        if (lane + st > 31) {
+            neA = 0; neB = 1; neC = 0; neR = 0; neM = 1;
+            noA = 0; noB = 1; noC = 0; noR = 0; noM = 1;
+        }
+        T k1 = fdiv(eA, peB), k2 = fdiv(eC, neB);
+        T xA = -k1 * peA, xC = -k2 * neC;
+        T xM = eM - k1 * peM - k2 * neM;
+        T xB = (xM + k1 * peA) + k2 * neC;
+        T xR = eR - k1 * peR - k2 * neR;
+        T k3 = fdiv(oA, poB), k4 = fdiv(oC, noB);
+        T yA = -k3 * poA, yC = -k4 * noC;
+        T yM = oM - k3 * poM - k4 * noM;
+        T yB = (yM + k3 * poA) + k4 * noC;
+        T yR = oR - k3 * poR - k4 * noR;
+        eA = xA; eB = xB; eC = xC; eR = xR; eM = xM;
+        oA = yA; oB = yB; oC = yC; oR = yR; oM = yM;
+    }
+    T x0 = fdiv(eR, eB), xl = fdiv(oR, oB);
+    r[0] = x0;
+    r[K - 1] = xl;
+#pragma unroll
+    for (int i = 1; i < K - 1; ++i) r[i] = r[i] - a[i] * x0 - c[i] * xl;
+}
+
 // ---------------------------------------------------------------- image model
 //
 // 1D linear interpolation of the m cell-centred samples of a PE line in index

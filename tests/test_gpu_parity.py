@@ -464,10 +464,6 @@ def test_zstep_mixed_tensor_cores(sac, m, pe):
 
 # ---------------------------------------------------------------- the benchmark's volume
 
-@pytest.mark.xfail(strict=True, reason=(
-    "mixed b-step at the benchmark's grid (h = 1/256, alpha = 50): 1.06e-3 voxel max against the 1e-3 bar; "
-    "the per-line GN system has condition ~1e5 (4 alpha / h^2 against rho + J^2) and its FP32 elimination "
-    "carries ~4e-5 of a step of ~20 voxels (FP32 assembly alone: 3e-6 voxel)"))
 def test_full_size_bstep_matches_the_oracle(sac):
     # the 256 x 256 x 80 volume of the benchmark (5.26M faces) with its
     # parameters and b-step kernel: the persistent TMA-staged segment kernel
@@ -487,4 +483,6 @@ def test_full_size_bstep_matches_the_oracle(sac):
     out, capped = sac.bstep(g, p, cu(I1, torch.float32), cu(I2, torch.float32), cu(b), cu(z), cu(u))
     assert not capped
     b_ref, _ = oracle.bstep(og, oracle.Params(alpha=50.0, rho=100.0, knot32=1), f32(I1), f32(I2), b, z, u)
-    assert np.max(np.abs(out.cpu().numpy() - b_ref)) / h[pe] <= 1e-3
+    err = np.max(np.abs(out.cpu().numpy() - b_ref)) / h[pe]
+    print(f"full-size mixed b-step: max |db| = {err:.3e} voxel")
+    assert err <= 1e-3
