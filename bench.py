@@ -52,22 +52,9 @@ def parse():
 
 
 def load_workload(name):
-    """Generate (or reuse a cached copy of) the seeded phantom pair."""
+    """The seeded phantom pair (cached in the temporary directory)."""
     from paper_1607_00531_gb300 import phantoms as ph
-    w = ph.WORKLOADS[name]
-    cache = os.path.join(tempfile.gettempdir(), f"sac_{name}_seed{w.seed}.npz")
-    if os.path.exists(cache):
-        z = np.load(cache)
-        d = {k: z[k] for k in z.files}
-        d.update(h=w.h, pe=w.pe, m=w.m, alpha=w.alpha, rho=w.rho)
-        d["peak_px"], d["max_d"] = float(d["peak_px"]), float(d["max_d"])
-        return w, d
-    d = ph.make_pair(w, dtype=np.float32)
-    try:
-        np.savez(cache, I1=d["I1"], I2=d["I2"], b_true=d["b_true"], peak_px=d["peak_px"], max_d=d["max_d"])
-    except OSError:
-        pass
-    return w, d
+    return ph.load_pair(name, np.float32)
 
 
 class Clocks:

@@ -334,6 +334,21 @@ int sac_profile_enable(int on);
 int sac_profile_read(double* ms, long long* launches, int reset);
 long long sac_launch_count(void);
 
+/* ---------------------------------------------------------------- failure detection
+ * Every wait of a kernel on an asynchronous copy or a tensor-core product is
+ * bounded: after `tests` barrier tests (each suspends the waiting thread for
+ * at most 20 us; default 50 000, about a second) the kernel raises an abort
+ * flag, its roles leave their loops, the copies and products in flight are
+ * drained (with the default bound), tensor memory is freed, and the call
+ * returns SAC_ETIMEOUT; the context stays usable.  sac_set_wait_limit changes
+ * that bound on the current device for the kernels selected by `which`
+ * (bit 0: the b-step segment kernel's tile copies; bit 1: the tensor-core
+ * z-step passes).  tests = 0 makes every such wait give up at once (a test of
+ * the abort path); tests < 0 restores the default.  Process-wide setting (no
+ * paper counterpart); returns SAC_EINVAL for other bits, SAC_ECUDA if the
+ * device rejects the update. */
+int sac_set_wait_limit(int which, long long tests);
+
 #ifdef __cplusplus
 }
 #endif

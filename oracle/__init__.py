@@ -61,6 +61,7 @@ def lib():
             "ref_corrected": g + [dp, dp, dp, dp, dp, dp],
             "ref_restrict": [ctypes.c_int, ip, dp, dp],
             "ref_prolong": [ctypes.c_int, ip, ctypes.c_int, dp, dp],
+            "ref_multilevel_admm": g + [P, ctypes.c_int, dp, dp, dp, dp, dp, lp, ip, dp, dp],
         }.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -296,67 +297,30 @@ def prolong(m, pe, bc):
 
 
 def multilevel_admm(m, h, pe, prm, I1, I2, levels):
-    """Coarse-to-fine ADMM (Sec. 4.4): images restricted level by level, ADMM
-    from b = 0 on the coarsest grid; each finer level starts from b0 = z0 =
-    (P b + P z) / 2 and u0 = 0 (the paper's third strategy; P b when the
-    average is infeasible), rho carried over (with adaptive rho: the last value
-    of the coarser level)."""
+    """Coarse-to-fine ADMM (Sec. 4.4; ref_multilevel_admm).  Returns one dict
+    per level, coarsest first, with the grid, the iterations, the converged
+    flag and the augmentation parameter carried to the next level; the finest
+    level's dict also holds b, z, u and the history."""
     m = tuple(int(x) for x in m)
     h = tuple(float(x) for x in h)
-    ims = [(np.asarray(I1, dtype=float), np.asarray(I2, dtype=float), m, h)]
-    for _ in range(levels - 1):
-        A, B, mm, hh = ims[-1]
-        ims.append((restrict(mm, A), restrict(mm, B), tuple(x // 2 for x in mm), tuple(2 * x for x in hh)))
-    ims.reverse()
+    g = Grid(m, h, pe)
+    b = np.zeros(g.face_shape)
+    z = np.zeros(g.face_shape)
+    u = np.zeros(g.face_shape)
+    iters = (ctypes.c_long * levels)()
+    conv = (ctypes.c_int * levels)()
+    rho = (ctypes.c_double * levels)()
+    hist = np.zeros((max(prm.max_iter, 1), 6))
+    st = lib().ref_multilevel_admm(*g.args(), ctypes.byref(prm.c()), int(levels), _dp(_f64(I1)), _dp(_f64(I2)),
+                                   _dp(b), _dp(z), _dp(u), iters, conv, rho, _dp(hist))
+    _check(st, "ref_multilevel_admm")
     out = []
-    b = z = None
-    rho = prm.rho
-    for lvl, (A, B, mm, hh) in enumerate(ims):
-        g = Grid(mm, hh, pe)
-        if b is None:
-            b0 = np.zeros(g.face_shape)
-        else:
-            b0 = _next_start(g, mm, pe, b, z)
-        p = Params(**{f.name: getattr(prm, f.name) for f in fields(prm)})
-        p.rho = rho
-        r = admm(g, p, A, B, b0, z0=b0.copy(), u0=np.zeros_like(b0), want_hist=True)
-        b, z = r["b"], r["z"]
-        rho = _rho_after(p, r)
-        out.append(dict(m=mm, h=hh, b=b, z=z, u=r["u"], iters=r["iters"], converged=r["converged"], rho=rho,
-                        hist=r["hist"]))
+    for lvl in range(levels):
+        f = 2 ** (levels - 1 - lvl)
+        out.append(dict(m=tuple(x // f for x in m), h=tuple(x * f for x in h), iters=iters[lvl],
+                        converged=bool(conv[lvl]), rho=rho[lvl]))
+    out[-1].update(b=b, z=z, u=u, hist=hist[:iters[levels - 1]])
     return out
-
-
-def _next_start(g, mm, pe, b, z):
-    # the third strategy's start (P b + P z) / 2; z is not constrained, so
-    # when the average leaves |D1 b| <= 1, P b (feasible with b); a start
-    # still outside by rounding is scaled back onto the set
-    b0 = 0.5 * (prolong(mm, pe, b) + prolong(mm, pe, z))
-    if max_abs_d1(g, b0) > 1.0:
-        b0 = prolong(mm, pe, b)
-    mx = max_abs_d1(g, b0)
-    if mx > 1.0:
-        b0 = b0 / mx
-    return b0
-
-
-def _rho_after(prm, r):
-    # rho after the last iteration: the last recorded rho, adapted once more
-    # unless the level stopped on its test (the rule is applied only to
-    # iterations that did not stop)
-    hs = r["hist"]
-    if len(hs) == 0:
-        return prm.rho
-    rho = hs[-1, 4]
-    if not prm.adapt_rho or r["converged"]:
-        return rho
-    rp, rd = hs[-1, 0], hs[-1, 1]
-    if rp > prm.rho_mu * rd:
-        return rho * prm.rho_tau
-    if rd > prm.rho_mu * rp:
-        nr = rho / prm.rho_tau
-        return rho if (prm.adapt_rho == 2 and nr < prm.rho_min) else nr
-    return rho
 
 
 def max_abs_d1(grid, b):

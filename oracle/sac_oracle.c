@@ -17,12 +17,13 @@
  *   - primal active-set QP with Schur-complement solves       (Sec. 4.2, Eqs. qp, schurasqp)
  *   - ADMM b-step (SQP), z-step (DCT), u-step, stopping       (Sec. 4.2, Eqs. admmStep1-3, dctdiag, admmStop)
  *   - block-Jacobi preconditioner and inexact GN-PCG          (Sec. 4.1, Eqs. Pblock, GNstep, inexactGNsolve, stopping1-3)
+ *   - image restriction, field prolongation, coarse-to-fine ADMM (Sec. 4.4)
  *
  * Readings where the paper is silent or garbled (interpolation at the
  * boundary, units of b, the D1^T in the b-step gradient and in grad P, gamma
  * in P_block, the step form of the QP, the active-set start, the number of SQP
- * passes, the DCT type, the line search) are the ones listed in the design
- * notes; each is restated at the place it is used.  One option serves the
+ * passes, the DCT type, the line search) are each stated at the place they
+ * are used.  One option serves the
  * comparison with single-precision kernels only: with knot32 the position at
  * which the image model is evaluated is formed in FP32 as they form it (the
  * model's interval is an integer decided in floating point), all else FP64.
@@ -938,9 +939,22 @@ double ref_max_abs_d1(int nd, const int* m, const double* h, int pe, const doubl
 /* unchanged.                                                                */
 /* info[0] = iterations, info[1] = converged flag, info[2] = capped QPs.     */
 /* ------------------------------------------------------------------------ */
+static int admm_run(int nd, const int* m, const double* h, int pe, const ref_params* prm,
+                    const double* I1, const double* I2, double* b, double* z, double* u,
+                    double* hist, long* info, double* rho_final);
+
 int ref_admm(int nd, const int* m, const double* h, int pe, const ref_params* prm,
              const double* I1, const double* I2, double* b, double* z, double* u,
              double* hist, long* info) {
+    return admm_run(nd, m, h, pe, prm, I1, I2, b, z, u, hist, info, NULL);
+}
+
+/* The iteration of ref_admm; rho_final (optional) receives the augmentation
+   parameter after the last iteration (adapted once more when that iteration
+   did not stop). */
+static int admm_run(int nd, const int* m, const double* h, int pe, const ref_params* prm,
+                    const double* I1, const double* I2, double* b, double* z, double* u,
+                    double* hist, long* info, double* rho_final) {
     grid_t g;
     int st = make_grid(nd, m, h, pe, &g);
     if (st) return st;
@@ -989,7 +1003,90 @@ int ref_admm(int nd, const int* m, const double* h, int pe, const ref_params* pr
     }
     free(zold); free(tmp);
     if (info) { info[0] = k; info[1] = conv; info[2] = capped_total; }
+    if (rho_final) *rho_final = pk.rho;
     return conv ? REF_OK : REF_NOTCONV;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coarse-to-fine ADMM (Sec. 4.4, multilevel strategy).  The images are      */
+/* restricted level by level (ref_restrict); ADMM runs from b = 0 on the     */
+/* coarsest grid; every finer level starts from the third initialisation    */
+/* strategy, b0 = z0 = (P b + P z) / 2 and u0 = 0, with P = ref_prolong.      */
+/* Readings: z is not constrained, so when the average leaves |D1 b| <= 1    */
+/* the start is P b (feasible with b); a start still outside by rounding is  */
+/* scaled back onto the set; the augmentation parameter carries from level   */
+/* to level (the value after the coarser level's last iteration).            */
+/* m, h: the finest grid (each coarser level halves m and doubles h; every   */
+/* axis must halve evenly).  Out: b, z, u on the finest grid; per level,     */
+/* coarsest first, iters[l], conv[l] and the carried rho_lvl[l]; hist        */
+/* (optional) the finest level's history as in ref_admm.                    */
+/* ------------------------------------------------------------------------ */
+int ref_multilevel_admm(int nd, const int* m, const double* h, int pe, const ref_params* prm, int levels,
+                        const double* I1, const double* I2, double* b, double* z, double* u,
+                        long* iters, int* conv, double* rho_lvl, double* hist) {
+    if (levels < 1 || levels > 12 || (nd != 2 && nd != 3)) return REF_EINVAL;
+    int M[12][3];
+    double H[12][3];
+    double* A[12];
+    double* B[12];
+    for (int a = 0; a < 3; ++a) {
+        M[0][a] = (a < nd) ? m[a] : 1;
+        H[0][a] = (a < nd) ? h[a] : 1.0;
+    }
+    for (int l = 1; l < levels; ++l)
+        for (int a = 0; a < 3; ++a) {
+            if (a < nd && (M[l - 1][a] % 2 || M[l - 1][a] < 2)) return REF_EINVAL;
+            M[l][a] = (a < nd) ? M[l - 1][a] / 2 : 1;
+            H[l][a] = (a < nd) ? 2.0 * H[l - 1][a] : 1.0;
+        }
+    A[0] = (double*)I1;
+    B[0] = (double*)I2;
+    for (int l = 1; l < levels; ++l) {
+        size_t nc = (size_t)M[l][0] * M[l][1] * M[l][2];
+        A[l] = (double*)malloc(sizeof(double) * nc);
+        B[l] = (double*)malloc(sizeof(double) * nc);
+        ref_restrict(nd, M[l - 1], A[l - 1], A[l]);
+        ref_restrict(nd, M[l - 1], B[l - 1], B[l]);
+    }
+    double rho = prm->rho;
+    double *bc = NULL, *zc = NULL;
+    int st = REF_OK;
+    for (int l = levels - 1; l >= 0; --l) {
+        size_t nf = (size_t)(M[l][0] + (pe == 0)) * (M[l][1] + (pe == 1)) * (M[l][2] + (pe == 2));
+        double* bl = (l == 0) ? b : (double*)malloc(sizeof(double) * nf);
+        double* zl = (l == 0) ? z : (double*)malloc(sizeof(double) * nf);
+        double* ul = (l == 0) ? u : (double*)malloc(sizeof(double) * nf);
+        if (!bc) {
+            memset(bl, 0, sizeof(double) * nf);
+        } else {
+            /* the third strategy's start */
+            ref_prolong(nd, M[l], pe, bc, bl);
+            ref_prolong(nd, M[l], pe, zc, zl);
+            for (size_t f = 0; f < nf; ++f) zl[f] = 0.5 * (bl[f] + zl[f]);
+            if (ref_max_abs_d1(nd, M[l], H[l], pe, zl) <= 1.0) memcpy(bl, zl, sizeof(double) * nf);
+            double mx = ref_max_abs_d1(nd, M[l], H[l], pe, bl);
+            if (mx > 1.0)
+                for (size_t f = 0; f < nf; ++f) bl[f] /= mx;
+            free(bc); free(zc);
+        }
+        memcpy(zl, bl, sizeof(double) * nf);
+        memset(ul, 0, sizeof(double) * nf);
+        ref_params pl = *prm;
+        pl.rho = rho;
+        long info[3];
+        int r = admm_run(nd, M[l], H[l], pe, &pl, A[l], B[l], bl, zl, ul, l == 0 ? hist : NULL, info, &rho);
+        if (r < 0 && st == REF_OK) st = r;
+        iters[levels - 1 - l] = info[0];
+        conv[levels - 1 - l] = (int)info[1];
+        rho_lvl[levels - 1 - l] = rho;
+        if (l > 0) {
+            free(ul);
+            bc = bl;
+            zc = zl;
+        }
+    }
+    for (int l = 1; l < levels; ++l) { free(A[l]); free(B[l]); }
+    return st;
 }
 
 /* ------------------------------------------------------------------------ */

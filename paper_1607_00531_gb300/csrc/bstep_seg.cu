@@ -683,4 +683,9 @@ cudaError_t launch_bstep_seg(const LineLaunch& L) {
     return cudaGetLastError();
 }
 
+// this translation unit's bounded-wait limit (tc_ptx.cuh), on the current device
+cudaError_t set_wait_tests_seg(long long tests) {
+    return cudaMemcpyToSymbol(tcx::g_wait_tests, &tests, sizeof(tests));
+}
+
 }  // namespace sac

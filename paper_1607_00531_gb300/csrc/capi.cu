@@ -616,6 +616,17 @@ int sac_profile_read(double* ms, long long* launches, int reset) {
 
 long long sac_launch_count(void) { return g_launches.load(); }
 
+int sac_set_wait_limit(int which, long long tests) {
+    if ((which & ~3) != 0) return SAC_EINVAL;
+    const long long n = tests < 0 ? kWaitTestsDefault : tests;
+    if (which & 1) SAC_CUDA(set_wait_tests_seg(n));
+    if (which & 2) {
+        SAC_CUDA(set_wait_tests_tc(n));
+        SAC_CUDA(set_wait_tests_tcn(n));
+    }
+    return SAC_OK;
+}
+
 const char* sac_status_string(int s) {
     switch (s) {
         case SAC_OK: return "ok";

@@ -17,6 +17,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // Status bits written by kernels (atomicOr into a device word).
 enum : int { kStQpCap = 1, kStNaN = 2, kStInfeasible = 4, kStTimeout = 8 };
 
+// Barrier tests a bounded device wait makes before it gives up (each test
+// suspends the thread for at most 20 us: about a second in all).
+constexpr long long kWaitTestsDefault = 50000;
+
 // One volume (job) as the kernels see it.  All pointers are device pointers;
 // element types are fixed by the launching code (float or double).
 struct Job {

@@ -106,6 +106,10 @@ inline long long seg_tiles(long long nlines) { return (nlines + seg_lines() - 1)
 size_t seg_smem_bytes(int mpe);   // dynamic shared memory of a CTA
 cudaError_t launch_bstep_seg(const LineLaunch& L);
 cudaError_t prepare_bstep_seg();
+// bounded-wait limits of the kernels with mbarrier waits (sac_set_wait_limit)
+cudaError_t set_wait_tests_seg(long long tests);
+cudaError_t set_wait_tests_tc(long long tests);
+cudaError_t set_wait_tests_tcn(long long tests);
 
 // prec: 0 FP64, 1 FP32, 2 FP64 compute on FP32 storage
 cudaError_t launch_bstep(int prec, const LineLaunch& L);

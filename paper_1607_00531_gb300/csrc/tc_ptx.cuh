@@ -11,7 +11,14 @@ namespace sac {
 namespace tcx {
 
 constexpr uint32_t kSuspendNs = 20000;             // longest suspension of one barrier test
-constexpr long long kWaitTests = 50000;            // barrier tests before a wait gives up (~1 s)
+constexpr long long kWaitTests = kWaitTestsDefault;   // barrier tests before a wait gives up (~1 s)
+
+// Tests a bounded wait (mbar_wait_ab) makes before it gives up: kWaitTests
+// unless set otherwise through sac_set_wait_limit (0: give up at once, which
+// exercises the abort path without a fault).  No relocatable device code, so
+// every translation unit including this header has its own copy and defines
+// a host setter for it (set_wait_tests_*).  Drain waits keep kWaitTests.
+static __device__ long long g_wait_tests = kWaitTests;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -67,11 +74,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
         : "=r"(ok) : "r"(a), "r"(parity), "n"(kSuspendNs) : "memory");
     return ok != 0;
 }
-// Bounded wait (at most kWaitTests tests, about a second) for the phase of
-// the given parity.  Gives up early when the CTA's abort flag is set; raises
-// the flag when the limit is reached.
+// Bounded wait (at most g_wait_tests tests, by default kWaitTests: about a
+// second) for the phase of the given parity.  Gives up early when the CTA's
+// abort flag is set; raises the flag when the limit is reached.
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t a, uint32_t parity, volatile int* abort) {
-    for (long long i = 0; i < kWaitTests; ++i) {
+    const long long lim = g_wait_tests;
+    for (long long i = 0; i < lim; ++i) {
         if (mbar_test(a, parity)) return true;
         if (*abort) return false;
     }

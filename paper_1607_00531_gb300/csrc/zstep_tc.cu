@@ -1222,4 +1222,9 @@ cudaError_t prepare_axis_tc() {
     return allow_max_dyn_smem((const void*)k_axis_tc<3>);
 }
 
+// this translation unit's bounded-wait limit (tc_ptx.cuh), on the current device
+cudaError_t set_wait_tests_tc(long long tests) {
+    return cudaMemcpyToSymbol(tcx::g_wait_tests, &tests, sizeof(tests));
+}
+
 }  // namespace sac

@@ -281,6 +281,34 @@ def make_pair(w: Workload, dtype=np.float64, chunk: int = 1 << 20):
                 sigma=sigma, alpha=w.alpha, rho=w.rho)
 
 
+def load_pair(name: str, dtype=np.float32):
+    """make_pair for a named workload of WORKLOADS, cached as an .npz file in
+    the temporary directory (the large phantoms take a minute to generate);
+    the cached arrays are those make_pair returns for the same seed."""
+    import os
+    import tempfile
+    w = WORKLOADS[name]
+    cache = os.path.join(tempfile.gettempdir(), f"sac_{name}_seed{w.seed}_{np.dtype(dtype).name}.npz")
+    if os.path.exists(cache):
+        try:
+            z = np.load(cache)
+            d = {k: z[k] for k in z.files}
+            d.update(h=w.h, pe=w.pe, m=w.m, alpha=w.alpha, rho=w.rho, sigma=float(d["sigma"]))
+            d["peak_px"], d["max_d"] = float(d["peak_px"]), float(d["max_d"])
+            return w, d
+        except (OSError, ValueError, KeyError):
+            pass
+    d = make_pair(w, dtype=dtype)
+    try:
+        tmp = cache + f".{os.getpid()}.npz"
+        np.savez(tmp, I1=d["I1"], I2=d["I2"], b_true=d["b_true"], peak_px=d["peak_px"], max_d=d["max_d"],
+                 sigma=d["sigma"])
+        os.replace(tmp, cache)
+    except OSError:
+        pass
+    return w, d
+
+
 def random_images(m, seed, lo=0.0, hi=1.0, zero_border=1):
     """Plain random cell images (uniform in [lo, hi]) with a zero border of
     `zero_border` cells, for unit tests that need generic data."""

@@ -97,6 +97,7 @@ def lib():
             "sac_profile_enable": (ctypes.c_int, [ctypes.c_int]),
             "sac_profile_read": (ctypes.c_int, [dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
             "sac_launch_count": (ctypes.c_longlong, []),
+            "sac_set_wait_limit": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -375,6 +376,15 @@ def profile_read(reset=True):
 
 def launch_count():
     return int(lib().sac_launch_count())
+
+
+WAIT_BSTEP, WAIT_ZSTEP = 1, 2
+
+
+def set_wait_limit(which, tests):
+    """Bounded-wait limit of the selected kernels on the current device
+    (tests < 0: the default)."""
+    _check("sac_set_wait_limit", lib().sac_set_wait_limit(int(which), int(tests)), allow_notconv=False)
 
 
 def _grid_array(grids):

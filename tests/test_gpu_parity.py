@@ -50,6 +50,38 @@ def f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+def knot_lines(og, b):
+    """Per line (the faces along the PE axis, moved last and flattened): whether
+    some cell's displaced position j +- A1 b / h lies within FP32 rounding of
+    a knot of the image model (an integer), where an FP32 and an FP64 position
+    can fall in different intervals (Sec. 3's model is piecewise linear)."""
+    pe, h = og.pe, og.h[og.pe]
+    bl = np.moveaxis(np.asarray(b, dtype=np.float64), pe, -1).reshape(-1, b.shape[pe])
+    a = 0.5 * (bl[:, :-1] + bl[:, 1:])
+    j = np.arange(a.shape[1], dtype=np.float64)
+    near = np.zeros(bl.shape[0], dtype=bool)
+    for sgn in (1.0, -1.0):
+        t = j + sgn * a / h
+        tol = 4.0 * np.spacing(np.maximum(np.abs(t), 1.0).astype(np.float32)).astype(np.float64)
+        near |= np.any(np.abs(t - np.round(t)) <= tol, axis=1)
+    return near
+
+
+def lines_off_the_plain_oracle(og, prm, I1, I2, b, z, u, out):
+    """The mixed b-step against the plain FP64 oracle (intervals decided in
+    FP64) on the FP32-rounded inputs: lines off by more than 1e-3 voxel must be
+    lines with a position within FP32 rounding of a knot; returns their count."""
+    b_def, _ = oracle.bstep(og, prm, f32(I1), f32(I2), f32(b), f32(z), f32(u))
+    pe = og.pe
+    d = np.moveaxis(np.abs(np.asarray(out) - b_def), pe, -1).reshape(-1, b.shape[pe])
+    off = np.max(d, axis=1) / og.h[pe] > 1e-3
+    near = knot_lines(og, f32(b))
+    print(f"{int(off.sum())} of {off.size} lines off the plain oracle by > 1e-3 voxel "
+          f"({int(near.sum())} lines with a position at a knot)")
+    assert np.all(near[off])
+    return int(off.sum())
+
+
 def case_data(m, pe, seed=0, max_d=0.5):
     h = tuple(1.0 / m[0] for _ in m)
     I1 = ph.random_images(m, seed + 1)
@@ -387,6 +419,7 @@ def test_bstep_mixed_segment_kernel(sac, m, pe):
         assert not capped
         outs.append(out.cpu().numpy())
         assert np.max(np.abs(outs[-1] - b_ref)) / h[pe] <= 1e-3
+        lines_off_the_plain_oracle(og, oracle.Params(alpha=0.5, rho=100.0), I1, I2, b, z, u, outs[-1])
     assert np.max(np.abs(outs[0] - outs[1])) / h[pe] <= 1e-4
 
 
@@ -410,6 +443,7 @@ def test_bstep_mixed_segment_kernel_queues_blocked_lines(sac, m, pe):
     out = out.cpu().numpy()
     assert np.max(np.abs(out - b_ref)) / h[pe] <= 1e-3
     assert oracle.max_abs_d1(og, out) <= 1 + 1e-5
+    lines_off_the_plain_oracle(og, oracle.Params(alpha=1e-3, rho=1e5), I1, I2, b, z, u, out)
 
 
 # ---------------------------------------------------------------- tensor-core z-step (mixed path)
@@ -483,6 +517,115 @@ def test_full_size_bstep_matches_the_oracle(sac):
     out, capped = sac.bstep(g, p, cu(I1, torch.float32), cu(I2, torch.float32), cu(b), cu(z), cu(u))
     assert not capped
     b_ref, _ = oracle.bstep(og, oracle.Params(alpha=50.0, rho=100.0, knot32=1), f32(I1), f32(I2), b, z, u)
-    err = np.max(np.abs(out.cpu().numpy() - b_ref)) / h[pe]
+    out = out.cpu().numpy()
+    err = np.max(np.abs(out - b_ref)) / h[pe]
     print(f"full-size mixed b-step: max |db| = {err:.3e} voxel")
     assert err <= 1e-3
+    lines_off_the_plain_oracle(og, oracle.Params(alpha=50.0, rho=100.0), I1, I2, b, z, u, out)
+
+
+@pytest.fixture(scope="module")
+def full_size():
+    """The benchmarked solve's inputs: the 256 x 256 x 80 phantom pair (5.26M
+    faces, FP32 images), alpha 50, rho 1e2, and the oracle's K = 20 ADMM
+    iterates from b = 0 with the model's intervals decided in FP64 (plain)
+    and in FP32 (knot32), on the FP32 images the GPU reads."""
+    w, d = ph.load_pair("3d_256x256x80", np.float32)
+    og = oracle.Grid(w.m, w.h, w.pe)
+    I1, I2 = d["I1"].astype(np.float64), d["I2"].astype(np.float64)
+    K = 20
+    ref = {}
+    for k32 in (0, 1):
+        op = oracle.Params(alpha=w.alpha, rho=w.rho, max_iter=K, eps_abs=0.0, eps_rel=0.0, knot32=k32)
+        ref[k32] = oracle.admm(og, op, I1, I2, np.zeros(og.face_shape))["b"]
+    return dict(w=w, d=d, og=og, I1=I1, I2=I2, K=K, ref=ref)
+
+
+def _objective(F, b):
+    return oracle.objective(F["og"], oracle.Params(alpha=F["w"].alpha), F["I1"], F["I2"], b)["J"]
+
+
+def _solve(sac, F, prec, K, eps_rel=0.0):
+    w = F["w"]
+    g = sac.grid(w.m, w.h, w.pe)
+    p = sac.params(alpha=w.alpha, rho=w.rho, max_iter=K, eps_abs=0.0, eps_rel=eps_rel, prec=prec, near_bound=1e-3)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    b = cu(np.zeros(F["og"].face_shape))
+    res = sac.admm_solve(g, p, cu(F["d"]["I1"], dt), cu(F["d"]["I2"], dt), b)
+    return res, b.cpu().numpy()
+
+
+def test_full_size_admm_mixed_matches_the_oracle(sac, full_size):
+    # K = 20 mixed ADMM iterations through sac_admm_solve against the FP64
+    # oracle that takes the model's interval decisions in FP32 (knot32) as
+    # the kernels do: the mixed arithmetic (FP32 lines, split-TF32 DCTs,
+    # FP64 reductions and near-bound re-solves) within the stated tolerances,
+    # 1e-3 voxel in b and 1e-6 relative objective.  Against the plain oracle
+    # (intervals decided in FP64) the iterate differs where a displaced
+    # position falls within FP32 rounding of a knot; the oracle itself moves
+    # by as much between its two interval rules, which is printed beside it.
+    F = full_size
+    h = F["w"].h[F["w"].pe]
+    res, bb = _solve(sac, F, "mixed", F["K"])
+    assert res["iters"] == F["K"]
+    J32, J64, Jm = _objective(F, F["ref"][1]), _objective(F, F["ref"][0]), _objective(F, bb)
+    err = np.max(np.abs(bb - F["ref"][1])) / h
+    err64 = np.max(np.abs(bb - F["ref"][0])) / h
+    own = np.max(np.abs(F["ref"][1] - F["ref"][0])) / h
+    print(f"full-size mixed ADMM, K = {F['K']}: against the oracle with FP32 interval decisions "
+          f"max |db| = {err:.3e} voxel, relative objective {abs(Jm - J32) / abs(J32):.3e}; against the plain "
+          f"oracle {err64:.3e} voxel, {abs(Jm - J64) / abs(J64):.3e}; the oracle's two interval rules differ "
+          f"by {own:.3e} voxel, {abs(J32 - J64) / abs(J64):.3e}")
+    assert err <= 1e-3
+    assert abs(Jm - J32) <= 1e-6 * abs(J32)
+
+
+def test_full_size_admm_f64_matches_the_plain_oracle(sac, full_size):
+    # the plain FP64 GPU path (the comparison path of the benchmark) on the
+    # same volume: 1e-9 relative in b against the plain oracle after K = 20
+    F = full_size
+    res, bb = _solve(sac, F, "f64", F["K"])
+    assert res["iters"] == F["K"]
+    ref = F["ref"][0]
+    assert np.linalg.norm(bb - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert rel(bb, ref) < 1e-9
+
+
+def test_full_size_converged_mixed_matches_converged_f64(sac, full_size):
+    # both precisions run to the benchmark's stopping test (relative residual
+    # 1e-4, eps_abs = 0, at most 2000 iterations); the converged mixed result
+    # against the converged plain FP64 result (which decides the model's
+    # intervals in FP64 as the oracle does, and matches it above): 1e-3 voxel
+    # in b, 1e-6 relative objective (objectives from the oracle)
+    F = full_size
+    h = F["w"].h[F["w"].pe]
+    rm, bm = _solve(sac, F, "mixed", 2000, eps_rel=1e-4)
+    rf, bf = _solve(sac, F, "f64", 2000, eps_rel=1e-4)
+    Jm, Jf = _objective(F, bm), _objective(F, bf)
+    err = np.max(np.abs(bm - bf)) / h
+    print(f"converged at relative residual 1e-4: mixed {rm['iters']} iterations, FP64 {rf['iters']}; "
+          f"max |db| = {err:.3e} voxel, relative objective {abs(Jm - Jf) / abs(Jf):.3e}")
+    assert rm["iters"] < 2000 and rf["iters"] < 2000
+    assert err <= 1e-3
+    assert abs(Jm - Jf) <= 1e-6 * abs(Jf)
+
+
+# ---------------------------------------------------------------- FP64 parity on the configurations' grids
+
+@pytest.mark.parametrize("name,K", [("2d_128", 50), ("3d_128x128x64", 20)])
+def test_admm_f64_on_the_configurations(sac, name, K):
+    # the 128 x 128 slice (alpha 50, K = 50) and the 128 x 128 x 64 volume
+    # (alpha 100, K = 20), plain FP64 ADMM from b = 0: 1e-9 relative in b
+    w, d = ph.load_pair(name, np.float64)
+    og = oracle.Grid(w.m, w.h, w.pe)
+    op = oracle.Params(alpha=w.alpha, rho=w.rho, max_iter=K, eps_abs=0.0, eps_rel=0.0)
+    ref = oracle.admm(og, op, d["I1"], d["I2"], np.zeros(og.face_shape), want_hist=True)
+    g = sac.grid(w.m, w.h, w.pe)
+    p = sac.params(alpha=w.alpha, rho=w.rho, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec="f64")
+    b = cu(np.zeros(og.face_shape))
+    res = sac.admm_solve(g, p, cu(d["I1"]), cu(d["I2"]), b, want_hist=True)
+    assert res["iters"] == K
+    bb = b.cpu().numpy()
+    assert np.linalg.norm(bb - ref["b"]) <= 1e-9 * np.linalg.norm(ref["b"])
+    assert rel(bb, ref["b"]) < 1e-9
+    np.testing.assert_allclose(res["hist"][:, :4], ref["hist"][:, :4], rtol=1e-7)

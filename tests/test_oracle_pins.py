@@ -501,9 +501,75 @@ def test_admm_dual_equals_regulariser_gradient_after_every_iteration():
                                    atol=1e-11 * np.abs(prm.alpha * lap).max())
 
 
+def _d1t_d1(g, b):
+    """D1^T D1 b from differences along the phase-encoding axis (numpy)."""
+    hpe = g.h[g.pe]
+    w = np.diff(b, axis=g.pe) / hpe
+    pad = [(0, 0)] * b.ndim
+    pad[g.pe] = (1, 1)
+    return -np.diff(np.pad(w, pad), axis=g.pe) / hpe
+
+
+def test_admm_stopping_quantities_on_a_quadratic_problem():
+    # Eq. admmStop pinned by the optimality of the b-step.  With I1 = I2 = 0
+    # the distance vanishes, the b-subproblem alpha/2 h^d |D1 b|^2 + rho/2
+    # h^d |b - z^k + u^k|^2 is quadratic (one Gauss-Newton step solves it) and
+    # its constraint stays inactive, so
+    #   alpha h^d D1^T D1 b^{k+1} + rho h^d (b^{k+1} - z^k + u^k) = 0,
+    # and with u^{k+1} = u^k + b^{k+1} - z^{k+1}:
+    #   |alpha h^d D1^T D1 b^{k+1} + rho h^d u^{k+1}| = rho h^d |z^{k+1} - z^k|,
+    # the dual residual; the primal residual is |b^{k+1} - z^{k+1}|, and the
+    # two tolerances are sqrt(n) eps_abs + eps_rel max(|b|, |z|) and
+    # sqrt(n) eps_abs + eps_rel |rho h^d u| (Boyd et al. (3.12), scaled form,
+    # the paper's h^d-weighted inner product)
+    m, pe = (8, 12, 6), 1
+    g = grid_of(m, pe)
+    hd = float(np.prod(g.h))
+    rng = np.random.default_rng(21)
+    z0 = 0.02 * g.h[pe] * rng.normal(size=g.face_shape)
+    u0 = 0.02 * g.h[pe] * rng.normal(size=g.face_shape)
+    Z = np.zeros(m)
+    n = z0.size
+    prev_z = z0
+    for k in range(1, 6):
+        prm = oracle.Params(alpha=3.0, rho=40.0, max_iter=k, eps_abs=1e-14, eps_rel=1e-12)
+        r = oracle.admm(g, prm, Z, Z, np.zeros(g.face_shape), z0=z0, u0=u0, want_hist=True)
+        assert r["iters"] == k
+        b, z, u = r["b"], r["z"], r["u"]
+        assert oracle.max_abs_d1(g, b) < 0.5
+        rp, rd, ep, ed = r["hist"][-1, :4]
+        opt = prm.alpha * hd * _d1t_d1(g, b) + prm.rho * hd * u
+        assert rd == pytest.approx(np.linalg.norm(opt), rel=1e-9)
+        assert rd == pytest.approx(prm.rho * hd * np.linalg.norm(z - prev_z), rel=1e-9)
+        assert rp == pytest.approx(np.linalg.norm(b - z), rel=1e-12)
+        assert ep == pytest.approx(math.sqrt(n) * 1e-14 + 1e-12 * max(np.linalg.norm(b), np.linalg.norm(z)),
+                                   rel=1e-12)
+        assert ed == pytest.approx(math.sqrt(n) * 1e-14 + 1e-12 * np.linalg.norm(prm.rho * hd * u), rel=1e-12)
+        prev_z = z
+
+
+def test_admm_primal_residual_vanishes_without_regulariser():
+    # alpha = 0: the z-step returns z = b + u (the spectral scale is 1), so
+    # u^{k+1} = 0 and r_pri = |b^1 - z^1| = |u^0| after the first iteration,
+    # then r_pri = 0 (to rounding) from the second on
+    m, pe = (8, 10, 6), 1
+    w = ph.small_workload(m, pe, seed=7)
+    d = ph.make_pair(w)
+    g = oracle.Grid(d["m"], d["h"], d["pe"])
+    u0 = 0.05 * g.h[pe] * np.random.default_rng(3).normal(size=g.face_shape)
+    prm = oracle.Params(alpha=0.0, rho=30.0, max_iter=4, eps_abs=0.0, eps_rel=0.0)
+    r = oracle.admm(g, prm, d["I1"], d["I2"], np.zeros(g.face_shape), u0=u0, want_hist=True)
+    hs = r["hist"]
+    assert hs[0, 0] == pytest.approx(np.linalg.norm(u0), rel=1e-12)
+    scale = np.linalg.norm(r["b"])
+    assert np.all(hs[1:, 0] <= 1e-13 * scale)
+    assert np.max(np.abs(r["u"])) <= 1e-14 * np.max(np.abs(r["b"]))
+
+
 def _next_rho(prm, rho, rp, rd):
-    # the adaptive rule as stated in the design notes (Boyd et al.'s varying
-    # penalty, optionally bounded below)
+    # Boyd et al.'s varying penalty, optionally bounded below: rho times tau
+    # when the primal residual exceeds mu times the dual one, divided by tau
+    # in the opposite case (not below rho_min in the bounded form)
     if rp > prm.rho_mu * rd:
         return rho * prm.rho_tau
     if rd > prm.rho_mu * rp:
