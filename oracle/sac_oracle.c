@@ -98,9 +98,10 @@ static long line_cell0(const grid_t* g, long l) {
     return o * g->mpe * g->n_inner + n;
 }
 
+/* nthreads > 0: that many OpenMP threads; 0: all the host's processors */
 static void set_threads(const ref_params* p) {
 #ifdef _OPENMP
-    if (p && p->nthreads > 0) omp_set_num_threads(p->nthreads);
+    if (p) omp_set_num_threads(p->nthreads > 0 ? p->nthreads : omp_get_num_procs());
 #else
     (void)p;
 #endif

@@ -106,16 +106,28 @@ __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs
                                                     const long long* __restrict__ prefix,
                                                     const double* __restrict__ b, double* __restrict__ part) {
     __shared__ double red[32];
+    __shared__ long long sStart[2];
     const long long t = blockIdx.x;
     if (t >= prefix[njobs]) return;
     const int jid = find_job(prefix, njobs, t);
     const Job& J = jobs[jid];
-    const long long f = (t - prefix[jid]) * 256 + threadIdx.x;
+    const long long f0 = (t - prefix[jid]) * 256, f = f0 + threadIdx.x;
+    const long long per_outer = (long long)J.mpe * J.n_inner;
+    if (threadIdx.x == 0) {
+        // the block's first cell as (outer index, offset): one division per block
+        const long long o = f0 / per_outer;
+        sStart[0] = o;
+        sStart[1] = f0 - o * per_outer;
+    }
+    __syncthreads();
     double mx = 0.0;
-    const long long ncell_rows = (long long)J.n_outer * J.mpe * J.n_inner;   // one entry per cell
+    const long long ncell_rows = (long long)J.n_outer * per_outer;   // one entry per cell
     if (f < ncell_rows) {
-        const long long per_outer = (long long)J.mpe * J.n_inner;
-        const long long o = f / per_outer, rem = f - o * per_outer;          // one 64-bit division per thread
+        long long o = sStart[0], rem = sStart[1] + threadIdx.x;
+        while (rem >= per_outer) {   // (at most 256 / per_outer + 1 steps)
+            rem -= per_outer;
+            ++o;
+        }
         const long long a = o * (J.mpe + 1) * (long long)J.n_inner + rem;   // face (o, i, n)
         const double d = fabs(b[a + J.n_inner] - b[a]);
         mx = (d == d) ? d : INFINITY;

@@ -108,6 +108,79 @@ def small_workload(m, pe=1, seed=0, peak_px=2.0, max_d=0.5, sigma=0.0, n_blobs=4
 # analytic phantom and field
 # --------------------------------------------------------------------------
 
+class _Numpy:
+    """Array operations of the phantom evaluation on numpy arrays."""
+    @staticmethod
+    def asarray(a, like):
+        return np.asarray(a, dtype=np.float64)
+    exp = staticmethod(np.exp)
+    minimum = staticmethod(np.minimum)
+    where = staticmethod(np.where)
+
+    @staticmethod
+    def clip(a, lo, hi):
+        return np.clip(a, lo, hi)
+
+    @staticmethod
+    def zeros(shape, like):
+        return np.zeros(shape)
+
+    @staticmethod
+    def sum_last(a):
+        return np.sum(a, axis=-1)
+
+    @staticmethod
+    def max_abs(a):
+        return float(np.max(np.abs(a)))
+
+
+class _Torch:
+    """The same operations on torch tensors (float64, any device): the bench
+    generates its many large phantoms on the GPU; the seeded parameters and
+    the noise still come from numpy, so the pair is the same up to the
+    rounding of exp."""
+    @staticmethod
+    def asarray(a, like):
+        import torch
+        return torch.as_tensor(np.asarray(a, dtype=np.float64), device=like.device)
+
+    @staticmethod
+    def exp(a):
+        import torch
+        return torch.exp(a)
+
+    @staticmethod
+    def minimum(a, b):
+        import torch
+        return torch.minimum(a, b)
+
+    @staticmethod
+    def where(c, a, b):
+        import torch
+        return torch.where(c, a, b)
+
+    @staticmethod
+    def clip(a, lo, hi):
+        return a.clamp(lo, hi)
+
+    @staticmethod
+    def zeros(shape, like):
+        import torch
+        return torch.zeros(shape, dtype=torch.float64, device=like.device)
+
+    @staticmethod
+    def sum_last(a):
+        return a.sum(dim=-1)
+
+    @staticmethod
+    def max_abs(a):
+        return float(a.abs().max().item())
+
+
+def _ns(X):
+    return _Numpy if isinstance(X, np.ndarray) else _Torch
+
+
 def _extent(w: Workload):
     return np.array([mm * hh for mm, hh in zip(w.m, w.h)])
 
@@ -136,17 +209,18 @@ class _Phantom:
         self.bias = rng.uniform(-0.15, 0.15, size=(nd, 2)) if w.bias else None
 
     def __call__(self, X):
-        """X: (..., nd) points in domain coordinates."""
-        val = np.zeros(X.shape[:-1])
+        """X: (..., nd) points in domain coordinates (numpy or torch)."""
+        xp = _ns(X)
+        val = xp.zeros(X.shape[:-1], X)
         for c, R, s, a in zip(self.c, self.R, self.s, self.a):
-            Y = (X - c) @ R
-            val += a * np.exp(-0.5 * np.sum((Y / s) ** 2, axis=-1))
+            Y = (X - xp.asarray(c, X)) @ xp.asarray(R, X)
+            val += a * xp.exp(-0.5 * xp.sum_last((Y / xp.asarray(s, X)) ** 2))
         if self.bias is not None:
-            t = X / self.ext - 0.5
-            val *= 1.0 + np.sum(self.bias[:, 0] * t + self.bias[:, 1] * t * t, axis=-1)
+            t = X / xp.asarray(self.ext, X) - 0.5
+            val *= 1.0 + xp.sum_last(xp.asarray(self.bias[:, 0], X) * t + xp.asarray(self.bias[:, 1], X) * t * t)
         for a in range(self.nd):
-            dist = np.minimum(X[..., a], self.ext[a] - X[..., a]) / self.h[a]
-            s = np.clip((dist - 2.0) / 4.0, 0.0, 1.0)
+            dist = xp.minimum(X[..., a], self.ext[a] - X[..., a]) / self.h[a]
+            s = xp.clip((dist - 2.0) / 4.0, 0.0, 1.0)
             val *= s * s * (3.0 - 2.0 * s)
         return val
 
@@ -169,99 +243,115 @@ class _Field:
     def cross_factors(self, X):
         """Per bump, the factor of the Gaussian that does not depend on the PE
         coordinate (fixed along a PE line)."""
+        xp = _ns(X)
         out = []
         for c, w, s in zip(self.c, self.w, self.s):
-            q = np.zeros(X.shape[:-1])
+            q = xp.zeros(X.shape[:-1], X)
             for a in range(X.shape[-1]):
                 if a != self.pe:
                     q += ((X[..., a] - c[a]) / w) ** 2
-            out.append(s * np.exp(-0.5 * q))
+            out.append(s * xp.exp(-0.5 * q))
         return out
 
     def along_pe(self, xpe, fac):
-        v = np.zeros(xpe.shape)
-        dv = np.zeros(xpe.shape)
+        xp = _ns(xpe)
+        v = xp.zeros(xpe.shape, xpe)
+        dv = xp.zeros(xpe.shape, xpe)
         for c, w, f in zip(self.c, self.w, fac):
             t = (xpe - c[self.pe]) / w
-            e = f * np.exp(-0.5 * t * t)
+            e = f * xp.exp(-0.5 * t * t)
             v += e
             dv -= e * t / w
         return self.scale * v, self.scale * dv
 
 
-def _grid_points(w: Workload, faces: bool):
+def _grid_points(w: Workload, faces: bool, device=None):
     axes = []
     for a, (mm, hh) in enumerate(zip(w.m, w.h)):
         if faces and a == w.pe:
             axes.append(np.arange(mm + 1) * hh)
         else:
             axes.append((np.arange(mm) + 0.5) * hh)
+    if device is not None:
+        import torch
+        G = torch.meshgrid(*[torch.as_tensor(x, dtype=torch.float64, device=device) for x in axes], indexing="ij")
+        return torch.stack(G, dim=-1)
     G = np.meshgrid(*axes, indexing="ij")
     return np.stack(G, axis=-1)
+
+
+def _np(a):
+    return a if isinstance(a, np.ndarray) else a.cpu().numpy()
 
 
 def _invert(field: _Field, X, sign, bmax):
     """Solve x + sign*b(x) = y along the PE coordinate for every point of X
     (X holds y in the PE slot): safeguarded Newton inside the bracket
     [y - bmax, y + bmax]."""
+    xp = _ns(X)
     pe = field.pe
-    y = X[..., pe].copy()
+    y = X[..., pe] + 0.0
     lo, hi = y - bmax - 1e-12, y + bmax + 1e-12
-    Z = X.copy()
-    x = y.copy()
+    Z = X + 0.0
+    x = y + 0.0
     fac = field.cross_factors(X)
-    tol = 4e-16 * (1.0 + np.max(np.abs(y)))
+    tol = 4e-16 * (1.0 + xp.max_abs(y))
     for _ in range(60):
         b, db = field.along_pe(x, fac)
         F = x + sign * b - y
-        if np.max(np.abs(F)) <= tol:
+        if xp.max_abs(F) <= tol:
             break
-        lo = np.where(F < 0, x, lo)
-        hi = np.where(F >= 0, x, hi)
+        lo = xp.where(F < 0, x, lo)
+        hi = xp.where(F >= 0, x, hi)
         xn = x - F / (1.0 + sign * db)
         bad = ~((xn >= lo) & (xn <= hi))
-        x = np.where(bad, 0.5 * (lo + hi), xn)
+        x = xp.where(bad, 0.5 * (lo + hi), xn)
     Z[..., pe] = x
     return Z
 
 
-def make_pair(w: Workload, dtype=np.float64, chunk: int = 1 << 20):
+def make_pair(w: Workload, dtype=np.float64, chunk: int = 1 << 20, device=None):
     """Returns dict(I1, I2, b_true, h, pe, m, peak_px, max_d, sigma) for workload w.
 
     I1 = I_v (displaced by +b), I2 = I_-v (displaced by -b); b_true on faces in
-    physical units.  Everything is a deterministic function of w.seed."""
+    physical units.  Everything is a deterministic function of w.seed.  With
+    a torch device the forward model is evaluated there (float64; numpy
+    arrays are returned either way)."""
     rng = np.random.default_rng(w.seed)
     phantom = _Phantom(w, rng)
     fld = _Field(w, rng)
     # scale the field: peak |b| = peak_px * h_pe, then shrink until max |d_v b| <= max_d
-    Xf = _grid_points(w, faces=True)
+    Xf = _grid_points(w, faces=True, device=device)
     v, dv = fld.val_and_dpe(Xf)
     hpe = w.h[w.pe]
-    fld.scale = w.peak_px * hpe / max(np.max(np.abs(v)), 1e-300)
+    xp = _ns(v)
+    fld.scale = w.peak_px * hpe / max(xp.max_abs(v), 1e-300)
     v, dv = fld.val_and_dpe(Xf)
-    Xc = _grid_points(w, faces=False)
+    Xc = _grid_points(w, faces=False, device=device)
     _, dvc = fld.val_and_dpe(Xc)
-    dmax = max(np.max(np.abs(dv)), np.max(np.abs(dvc)), np.max(np.abs(np.diff(v, axis=w.pe))) / hpe)
+    dmax = max(xp.max_abs(dv), xp.max_abs(dvc), float(np.max(np.abs(np.diff(_np(v), axis=w.pe)))) / hpe)
     if dmax > w.max_d:
         fld.scale *= w.max_d / dmax
-    b_true = fld.val_and_dpe(Xf)[0]
+    b_true = _np(fld.val_and_dpe(Xf)[0])
     bmax = float(np.max(np.abs(b_true))) * 1.001 + 1e-9
     # exact forward model at the cell centres, in chunks
     flat = Xc.reshape(-1, Xc.shape[-1])
     I1 = np.empty(flat.shape[0])
     I2 = np.empty(flat.shape[0])
+    if device is not None:
+        chunk = max(chunk, 1 << 23)
     for s in range(0, flat.shape[0], chunk):
         X = flat[s:s + chunk]
         for sign, out in ((1.0, I1), (-1.0, I2)):
             Z = _invert(fld, X, sign, bmax)
             _, db = fld.val_and_dpe(Z)
-            out[s:s + chunk] = phantom(Z) / (1.0 + sign * db)
+            out[s:s + chunk] = _np(phantom(Z) / (1.0 + sign * db))
     I1 = I1.reshape(w.m)
     I2 = I2.reshape(w.m)
     nrng = np.random.default_rng(w.seed + 1_000_003)
     sigma = w.sigma
     if w.snr is not None:
-        fg = phantom(Xc)
+        fg = _np(phantom(Xc))
         mask = fg > 0.1 * fg.max()
         snr = nrng.uniform(*w.snr)
         sigma = float(fg[mask].mean() / snr)
