@@ -353,6 +353,10 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     if ((long long)blockIdx.x < total) stage_tile(jobs, njobs, prefix, blockIdx.x, Rg, Rg.b(0), bar);
     int it = 0;
     uint32_t nwait = 0;   // TMA-staged tiles consumed (the parity of the next phase)
+    // the job's FP32 parameters, converted from its FP64 fields once per job
+    // and CTA (FP64 arithmetic, the reciprocal above all, is slow on this GPU)
+    int cjid = -1;
+    float inv_h = 0.f, ih2 = 0.f, alpha = 0.f, rho = 0.f, us = 0.f;
     for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
     const int jid = find_job(prefix, njobs, t);
     const Job& J = jobs[jid];
@@ -391,8 +395,14 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
     const float* sU = Rg.u;
     const long long L = L0 + lane;
     const bool valid = L < nlines;   // rows of lanes past the last line are not staged
-    const float inv_h = (float)(1.0 / J.hpe), ih2 = inv_h * inv_h;   // (1/h rounded once, as in the warp kernels)
-    const float alpha = (float)J.alpha, rho = (float)J.rho, us = (float)J.uscale;
+    if (jid != cjid) {
+        cjid = jid;
+        inv_h = (float)(1.0 / J.hpe);   // (1/h rounded once, as in the warp kernels)
+        ih2 = inv_h * inv_h;
+        alpha = (float)J.alpha;
+        rho = (float)J.rho;
+        us = (float)J.uscale;
+    }
     const bool on = g < G && valid;
     const int s = g * S;
     const float* rI1 = sI1 + lane;

@@ -105,7 +105,6 @@ __global__ void __launch_bounds__(256) k_hessvec(const Job* __restrict__ jobs, i
 __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs, int njobs,
                                                     const long long* __restrict__ prefix,
                                                     const double* __restrict__ b, double* __restrict__ part) {
-    __shared__ double red[32];
     __shared__ long long sStart[2];
     const long long t = blockIdx.x;
     if (t >= prefix[njobs]) return;
@@ -120,7 +119,10 @@ __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs
         sStart[1] = f0 - o * per_outer;
     }
     __syncthreads();
-    double mx = 0.0;
+    // |d| as the bits of a non-negative double: their unsigned order is the
+    // numeric order, and a NaN sorts above +inf; the maximum runs on the
+    // integer units (FP64 comparisons and shuffles are slow on this GPU)
+    unsigned long long mx = 0ull;
     const long long ncell_rows = (long long)J.n_outer * per_outer;   // one entry per cell
     if (f < ncell_rows) {
         long long o = sStart[0], rem = sStart[1] + threadIdx.x;
@@ -129,17 +131,28 @@ __global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs
             ++o;
         }
         const long long a = o * (J.mpe + 1) * (long long)J.n_inner + rem;   // face (o, i, n)
-        const double d = fabs(b[a + J.n_inner] - b[a]);
-        mx = (d == d) ? d : INFINITY;
+        mx = (unsigned long long)__double_as_longlong(b[a + J.n_inner] - b[a]) & 0x7fffffffffffffffull;
     }
-    mx = warp_max(mx);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, mx, d);
+        mx = o > mx ? o : mx;
+    }
+    __shared__ unsigned long long redu[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = mx;
+    if (lane == 0) redu[wid] = mx;
     __syncthreads();
     if (wid == 0) {
-        mx = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-        mx = warp_max(mx);
-        if (lane == 0) part[blockIdx.x] = mx / J.hpe;
+        mx = (lane < (int)(blockDim.x >> 5)) ? redu[lane] : 0ull;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, mx, d);
+            mx = o > mx ? o : mx;
+        }
+        if (lane == 0) {
+            const double v = __longlong_as_double((long long)mx);
+            part[blockIdx.x] = (v == v) ? v / J.hpe : INFINITY;
+        }
     }
 }
 
@@ -150,25 +163,38 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
     __shared__ double red[32 * 8];
     const bool is_max = ncomp < 0;
     const int nc = is_max ? 1 : ncomp;
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
-        for (int c = 0; c < nc; ++c) {
-            const double v = part[(long long)p * nc + c];
-            acc[c] = is_max ? fmax(acc[c], v) : acc[c] + v;
-        }
     if (is_max) {
-        double m = warp_max(acc[0]);
+        // non-negative values (or +inf, NaN): the maximum of their bits as
+        // unsigned integers, on the integer units (a NaN sorts above +inf)
+        unsigned long long m = 0ull;
+        for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+            const unsigned long long v = (unsigned long long)__double_as_longlong(part[p]) & 0x7fffffffffffffffull;
+            m = v > m ? v : m;
+        }
+        unsigned long long* redu = reinterpret_cast<unsigned long long*>(red);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, m, d);
+            m = o > m ? o : m;
+        }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) red[wid] = m;
+        if (lane == 0) redu[wid] = m;
         __syncthreads();
         if (wid == 0) {
-            m = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-            m = warp_max(m);
-            if (lane == 0) out[0] = m;
+            m = (lane < (int)(blockDim.x >> 5)) ? redu[lane] : 0ull;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(kFull, m, d);
+                m = o > m ? o : m;
+            }
+            if (lane == 0) out[0] = __longlong_as_double((long long)m);
         }
         return;
     }
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+        for (int c = 0; c < nc; ++c) acc[c] += part[(long long)p * nc + c];
     block_sum<8>(acc, red);
     if (threadIdx.x == 0)
         for (int c = 0; c < nc; ++c) out[c] = acc[c];
