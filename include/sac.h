@@ -349,6 +349,11 @@ long long sac_launch_count(void);
  * device rejects the update. */
 int sac_set_wait_limit(int which, long long tests);
 
+/* The cudaError_t code behind the most recent SAC_ECUDA returned by this
+   library (0 if none so far): which CUDA call failed is not recorded, only
+   its code.  No paper counterpart. */
+int sac_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

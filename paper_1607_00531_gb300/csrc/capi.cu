@@ -98,11 +98,16 @@ struct PhaseScope {
     }
 };
 
+// the CUDA error code behind the most recent SAC_ECUDA of this library
+static std::atomic<int> g_last_cuda_error{0};
+void note_cuda_error(int code) { g_last_cuda_error.store(code); }
+
 #define SAC_CUDA(x)                                  \
     do {                                             \
         cudaError_t e_ = (x);                        \
         if (e_ != cudaSuccess) {                     \
             cudaGetLastError();                      \
+            g_last_cuda_error = (int)e_;             \
             return SAC_ECUDA;                        \
         }                                            \
     } while (0)
@@ -615,6 +620,8 @@ int sac_profile_read(double* ms, long long* launches, int reset) {
 }
 
 long long sac_launch_count(void) { return g_launches.load(); }
+
+int sac_last_cuda_error(void) { return g_last_cuda_error.load(); }
 
 int sac_set_wait_limit(int which, long long tests) {
     if ((which & ~3) != 0) return SAC_EINVAL;

@@ -24,6 +24,7 @@ namespace sac {
         cudaError_t e_ = (x);                        \
         if (e_ != cudaSuccess) {                     \
             cudaGetLastError();                      \
+            note_cuda_error((int)e_);                \
             return SAC_ECUDA;                        \
         }                                            \
     } while (0)
@@ -268,6 +269,8 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         }
         ngeo_ = (int)rep.size();
         long long* zp = (long long*)take(sizeof(long long) * (nj + 1) * 4 * ngeo_);
+        // every table above lies inside what table_bytes reserved
+        if (off > table_bytes(in, p)) return SAC_EINVAL;
         std::vector<long long> hz((nj + 1) * 4 * ngeo_, 0);
         zpref_.assign(4 * ngeo_, nullptr);
         ztiles_.assign(4 * ngeo_, 0);

@@ -29,6 +29,8 @@ inline cudaError_t allow_max_dyn_smem(const void* k) {
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
+// records the code behind a SAC_ECUDA (sac_last_cuda_error)
+void note_cuda_error(int code);
 cudaError_t prepare_bstep_f64();
 cudaError_t prepare_bstep_f32();
 cudaError_t prepare_bstep_mixed();

@@ -41,7 +41,13 @@ class SacParams(ctypes.Structure):
 
 class SacError(RuntimeError):
     def __init__(self, name, status):
-        super().__init__(f"{name} failed with status {status} ({status_string(status)})")
+        extra = ""
+        if status == SAC_ECUDA:
+            try:
+                extra = f", cudaError {int(lib().sac_last_cuda_error())}"
+            except (AttributeError, OSError):
+                pass
+        super().__init__(f"{name} failed with status {status} ({status_string(status)}{extra})")
         self.status = status
 
 
@@ -98,6 +104,7 @@ def lib():
             "sac_profile_read": (ctypes.c_int, [dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
             "sac_launch_count": (ctypes.c_longlong, []),
             "sac_set_wait_limit": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
+            "sac_last_cuda_error": (ctypes.c_int, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
