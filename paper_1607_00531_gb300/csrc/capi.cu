@@ -501,8 +501,10 @@ static int max_abs_d1_dev(Plan& P, const double* b, double* out, cudaStream_t st
     return SAC_OK;
 }
 
-// z-step passes on the plan's job (arrays already bound in the job)
-static int zstep_passes(Plan& P, cudaStream_t st) {
+// z-step passes on the plan's job (arrays already bound in the job); with
+// norms, the five residual sums into d_out + 16 (else left unreduced: the
+// ADMM driver needs them only at its stopping tests)
+static int zstep_passes(Plan& P, cudaStream_t st, bool norms = true) {
     const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
     for (int q = 0; q < 4; ++q) {
         if (P.use_tc && P.fuse12 && q == 2) continue;   // done with pass 1
@@ -531,8 +533,8 @@ static int zstep_passes(Plan& P, cudaStream_t st) {
         AdmmCheck none;
         memset(&none, 0, sizeof(none));
         SAC_CUDA(launch_admm_update(P.d_job, 1, P.d_pref_admm, P.admm_blocks, P.d_part, none, st));
-        SAC_CUDA(launch_reduce(P.d_part, (int)P.admm_blocks, 5, P.d_out + 16, st));
-    } else {
+        if (norms) SAC_CUDA(launch_reduce(P.d_part, (int)P.admm_blocks, 5, P.d_out + 16, st));
+    } else if (norms) {
         SAC_CUDA(launch_reduce(P.d_part, (int)P.pass_tiles[3], 5, P.d_out + 16, st));
     }
     return SAC_OK;
@@ -759,6 +761,25 @@ int sac_zstep(const sac_grid* g, const sac_params* p, const double* b, const dou
 
 }  // extern "C"
 
+// One ADMM iteration captured as a CUDA graph and replayed between the
+// stopping tests, on a stream of the library's own (the caller's stream may
+// be the legacy default stream, which cannot be captured) joined to the
+// caller's stream with an event; released (after its work) on every return.
+struct IterGraph {
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~IterGraph() {
+        if (gs) cudaStreamSynchronize(gs);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (gs) cudaStreamDestroy(gs);
+        cudaGetLastError();
+    }
+};
+
 // ADMM on one volume starting from rho0 (the parameters' rho replaced); on
 // return *rho_out (may be null) holds rho after the last iteration (the
 // adaptive rule applied to every iteration that did not stop)
@@ -799,13 +820,37 @@ static int admm_solve_impl(const sac_grid* g, const sac_params* p0, double rho0,
     int k = 0, conv = 0;
     double rp = 0.0, rd = 0.0, rho = p->rho, us_dev = 1.0;
     char* dj = (char*)P.d_job;
+    // iterations between stopping tests: one captured iteration replayed
+    // (fewer launch gaps); the tests' iterations and profiled runs launch
+    // directly (the residual sums and the phase events)
+    IterGraph IG;
+    cudaStream_t ist = st;
+    if (every >= 2 && p->max_iter >= 4 && !profiling_on()) {
+        SAC_CUDA(cudaStreamCreateWithFlags(&IG.gs, cudaStreamNonBlocking));
+        SAC_CUDA(cudaEventCreateWithFlags(&IG.ev, cudaEventDisableTiming));
+        SAC_CUDA(cudaEventRecord(IG.ev, st));
+        SAC_CUDA(cudaStreamWaitEvent(IG.gs, IG.ev, 0));
+        SAC_CUDA(cudaStreamBeginCapture(IG.gs, cudaStreamCaptureModeThreadLocal));
+        int cs = bstep_dev(P, p, IG.gs);
+        if (cs == SAC_OK) cs = zstep_passes(P, IG.gs, false);
+        const cudaError_t ce = cudaStreamEndCapture(IG.gs, &IG.graph);
+        if (cs != SAC_OK) return cs;
+        SAC_CUDA(ce);
+        SAC_CUDA(cudaGraphInstantiate(&IG.exec, IG.graph, 0));
+        ist = IG.gs;
+    }
     for (k = 0; k < p->max_iter;) {
-        SAC_TRY(bstep_dev(P, p, st));
-        SAC_TRY(zstep_passes(P, st));
+        const bool check = ((k + 1) % every == 0) || (k + 1 == p->max_iter);
+        if (!check && IG.exec) {
+            SAC_CUDA(cudaGraphLaunch(IG.exec, ist));
+        } else {
+            SAC_TRY(bstep_dev(P, p, ist));
+            SAC_TRY(zstep_passes(P, ist, check));
+        }
         ++k;
-        if (k % every == 0 || k == p->max_iter) {
+        if (check) {
             double s[5];
-            SAC_TRY(read_back(s, P.d_out + 16, sizeof(s), st));
+            SAC_TRY(read_back(s, P.d_out + 16, sizeof(s), ist));
             // the batched engine's arithmetic (admm_norms), so that a volume
             // stops and adapts rho alike alone and in a batch
             const AdmmNorms nr = admm_norms(s, rho, P.G.hd, nf, p->eps_abs, p->eps_rel);
@@ -824,16 +869,21 @@ static int admm_solve_impl(const sac_grid* g, const sac_params* p0, double rho0,
                 const double rn = adapt_rho_next(p->adapt_rho, rho, rp, rd, p->rho_min, p->rho_tau, p->rho_mu);
                 const double us = rho / rn;
                 if (us != us_dev) {
-                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, uscale), &us, sizeof(double), cudaMemcpyHostToDevice, st));
+                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, uscale), &us, sizeof(double), cudaMemcpyHostToDevice, ist));
                     us_dev = us;
                 }
                 if (rn != rho) {
                     rho = rn;
-                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, rho), &rn, sizeof(double), cudaMemcpyHostToDevice, st));
-                    SAC_CUDA(launch_rebuild_scale(P.d_job, st));
+                    SAC_CUDA(cudaMemcpyAsync(dj + offsetof(Job, rho), &rn, sizeof(double), cudaMemcpyHostToDevice, ist));
+                    SAC_CUDA(launch_rebuild_scale(P.d_job, ist));
                 }
             }
         }
+    }
+    if (IG.gs) {
+        // the caller's stream continues after the iterations
+        SAC_CUDA(cudaEventRecord(IG.ev, IG.gs));
+        SAC_CUDA(cudaStreamWaitEvent(st, IG.ev, 0));
     }
     if (mixed) {
         SAC_CUDA(launch_cast_back(nf, bf, b, st));

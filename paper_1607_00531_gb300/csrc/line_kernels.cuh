@@ -469,6 +469,7 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
         // rows by off-diagonals and row sums (warp_tridiag_solve_rs): the
         // alpha h^-2 D1^T D1 part has zero row sums, so
         // sum_i = rho + Ju_{i-1} (Jd_{i-1} + Ju_{i-1}) + Jd_i (Jd_i + Ju_i)
+        // (FP64: sg holds the diagonal itself, the plain elimination below)
         T aa[K], sg[K], cc[K], xh[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -477,7 +478,8 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
                 T Jup = k ? Ju[k - 1] : Ju_p, rup = k ? r[k - 1] : r_p, dup = k ? dc[k - 1] : d_p;
                 T pup = k ? p2[k - 1] : p2_p;
                 if (i == 0) { Jup = T(0); rup = T(0); dup = T(0); pup = T(0); }
-                sg[k] = rho + Jup * pup + Jd[k] * p2[k];
+                if constexpr (sizeof(T) == 4) sg[k] = rho + Jup * pup + Jd[k] * p2[k];
+                else sg[k] = Jup * Jup + Jd[k] * Jd[k] + alpha * T((i > 0) + (i < m)) * ih2 + rho;
                 cc[k] = (i < m) ? (Jd[k] * Ju[k] - alpha * ih2) : T(0);
                 xh[k] = -(Jup * rup + Jd[k] * r[k] + alpha * (dup - dc[k]) * inv_h + rho * (bv[k] + zu[k]));
             } else {
@@ -487,7 +489,8 @@ __device__ __forceinline__ bool bstep_line_fast(const Job& J, int n_sqp, double 
         T cprev = from_prev(cc[K - 1]);
 #pragma unroll
         for (int k = 0; k < K; ++k) aa[k] = k ? cc[k - 1] : cprev;
-        warp_tridiag_solve_rs<T, K>(aa, cc, sg, xh);
+        if constexpr (sizeof(T) == 4) warp_tridiag_solve_rs<T, K>(aa, cc, sg, xh);
+        else warp_tridiag_solve<T, K>(aa, sg, cc, xh);   // FP64 holds the row sums well enough
         // ratio test of the full step from x = 0 (line_qp's first pass)
         T sn = from_next(xh[0]);
         bool blocked = false;
