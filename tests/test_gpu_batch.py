@@ -116,3 +116,49 @@ def test_batch_stops_each_volume_on_its_own_residuals(sac):
         d = vols[grids.index(g)]
         sac.admm_solve(g, q, cu(d["I1"], torch.float32), cu(d["I2"], torch.float32), b)
         assert (b - bb).abs().max().item() <= 1e-12 * max(b.abs().max().item(), 1e-30)
+
+
+# ---------------------------------------------------------------- the 64-pair DTI-like batch
+
+@pytest.fixture(scope="module")
+def dti_batch():
+    """The 64 pairs of 96 x 96 x 60 (independent seeded fields of 2-6 px, SNR
+    10-40) of the batched workload, generated on the GPU."""
+    ws = ph.batch_workloads(64)
+    pairs = [ph.make_pair(w, dtype=np.float32, device="cuda") for w in ws]
+    return ws, pairs
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_dti_batch_of_64_matches_the_oracle_on_sampled_pairs(sac, dti_batch, prec):
+    # all 64 pairs in one engine (one launch per phase over all lines and
+    # slabs, CUDA-graph replay: the launch configuration the bench times),
+    # K = 8 iterations; pairs 0, 37 and 63 against the oracle run alone:
+    # FP64 to 1e-9 relative in b; mixed to 1e-3 voxel against the oracle
+    # with the FP32 interval decisions of the kernels (knot32)
+    ws, pairs = dti_batch
+    K = 8
+    w0 = ws[0]
+    dt = torch.float64 if prec == "f64" else torch.float32
+    p = sac.params(alpha=w0.alpha, rho=w0.rho, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, near_bound=1e-3)
+    grids = [sac.grid(w.m, w.h, w.pe) for w in ws]
+    I1s = [cu(d["I1"], dt) for d in pairs]
+    I2s = [cu(d["I2"], dt) for d in pairs]
+    bs = [torch.zeros(sac.face_shape(g), dtype=torch.float64, device="cuda") for g in grids]
+    bt = sac.Batch(grids, p, I1s, I2s, bs)
+    bt.run(K, chunk=K)
+    st = bt.stats()
+    bt.finish()
+    bt.close()
+    assert np.all(st["iters"] == K)
+    for k in (0, 37, 63):
+        w, d = ws[k], pairs[k]
+        og = oracle.Grid(w.m, w.h, w.pe)
+        op = oracle.Params(alpha=w.alpha, rho=w.rho, max_iter=K, eps_abs=0.0, eps_rel=0.0,
+                           knot32=1 if prec == "mixed" else 0)
+        ref = oracle.admm(og, op, d["I1"].astype(np.float64), d["I2"].astype(np.float64), np.zeros(og.face_shape))
+        bb = bs[k].cpu().numpy()
+        if prec == "f64":
+            assert np.linalg.norm(bb - ref["b"]) <= 1e-9 * np.linalg.norm(ref["b"]), k
+        else:
+            assert np.max(np.abs(bb - ref["b"])) / w.h[w.pe] <= 1e-3, k
