@@ -341,6 +341,13 @@ def serve_run(args, sac, dev):
                                   "assigned its kind's time; sum_s: all requests back to back"}}
 
 
+def workload_config(w, nf, world):
+    """The workload both arms run (the same dict in both JSON lines)."""
+    return {"workload": w.name, "faces": nf, "grid": list(w.m), "pe_axis": w.pe, "alpha": w.alpha, "rho": w.rho,
+            "parallelism": f"replicas{world}",
+            "l2": "working set > 129 MB L2 (images, b, z, u, two scratch arrays)"}
+
+
 def batch64_run(args, sac, dev):
     """The DTI-like batch: 64 pairs of 96 x 96 x 60 (independent seeded
     fields of 2-6 px, SNR 10-40) in one engine, one launch per phase over all
@@ -472,7 +479,8 @@ def run_reference(args, w, d, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "faces": nf, "prec": "f64-cpu-oracle"},
+            "data": "synthetic", "config": workload_config(w, nf, args.gpus),
+            "timed": "the FP64 CPU oracle (sac_oracle.c) as it stands: K full ADMM iterations on the host cores",
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full ADMM iterations of {w.name} after {args.warmup} warm-up"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -727,10 +735,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": w.name, "faces": nf, "grid": list(w.m), "pe_axis": w.pe,
-                           "alpha": w.alpha, "rho": w.rho, "prec": "mixed", "parallelism": f"replicas{world}",
-                           "timed": "sac_batch_run (one volume): CUDA-graph replay of K iterations, device time",
-                           "l2": "working set > 129 MB L2 (images, b, z, u, two scratch arrays)"},
+                "config": workload_config(w, nf, world),
+                "prec": "mixed",
+                "timed": "sac_batch_run (one volume): CUDA-graph replay of K iterations, device time",
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 "profiled_run_ms_per_step": t_prof_ms / args.steps,
