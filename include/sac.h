@@ -109,8 +109,14 @@ typedef struct {
     double near_bound;   /* SAC_MIXED: lines with 1 - max|D1 b| < near_bound are
                             re-solved in FP64 after the FP32 b-step */
     int check_every;     /* ADMM: test the stopping rule every k iterations */
-    int zstep_kernel;    /* SAC_MIXED z-step DCTs: 0 tensor cores (tcgen05, split TF32)
-                            where the grid allows (else SIMT), 1 SIMT FP32 */
+    int zstep_kernel;    /* SAC_MIXED z-step: 0 tensor cores -- on 3D grids whose
+                            last axis is not the PE axis, with at most 256
+                            faces along the first non-PE axis and 128 along
+                            the last, one on-chip launch per iteration (all
+                            four DCT contractions, the scaling and the dual
+                            update, split FP16); otherwise per-axis passes
+                            (split TF32) where the grid allows, else SIMT;
+                            1 SIMT FP32; 2 tensor cores, per-axis passes only */
     int autotune;        /* batched runs: 1 = pick the b-step tile width on the
                             first live iterations (results do not depend on it) */
     int bstep_kernel;    /* SAC_MIXED b-step with n_sqp = 1: 0 one thread per
@@ -133,11 +139,13 @@ const char* sac_status_string(int status);
 /* Workspace for the single-volume entry points below. */
 size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p);
 
-/* Host only (no device needed): 1 when the z-step of this grid and these
-   parameters runs its second-axis DCT, spectral scale and inverse DCT
-   (passes 1 and 2, Sec. 4.2 Eq. dctdiag) as one tensor-core launch, 0 when
-   it runs them as separate launches or on the SIMT path, SAC_EINVAL for an
-   invalid grid or parameters. */
+/* Host only (no device needed): 2 when the z-step of this grid and these
+   parameters runs on the chip in one launch (all contractions of Sec. 4.2
+   Eq. dctdiag, the scaling and the dual update, one PE slab at a time), 1
+   when it runs its second-axis DCT, spectral scale and inverse DCT (passes
+   1 and 2) as one tensor-core launch among per-axis passes, 0 when it runs
+   them as separate launches or on the SIMT path, SAC_EINVAL for an invalid
+   grid or parameters. */
 int sac_zstep_fused(const sac_grid* g, const sac_params* p);
 
 /* Objective (Sec. 3, Eqs. D, S, P, JGN): out[0..3] = {J_GN, D, S, P} with
@@ -326,10 +334,13 @@ void sac_server_destroy(sac_server s);
  *   5 z-step pass 3 (inverse DCT along the first non-PE axis)
  *   6 dual update u <- u + b - z, z update, residual-norm partial sums and
  *     the stopping test (tensor-core z-step: the element-wise update kernel;
- *     SIMT z-step: the reduction of the sums pass 3 produced)
+ *     SIMT z-step: the reduction of the sums pass 3 produced; on-chip
+ *     z-step: the reduction of its per-slab sums)
+ *   7 on-chip z-step: the four contractions, the scaling and the dual
+ *     update in one launch (phases 2-5 then stay empty)
  * sac_launch_count returns the number of kernels this library has launched
  * in the process so far. */
-#define SAC_NPHASES 7
+#define SAC_NPHASES 8
 int sac_profile_enable(int on);
 int sac_profile_read(double* ms, long long* launches, int reset);
 long long sac_launch_count(void);

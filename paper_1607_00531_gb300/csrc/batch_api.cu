@@ -21,7 +21,7 @@ static int batch_jobs(int njobs, const sac_grid* grids, const sac_params* p, std
     int st = check_params(p);
     if (st < 0) return st;
     jobs->assign(njobs, EngineJob{});
-    int use_tc = (p->prec == SAC_MIXED && p->zstep_kernel == 0);
+    int use_tc = (p->prec == SAC_MIXED && p->zstep_kernel != 1);
     for (int j = 0; j < njobs; ++j) {
         EngineJob& E = (*jobs)[j];
         st = make_geometry(&grids[j], &E.G);
@@ -54,7 +54,7 @@ int sac_batch_create(int njobs, const sac_grid* grids, const sac_params* p, cons
     if (st < 0) return st;
     const size_t tb = a256b(Engine::table_bytes(jobs, *p));
     if (ws_bytes < tb + states || ((uintptr_t)ws & 255)) return ws_bytes < tb + states ? SAC_ENOMEM : SAC_EINVAL;
-    const int use_tc = (p->prec == SAC_MIXED && p->zstep_kernel == 0) ? 1 : 0;
+    const int use_tc = (p->prec == SAC_MIXED && p->zstep_kernel != 1) ? 1 : 0;
     int use_tc_all = use_tc;
     for (auto& E : jobs)
         for (int q = 0; q < 4; ++q)

@@ -28,7 +28,7 @@ int prepare_kernels() {
     if (g_prep_device == dev) return SAC_OK;
     if (prepare_bstep_f64() != cudaSuccess || prepare_bstep_f32() != cudaSuccess ||
         prepare_bstep_mixed() != cudaSuccess || prepare_line_eval() != cudaSuccess ||
-        prepare_axis_tc() != cudaSuccess || prepare_bstep_seg() != cudaSuccess) {
+        prepare_axis_tc() != cudaSuccess || prepare_bstep_seg() != cudaSuccess || prepare_zslab() != cudaSuccess) {
         cudaGetLastError();
         return SAC_ECUDA;
     }
@@ -156,7 +156,7 @@ int check_params(const sac_params* p) {
     if (p->precond < 0 || p->precond > 2) return SAC_EINVAL;
     if (p->prec != SAC_F64 && p->prec != SAC_MIXED) return SAC_EINVAL;
     if (!(p->near_bound >= 0)) return SAC_EINVAL;
-    if (p->zstep_kernel < 0 || p->zstep_kernel > 1) return SAC_EINVAL;
+    if (p->zstep_kernel < 0 || p->zstep_kernel > 2) return SAC_EINVAL;
     if (p->bstep_kernel < 0 || p->bstep_kernel > 1) return SAC_EINVAL;
     if (p->adapt_rho < 0 || p->adapt_rho > 2) return SAC_EINVAL;
     if (p->adapt_rho && (!(p->rho_tau > 1.0) || !(p->rho_mu > 0.0) || !(p->rho_min > 0.0))) return SAC_EINVAL;
@@ -208,7 +208,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     const int axes[4] = {G.ax1, G.ax2, G.ax2, G.ax1};
     for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
     P->elem_blocks = (G.nf + 255) / 256;
-    P->use_tc = (p->prec == SAC_MIXED && p->zstep_kernel == 0);
+    P->use_tc = (p->prec == SAC_MIXED && p->zstep_kernel != 1);
     for (int q = 0; q < 4; ++q) {
         if (!tc_pass_supported(G.F, G.ax1, G.ax2, q)) P->use_tc = 0;
         P->tc_tiles[q] = tc_pass_tiles(G.F, G.ax1, G.ax2, q);
@@ -227,6 +227,15 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
             P->fuse12 = 1;
         }
     }
+    // the whole z-step and dual update on the chip, one PE slab at a time
+    P->use_zs = (p->prec == SAC_MIXED && p->zstep_kernel == 0 && zs_supported(G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
+    if (P->use_zs) {
+        P->zs_cfg = ZsCfg();
+        zs_cfg_add(&P->zs_cfg, G.F, G.pe, G.ax1);
+        if (!zs_cfg_finish(&P->zs_cfg)) P->use_zs = 0;
+    }
+    P->zs_slabs = P->use_zs ? zs_slabs(G.F, G.pe) : 0;
+    P->zs_bytes = P->use_zs ? zs_matrix_bytes(G.F, G.pe, G.ax1) : 0;
     const long long nlines = (long long)G.n_outer * G.n_inner;
     P->rcap = (int)nlines;
     long long np = 4 * P->line_tiles;
@@ -234,6 +243,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->admm_blocks = admm_update_blocks(G.nf);
     if (5 * P->admm_blocks > np) np = 5 * P->admm_blocks;
     if (P->elem_blocks > np) np = P->elem_blocks;
+    if (5 * P->zs_slabs > np) np = 5 * P->zs_slabs;
     if (2 * 1216 > np) np = 2 * 1216;
     P->n_part = np;
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -241,7 +251,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     size_t o_job = take(sizeof(Job));
-    size_t o_pref = take(sizeof(long long) * 2 * 12);
+    size_t o_pref = take(sizeof(long long) * 2 * 13);
     size_t o_stat = take(256);
     size_t o_out = take(sizeof(double) * 64);
     size_t o_rlist = take(sizeof(unsigned long long) * (size_t)P->rcap);
@@ -259,6 +269,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) o_tc[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tc_floats[q] : 0));
     size_t o_tn[4];
     for (int q = 0; q < 4; ++q) o_tn[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tn_floats[q] : 0));
+    size_t o_zs = take((size_t)P->zs_bytes);
     const bool maps = P->use_tc || P->seg_S > 0;   // TMA tensor maps of the z-step passes / the b-step
     size_t o_tmap = take(maps ? tc_map_bytes() : 0);
     size_t o_arr[10];
@@ -275,6 +286,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     for (int q = 0; q < 4; ++q) P->d_pref_tc[q] = pref + 12 + 2 * q;
     P->d_pref_admm = pref + 20;
     P->d_pref_seg = pref + 22;
+    P->d_pref_zs = pref + 24;
+    P->d_Czs = P->use_zs ? (unsigned char*)(base + o_zs) : nullptr;
     for (int q = 0; q < 4; ++q) P->d_Ctc[q] = P->use_tc ? (float*)(base + o_tc[q]) : nullptr;
     for (int q = 0; q < 4; ++q) P->d_Ctn[q] = (P->use_tc && P->tn_floats[q]) ? (float*)(base + o_tn[q]) : nullptr;
     P->d_scale = (float*)(base + o_scale);
@@ -321,6 +334,7 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     for (int q = 0; q < 4; ++q) J.Ctn[q] = P->d_Ctn[q];
     for (int q = 0; q < 4; ++q) J.tc_T[q] = tc_tile_lines(G.F, G.ax1, G.ax2, q);
     J.scale = P->d_scale;
+    J.Czs = P->d_Czs;
     J.active = 1;
     const bool tc_maps = P->use_tc && P->d_tmaps && b && u && t1 && t2;
     const bool seg_maps = P->seg_S > 0 && P->d_tmaps && I1 && I2 && b && z && u;
@@ -337,9 +351,10 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                                         (const float*)b, (const float*)z, (const float*)u, maps.data());
         SAC_CUDA(cudaMemcpyAsync(P->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
     }
-    long long pref[24] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
+    long long pref[26] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],
                           0, P->pass_tiles[3], 0, P->elem_blocks, 0, P->tc_tiles[0], 0, P->tc_tiles[1],
-                          0, P->tc_tiles[2], 0, P->tc_tiles[3], 0, P->admm_blocks, 0, P->seg_tiles};
+                          0, P->tc_tiles[2], 0, P->tc_tiles[3], 0, P->admm_blocks, 0, P->seg_tiles,
+                          0, P->zs_slabs};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -376,6 +391,11 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                 SAC_CUDA(cudaMemcpyAsync(P->d_Ctn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
             }
         }
+    }
+    if (P->use_zs) {
+        std::vector<unsigned char> zsm((size_t)P->zs_bytes);
+        zs_arrange(G.F, G.pe, G.ax1, C1.data(), C2.data(), zsm.data());
+        SAC_CUDA(cudaMemcpyAsync(P->d_Czs, zsm.data(), zsm.size(), cudaMemcpyHostToDevice, st));
     }
     SAC_CUDA(cudaMemcpyAsync(P->d_C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
@@ -505,6 +525,19 @@ static int max_abs_d1_dev(Plan& P, const double* b, double* out, cudaStream_t st
 // norms, the five residual sums into d_out + 16 (else left unreduced: the
 // ADMM driver needs them only at its stopping tests)
 static int zstep_passes(Plan& P, cudaStream_t st, bool norms = true) {
+    if (P.use_zs) {
+        // one launch: the four contractions, the scaling and the dual update
+        {
+            PhaseScope ps(7, st);
+            SAC_CUDA(launch_zslab(P.d_job, 1, P.d_pref_zs, P.zs_slabs, P.zs_cfg, P.d_part, norms ? 1 : 0, nullptr,
+                                  P.d_status, st));
+        }
+        if (norms) {
+            PhaseScope ps(6, st);
+            SAC_CUDA(launch_reduce(P.d_part, (int)P.zs_slabs, 5, P.d_out + 16, st));
+        }
+        return SAC_OK;
+    }
     const int prec = (P.prec == SAC_MIXED) ? 1 : 0;
     for (int q = 0; q < 4; ++q) {
         if (P.use_tc && P.fuse12 && q == 2) continue;   // done with pass 1
@@ -632,6 +665,7 @@ int sac_set_wait_limit(int which, long long tests) {
     if (which & 2) {
         SAC_CUDA(set_wait_tests_tc(n));
         SAC_CUDA(set_wait_tests_tcn(n));
+        SAC_CUDA(set_wait_tests_zs(n));
     }
     return SAC_OK;
 }
@@ -660,6 +694,7 @@ size_t sac_workspace_bytes(const sac_grid* g, const sac_params* p) {
 int sac_zstep_fused(const sac_grid* g, const sac_params* p) {
     Plan P;
     if (plan_layout(g, p, nullptr, &P) != SAC_OK) return SAC_EINVAL;
+    if (P.use_zs) return 2;
     return (P.use_tc && P.fuse12) ? 1 : 0;
 }
 

@@ -54,6 +54,8 @@ void set_tuned_lines_per_cta(int K, int prec, int inner_fast, int W) {
 struct StateLayout {
     size_t b32, z, u, t1, t2;          // face arrays
     size_t C1, C2, C1f, C2f, l1, l2, l1f, l2f, scale, tc[4], tn[4], tmap;
+    size_t zs;                         // split FP16 operands of the on-chip z-step (0 bytes: none)
+    size_t zs_bytes;
     size_t bytes;
 };
 
@@ -82,6 +84,9 @@ static StateLayout state_layout(const Geometry& G, int prec, int use_tc) {
     for (int q = 0; q < 4; ++q)
         s.tn[q] = take(use_tc ? 4 * (size_t)tcn_matrix_floats(G.F, G.ax1, G.ax2, q) : 0);
     s.tmap = take((use_tc || prec == SAC_MIXED) ? tc_map_bytes() : 0);   // z-step passes, b-step staging
+    s.zs_bytes = (use_tc && prec == SAC_MIXED && zs_supported(G.nd, G.F, G.pe, G.ax1, G.ax2))
+                     ? (size_t)zs_matrix_bytes(G.F, G.pe, G.ax1) : 0;
+    s.zs = take(s.zs_bytes);
     s.bytes = off;
     return s;
 }
@@ -122,13 +127,14 @@ __global__ void k_init_state(long long n, const double* __restrict__ b, void* b3
 size_t Engine::table_bytes(const std::vector<EngineJob>& jobs, const sac_params& p) {
     (void)p;
     const size_t nj = jobs.size();
-    long long lines = 0, ablocks = 0, tiles_ax3 = 0;
+    long long lines = 0, ablocks = 0, tiles_ax3 = 0, slabs = 0;
     for (auto& j : jobs) {
         lines += (long long)j.G.n_outer * j.G.n_inner;
         ablocks += admm_update_blocks(j.G.nf);
         tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
+        slabs += zs_slabs(j.G.F, j.G.pe);   // bound: on-chip z-step partial sets after the update's
     }
-    long long np = 5 * std::max(ablocks, tiles_ax3) + 8;
+    long long np = 5 * std::max(ablocks + slabs, tiles_ax3) + 8;
     size_t off = 0;
     off += a256(sizeof(Job) * nj);
     off += a256(sizeof(long long) * (nj + 1) * (4 + 8 + 8));   // class prefixes (<= 8 classes), 4 pass prefixes, ADMM update blocks, spare
@@ -170,7 +176,7 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     std::stable_sort(order_.begin(), order_.end(), [&](int a, int b) { return cls_key(in[a]) < cls_key(in[b]); });
     jobs_.clear();
     for (int i : order_) jobs_.push_back(in[i]);
-    use_tc_ = (prec == SAC_MIXED && p.zstep_kernel == 0);
+    use_tc_ = (prec == SAC_MIXED && p.zstep_kernel != 1);
     for (auto& j : jobs_)
         for (int q = 0; q < 4; ++q)
             if (!tc_pass_supported(j.G.F, j.G.ax1, j.G.ax2, q)) use_tc_ = 0;
@@ -188,12 +194,20 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     d_status_ = d_rcount_ + kMaxCls;
     d_nactive_ = d_rcount_ + kMaxCls + 1;
     d_counters_ = (int*)take(sizeof(int) * nj);
-    long long ablocks = 0, tiles_ax3 = 0;
+    long long ablocks = 0, tiles_ax3 = 0, slabs = 0;
     for (auto& j : jobs_) {
         ablocks += admm_update_blocks(j.G.nf);
         tiles_ax3 += axis_pass_tiles(j.G.F, j.G.ax1);
+        slabs += zs_slabs(j.G.F, j.G.pe);
     }
-    d_part_ = (double*)take(sizeof(double) * (size_t)(5 * std::max(ablocks, tiles_ax3) + 8));
+    d_part_ = (double*)take(sizeof(double) * (size_t)(5 * std::max(ablocks + slabs, tiles_ax3) + 8));
+    // jobs whose z-step and dual update run on the chip (zstep_slab.cu)
+    zs_job_.assign(nj, 0);
+    for (size_t i = 0; i < nj; ++i) {
+        const Geometry& G = jobs_[i].G;
+        zs_job_[i] = (use_tc_ && prec == SAC_MIXED && p.zstep_kernel == 0 &&
+                      zs_supported(G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
+    }
     d_stats_ = (double*)take(sizeof(double) * 8 * nj);
     // classes
     std::vector<long long> hpref((nj + 1) * (4 + 8 + 8), 0);
@@ -283,8 +297,9 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
                 long long* h = hz.data() + (size_t)z * (nj + 1);
                 for (size_t i = 0; i < nj; ++i) {
                     const Geometry& G = jobs_[i].G;
-                    h[i + 1] = h[i] + (gid[i] == gr ? tc_pass_tiles(G.F, G.ax1, G.ax2, q) : 0);
-                    if (gid[i] == gr) tc_cfg_add(&zcfg_[z], G.F, G.ax1, G.ax2, q);
+                    const bool mine = gid[i] == gr && !zs_job_[i];
+                    h[i + 1] = h[i] + (mine ? tc_pass_tiles(G.F, G.ax1, G.ax2, q) : 0);
+                    if (mine) tc_cfg_add(&zcfg_[z], G.F, G.ax1, G.ax2, q);
                 }
                 ztiles_[z] = h[nj];
                 if (q == 1 && use_tc_) {
@@ -302,8 +317,20 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         d_pref_admm_ = pref + 12 * (nj + 1);
         long long* hb = hpref.data() + 12 * (nj + 1);
         hb[0] = 0;
-        for (size_t i = 0; i < nj; ++i) hb[i + 1] = hb[i] + admm_update_blocks(jobs_[i].G.nf);
+        for (size_t i = 0; i < nj; ++i) hb[i + 1] = hb[i] + (zs_job_[i] ? 0 : admm_update_blocks(jobs_[i].G.nf));
         admm_blocks_ = hb[nj];
+        // slabs of the on-chip z-step per job (the others: none)
+        d_pref_zs_ = pref + 13 * (nj + 1);
+        long long* hs = hpref.data() + 13 * (nj + 1);
+        hs[0] = 0;
+        zs_cfg_ = ZsCfg();
+        for (size_t i = 0; i < nj; ++i) {
+            const Geometry& G = jobs_[i].G;
+            hs[i + 1] = hs[i] + (zs_job_[i] ? zs_slabs(G.F, G.pe) : 0);
+            if (zs_job_[i]) zs_cfg_add(&zs_cfg_, G.F, G.pe, G.ax1);
+        }
+        zs_total_ = hs[nj];
+        if (zs_total_ > 0 && !zs_cfg_finish(&zs_cfg_)) return SAC_EINVAL;
     }
     ENG_CUDA(cudaMemcpyAsync(pref, hpref.data(), hpref.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     // jobs: state layout, tables, initial state
@@ -352,6 +379,7 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
             ENG_CUDA(cudaMemcpyAsync(s + L.tmap, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
         }
         J.part = d_part_;
+        J.Czs = zs_job_[i] ? (const void*)(s + L.zs) : nullptr;
         J.active = 1;
         if (E.fresh) {
             // tables (host-computed, FP64 then FP32 / split TF32 copies)
@@ -394,6 +422,11 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
                         ENG_CUDA(cudaMemcpyAsync(s + L.tn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
                     }
                 }
+            }
+            if (L.zs_bytes) {
+                std::vector<unsigned char> zsm(L.zs_bytes);
+                zs_arrange(G.F, G.pe, G.ax1, C1.data(), C2.data(), zsm.data());
+                ENG_CUDA(cudaMemcpyAsync(s + L.zs, zsm.data(), zsm.size(), cudaMemcpyHostToDevice, st));
             }
             count_launch();
             k_init_state<<<256, 256, 0, st>>>(G.nf, E.b, s + L.b32, s + L.z, s + L.u, prec == SAC_MIXED);
@@ -505,6 +538,15 @@ int Engine::enqueue_iteration(int slot) {
         ENG_CUDA(cudaGetLastError());
     }
     prof_mark(slot, 6, 1);
+    if (zs_total_ > 0) {
+        // on-chip z-step jobs: the contractions, the scaling, the dual update
+        // and (the CTA finishing a job's last slab) the stopping test
+        prof_mark(slot, 7, 0);
+        const AdmmCheck chk = check_args();
+        ENG_CUDA(launch_zslab(d_jobs_, nj, d_pref_zs_, zs_total_, zs_cfg_, d_part_ + 5 * admm_blocks_, 1, &chk,
+                              d_status_, st_));
+        prof_mark(slot, 7, 1);
+    }
     return SAC_OK;
 }
 

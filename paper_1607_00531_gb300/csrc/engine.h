@@ -98,6 +98,12 @@ private:
     long long ax_tiles_[4] = {0, 0, 0, 0};
     long long* d_pref_admm_ = nullptr;   // ADMM update blocks per job (tensor-core z-step)
     long long admm_blocks_ = 0;
+    // on-chip z-step (zstep_slab.cu): which jobs, their slab prefix, the
+    // launch's shared-memory layout
+    std::vector<char> zs_job_;
+    long long* d_pref_zs_ = nullptr;
+    long long zs_total_ = 0;
+    ZsCfg zs_cfg_;
     unsigned long long* d_rlist_ = nullptr;
     int* d_rcount_ = nullptr;      // one counter per class, then status and active count
     int* d_counters_ = nullptr;    // per job: finished blocks of the ADMM update (fused stopping test)

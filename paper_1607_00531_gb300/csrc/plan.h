@@ -46,6 +46,9 @@ struct Plan {
     TcCfg tc_cfg[4];           // ring / accumulator layout of each tensor-core pass
     TcCfg tc_cfg12;            // passes 1 and 2 in one launch (valid when fuse12)
     int fuse12;
+    int use_zs;                // the z-step and dual update on the chip (zstep_slab.cu)
+    long long zs_slabs, zs_bytes;
+    ZsCfg zs_cfg;
     int rcap;
     // device pointers inside ws
     Job* d_job;
@@ -55,6 +58,8 @@ struct Plan {
     long long* d_pref_tc[4];
     long long* d_pref_admm;   // blocks of the ADMM update after the tensor-core passes
     long long* d_pref_seg;    // tiles of the b-step segment kernel
+    long long* d_pref_zs;     // slabs of the on-chip z-step
+    unsigned char* d_Czs;     // its split FP16 DCT operands
     float* d_Ctc[4];
     float* d_Ctn[4];
     void* d_tmaps;            // tensor maps of the tensor-core passes

@@ -62,6 +62,7 @@ struct Job {
     double uscale;
     const float* lam1f;  // FP32 copies of lam1 / lam2 (the scale table is rebuilt from them)
     const float* lam2f;
+    const void* Czs;     // on-chip z-step: split FP16 DCT operands (zstep_slab.cu)
 };
 
 // ---------------------------------------------------------------- job lookup

@@ -112,6 +112,34 @@ cudaError_t prepare_bstep_seg();
 cudaError_t set_wait_tests_seg(long long tests);
 cudaError_t set_wait_tests_tc(long long tests);
 cudaError_t set_wait_tests_tcn(long long tests);
+cudaError_t set_wait_tests_zs(long long tests);
+
+// ---- z-step on the chip, one PE slab per CTA at a time (zstep_slab.cu):
+// the four DCT contractions, the spectral scaling and the dual update of 3D
+// jobs whose last axis is not the PE axis, with at most 256 faces along the
+// first non-PE axis and 128 along the last.  Shared-memory layout of a launch,
+// sized for its largest job (zs_cfg_add per job, then zs_cfg_finish).
+struct ZsCfg {
+    int N1 = 0, N2 = 0;                 // largest padded slab dimensions
+    uint32_t off_bxlo = 0, off_by = 0, off_bylo = 0, off_ring = 0;   // byte offsets
+    uint32_t slot = 0;                  // bytes of a DCT ring slot
+    int ring = 0;                       // ring stages
+    size_t smem = 0;                    // dynamic shared memory per CTA
+};
+bool zs_supported(int nd, const int F[3], int pe, int ax1, int ax2);
+long long zs_slabs(const int F[3], int pe);
+long long zs_matrix_bytes(const int F[3], int pe, int ax1);
+void zs_cfg_add(ZsCfg* c, const int F[3], int pe, int ax1);
+bool zs_cfg_finish(ZsCfg* c);
+// Host: a job's split FP16 DCT operands (zs_matrix_bytes bytes) from its
+// orthonormal DCT-II matrices C1 (along ax1) and C2 (along the last axis)
+void zs_arrange(const int F[3], int pe, int ax1, const double* C1, const double* C2, unsigned char* out);
+cudaError_t prepare_zslab();
+// prefix[j]: first slab of job j.  part: 5 partial sums per slab, FP64
+// (norms != 0, chk null or without counters), or FP32 with the fused
+// stopping test (chk->counters: the CTA finishing a job's last slab tests it)
+cudaError_t launch_zslab(Job* jobs, int njobs, const long long* prefix, long long total, const ZsCfg& cfg,
+                         double* part, int norms, const AdmmCheck* chk, int* status, cudaStream_t st);
 
 // prec: 0 FP64, 1 FP32, 2 FP64 compute on FP32 storage
 cudaError_t launch_bstep(int prec, const LineLaunch& L);
@@ -145,6 +173,7 @@ struct TcCfg {
     int acc_need = 0;                // TMEM columns of one tile's accumulator
     int sd = 0, sr = 0, st = 0;      // ring stages: DCT, raw X, split X (tensor memory)
     int st2 = 0;                     // fused passes 1 + 2: stages of the second split ring (D2's operand)
+    int nd1 = 2;                     // fused passes 1 + 2: D1 buffers in tensor memory
     int nacc = 0;                    // accumulator buffers (2 when both fit in TMEM)
     uint32_t acc_cols = 0;           // TMEM columns per accumulator buffer
     uint32_t epi_off = 0;            // shared-memory offset of the epilogue transpose buffers

@@ -111,7 +111,7 @@ struct sac_server_s {
 
 static size_t req_bytes(const sac_server_s* S, const Geometry& G) {
     const size_t es = (S->p.prec == SAC_MIXED) ? 4 : 8;
-    const int use_tc = (S->p.prec == SAC_MIXED && S->p.zstep_kernel == 0);
+    const int use_tc = (S->p.prec == SAC_MIXED && S->p.zstep_kernel != 1);
     return a256s(2 * es * (size_t)G.nc) + a256s(8 * (size_t)G.nf) + a256s(job_state_bytes(G, S->p.prec, use_tc));
 }
 
@@ -150,7 +150,7 @@ int sac_server_submit(struct sac_server_s* S, const sac_grid* g, const void* I1_
     ServeReq R;
     int s = make_geometry(g, &R.G);
     if (s < 0) return s;
-    if (S->p.prec == SAC_MIXED && S->p.zstep_kernel == 0)
+    if (S->p.prec == SAC_MIXED && S->p.zstep_kernel != 1)
         for (int q = 0; q < 4; ++q)
             if (!tc_pass_supported(R.G.F, R.G.ax1, R.G.ax2, q)) return SAC_EINVAL;
     R.bytes = req_bytes(S, R.G);

@@ -215,15 +215,20 @@ bool tc_cfg_fuse12(TcCfg* c) {
     if (need() > budget) return false;
     while (c->sr < tc::kMaxRStages && need() + c->rslot <= budget) c->sr++;
     c->acc_cols = (uint32_t)((c->acc_need + 31) & ~31);
-    // the accumulators, D1, then at least two X slots
-    // one accumulator (D2), two D1 buffers (the next tile's first product
-    // runs while group B converts this tile's D1), then ring A (at least two
-    // slots) and ring B (at least one)
+    // one accumulator (D2), one D1 buffer, ring A (two slots) and ring B (all
+    // the rest, up to the chunks of one tile): with ring B able to take a
+    // whole tile's scaled D1, group B converts a tile without waiting for D2's
+    // products, frees D1 early and the next tile's D1 product follows at
+    // once.  (Measured by per-role traces: with two D1 buffers and one ring-B
+    // slot every ring-B chunk waited for the tensor pipe, ~4-8 k cycles.)
     c->nacc = 1;
-    const int slots = (int)((tc::kTmemCols - 3 * c->acc_cols) / tc::kXCols);   // D2, two D1
+    c->nd1 = 1;
+    const int slots = (int)((tc::kTmemCols - 2 * c->acc_cols) / tc::kXCols);   // D2, D1
     if (slots < 3) return false;
-    c->st2 = (slots >= 4) ? 2 : 1;
-    c->st = slots - c->st2 > tc::kMaxTStages ? tc::kMaxTStages : slots - c->st2;
+    c->st = 2;
+    c->st2 = slots - c->st;
+    if (c->st2 > c->nch) c->st2 = c->nch;
+    if (c->st2 > tc::kMaxTStages) c->st2 = tc::kMaxTStages;
     c->resident = 1;
     c->epi_off = (uint32_t)need();
     c->smem = need() + tc::kEpiBytes;
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const uint32_t tmem = tmem_slot;
     // TMEM columns: the accumulators, (fused) two D1 buffers, then the X slots
     const uint32_t d1col = (uint32_t)cfg.nacc * cfg.acc_cols;
-    const uint32_t xcol0 = d1col + (FUSED ? 2u * cfg.acc_cols : 0u);
+    const uint32_t xcol0 = d1col + (FUSED ? (uint32_t)cfg.nd1 * cfg.acc_cols : 0u);
     const long long t0 = blockIdx.x, dt = gridDim.x;
 
     if (FUSED && warp < kConvWarps) {
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         const uint32_t colA = xcol0, colB = xcol0 + (uint32_t)cfg.st * kXCols;
         RingPos rr, tr;
-        uint32_t nd1 = 0;   // group B: D1 buffers consumed (buffer nd1 & 1, parity (nd1 >> 1) & 1)
+        uint32_t nd1 = 0;   // group B: D1 products consumed (buffer nd1 % cfg.nd1, parity (nd1 / cfg.nd1) & 1)
         for (long long t = t0; t < total; t += dt) {
             const TcTile s = tc_tile(jobs, njobs, prefix, PIN, tc_unit_tile(t, nfull));
             if (!s.active) continue;
@@ -574,8 +579,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     tr.next(cfg.st);
                 }
             } else {
-                const uint32_t d1b = nd1 & 1u;
-                ok = __all_sync(kFull, mbar_wait_ab(b_d1full + 8 * d1b, (nd1 >> 1) & 1u, abort));
+                const uint32_t d1b = nd1 % (uint32_t)cfg.nd1;
+                ok = __all_sync(kFull, mbar_wait_ab(b_d1full + 8 * d1b, (nd1 / (uint32_t)cfg.nd1) & 1u, abort));
                 if (!ok) break;
                 ++nd1;
                 fence_after();
@@ -796,7 +801,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             // one product of a tile: its nch X chunks from ring A (or, fused
             // D2, ring B) against the DCT chunks (resident: slots dbase + c;
             // else the DCT ring)
-            auto product = [&](uint32_t dacc, int dbase, int nch, int Np, int n0, int nN, bool ringB) -> bool {
+            // (K steps past the contracted length L multiply zero padding and
+            // are not issued)
+            auto product = [&](uint32_t dacc, int dbase, int nch, int Np, int n0, int nN, bool ringB, int L) -> bool {
                 const uint32_t idesc = idesc_tf32(kTileLines, nN);
                 RingPos& xr = ringB ? tr2 : tr;
                 const uint32_t fb = ringB ? b_t2full : b_tfull, eb = ringB ? b_t2empty : b_tempty;
@@ -818,16 +825,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     const uint64_t cl = ch + (uint32_t)Np * 8u;
                     const uint32_t xh = tmem + xc0 + (uint32_t)ts * kXCols, xl = xh + kBK;
                     const uint32_t en = (c > 0) ? 1u : 0u;   // the tile's first K step overwrites
+                    const int nks = (L - kBK * c + 7) / 8;     // K steps of this chunk with data (>= 1)
                     // product by product (hi x hi over the chunk's K steps, then
                     // hi x lo, then lo x hi): consecutive MMAs walk along K, which
                     // issues measurably faster than alternating the split
                     // operands at every K step
 #pragma unroll
-                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xh + 8 * ks, ch + 16u * ks, idesc, ks ? 1u : en);
+                    for (int ks = 0; ks < kBK / 8; ++ks)
+                        if (ks < nks) mma_tf32_ta(dacc, xh + 8 * ks, ch + 16u * ks, idesc, ks ? 1u : en);
 #pragma unroll
-                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xh + 8 * ks, cl + 16u * ks, idesc, 1u);
+                    for (int ks = 0; ks < kBK / 8; ++ks)
+                        if (ks < nks) mma_tf32_ta(dacc, xh + 8 * ks, cl + 16u * ks, idesc, 1u);
 #pragma unroll
-                    for (int ks = 0; ks < kBK / 8; ++ks) mma_tf32_ta(dacc, xl + 8 * ks, ch + 16u * ks, idesc, 1u);
+                    for (int ks = 0; ks < kBK / 8; ++ks)
+                        if (ks < nks) mma_tf32_ta(dacc, xl + 8 * ks, ch + 16u * ks, idesc, 1u);
                     if (!cfg.resident) mma_commit(b_dempty + 8 * ds);
                     mma_commit(eb + 8 * ts);
                     dr.next(cfg.sd);
@@ -839,26 +850,27 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 // D1 of tile t (two buffers) is issued before D2 of the
                 // previous tile, so that the tensor pipe works on the next
                 // tile while converter group B turns D1 into D2's operand
-                uint32_t n1 = 0;       // D1 products issued (buffer n1 & 1)
+                uint32_t n1 = 0;       // D1 products issued (buffer n1 % cfg.nd1)
                 bool pending = false;  // a tile whose D2 is still to do
-                int pnch = 0, pNp = 0;
+                int pnch = 0, pNp = 0, pL = 0;
                 for (long long t = t0;; t += dt) {
                     const bool more = t < total && !*abort;
                     bool have = false;
-                    int nch = 0, Np = 0;
+                    int nch = 0, Np = 0, L = 0;
                     if (more) {
                         const TcTile s = tc_tile(jobs, njobs, prefix, PIN, t);
                         have = s.active;
                         nch = s.nch;
                         Np = s.Np;
+                        L = s.L;
                     }
                     bool ok = true;
                     if (have) {
-                        const uint32_t b = n1 & 1u;
-                        ok = mbar_wait_ab(b_d1empty + 8 * b, ((n1 >> 1) & 1u) ^ 1u, abort);
+                        const uint32_t b = n1 % (uint32_t)cfg.nd1;
+                        ok = mbar_wait_ab(b_d1empty + 8 * b, ((n1 / (uint32_t)cfg.nd1) & 1u) ^ 1u, abort);
                         if (ok) {
                             fence_after();
-                            ok = product(tmem + d1col + b * cfg.acc_cols, 0, nch, Np, 0, Np, false);
+                            ok = product(tmem + d1col + b * cfg.acc_cols, 0, nch, Np, 0, Np, false, L);
                         }
                         if (ok) {
                             mma_commit(b_d1full + 8 * b);
@@ -870,7 +882,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         ok = mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort);
                         if (ok) {
                             fence_after();
-                            ok = product(tmem + (uint32_t)a * cfg.acc_cols, pnch, pnch, pNp, 0, pNp, true);
+                            ok = product(tmem + (uint32_t)a * cfg.acc_cols, pnch, pnch, pNp, 0, pNp, true, pL);
                         }
                         if (ok) {
                             mma_commit(b_afull + 8 * a);
@@ -883,6 +895,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         pending = true;
                         pnch = nch;
                         pNp = Np;
+                        pL = L;
                     }
                     if (!more && !pending) break;
                 }
@@ -895,7 +908,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 const int a = ar.slot;
                 if (!mbar_wait_ab(b_aempty + 8 * a, ar.phase ^ 1u, abort)) break;
                 fence_after();
-                if (!product(tmem + (uint32_t)a * cfg.acc_cols, 0, s.nch, s.Np, n0, nN, false)) break;
+                if (!product(tmem + (uint32_t)a * cfg.acc_cols, 0, s.nch, s.Np, n0, nN, false, s.L)) break;
                 mma_commit(b_afull + 8 * a);
                 ar.next(cfg.nacc);
             }

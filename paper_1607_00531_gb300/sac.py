@@ -165,11 +165,12 @@ def _torch():
 
 
 def zstep_fused(g, p):
-    """Whether the z-step runs passes 1 and 2 as one launch (host only)."""
+    """How the z-step is launched (host only): 2 on the chip in one launch per
+    iteration, 1 with passes 1 and 2 as one launch, 0 pass by pass."""
     r = int(lib().sac_zstep_fused(ctypes.byref(g), ctypes.byref(p)))
     if r < 0:
         raise SacError("sac_zstep_fused", r)
-    return bool(r)
+    return r
 
 
 def workspace(g, p, device="cuda"):
@@ -367,7 +368,7 @@ def gnpcg_solve(g, p, I1, I2, b, want_hist=False, ws=None, stream=None):
     return res
 
 
-PHASES = ["bstep", "bstep_refine", "zpass0", "zpass1", "zpass2", "zpass3", "admm_update"]
+PHASES = ["bstep", "bstep_refine", "zpass0", "zpass1", "zpass2", "zpass3", "admm_update", "zslab"]
 
 
 def profile_enable(on=True):

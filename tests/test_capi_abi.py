@@ -54,17 +54,26 @@ def test_entry_points_reject_null_arrays(L):
 
 
 def test_zstep_fusion_decision_needs_no_device(L):
-    # passes 1 and 2 run as one launch when both DCT matrices of the second
-    # non-PE axis fit beside the rings (axes up to 96 faces), only on the
-    # tensor-core path of the mixed precision
-    def fused(m, pe, prec):
+    # 2: the whole z-step on the chip (3D, last axis not the PE axis, at most
+    # 256 faces along the first non-PE axis and 128 along the last; mixed
+    # precision, zstep_kernel 0); 1: passes 1 and 2 as one launch when both
+    # DCT matrices of the second non-PE axis fit beside the rings (axes up to
+    # 96 faces); 0: pass by pass
+    def fused(m, pe, prec, kern=0):
         g = sac.grid(m, tuple(1.0 / x for x in m), pe)
-        return sac.zstep_fused(g, sac.params(prec=prec))
-    assert fused((256, 256, 80), 1, "mixed")
-    assert fused((64, 60, 96), 1, "mixed")
-    assert not fused((64, 60, 112), 1, "mixed")
-    assert not fused((64, 60, 128), 1, "mixed")
-    assert not fused((256, 256, 80), 1, "f64")
-    assert not fused((128, 128), 1, "mixed")          # 2D: no second axis to fuse
+        return sac.zstep_fused(g, sac.params(prec=prec, zstep_kernel=kern))
+    assert fused((256, 256, 80), 1, "mixed") == 2
+    assert fused((64, 60, 128), 1, "mixed") == 2
+    assert fused((60, 64, 128), 0, "mixed") == 2
+    assert fused((300, 9, 8), 1, "mixed") != 2         # 301 faces along the first non-PE axis
+    assert fused((8, 9, 130), 1, "mixed") != 2         # 130 along the last
+    assert fused((64, 60, 96), 2, "mixed") == 1        # PE last: per-axis passes, 1 + 2 fused
+    assert fused((256, 256, 80), 1, "mixed", 2) == 1
+    assert fused((64, 60, 96), 1, "mixed", 2) == 1
+    assert fused((64, 60, 112), 1, "mixed", 2) == 0
+    assert fused((64, 60, 128), 1, "mixed", 2) == 0
+    assert fused((256, 256, 80), 1, "mixed", 1) == 0
+    assert fused((256, 256, 80), 1, "f64") == 0
+    assert fused((128, 128), 1, "mixed") == 0          # 2D: no second axis to fuse
     with pytest.raises(sac.SacError):
         sac.zstep_fused(sac.grid((16, 12), (0.1, 0.1), 2), sac.params())
