@@ -112,11 +112,13 @@ typedef struct {
     int zstep_kernel;    /* SAC_MIXED z-step: 0 tensor cores -- on 3D grids whose
                             last axis is not the PE axis, with at most 256
                             faces along the first non-PE axis and 128 along
-                            the last, one on-chip launch per iteration (all
-                            four DCT contractions, the scaling and the dual
-                            update, split FP16); otherwise per-axis passes
-                            (split TF32) where the grid allows, else SIMT;
-                            1 SIMT FP32; 2 tensor cores, per-axis passes only */
+                            the last, and slabs of at least 8192 faces, one
+                            on-chip launch per iteration
+                            (all four DCT contractions, the scaling and the
+                            dual update, split FP16); otherwise per-axis
+                            passes (split TF32) where the grid allows, else
+                            SIMT; 1 SIMT FP32; 2 tensor cores, per-axis passes
+                            only; 3 as 0, on the chip for slabs of any size */
     int autotune;        /* batched runs: 1 = pick the b-step tile width on the
                             first live iterations (results do not depend on it) */
     int bstep_kernel;    /* SAC_MIXED b-step with n_sqp = 1: 0 one thread per

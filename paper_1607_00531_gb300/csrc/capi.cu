@@ -156,7 +156,7 @@ int check_params(const sac_params* p) {
     if (p->precond < 0 || p->precond > 2) return SAC_EINVAL;
     if (p->prec != SAC_F64 && p->prec != SAC_MIXED) return SAC_EINVAL;
     if (!(p->near_bound >= 0)) return SAC_EINVAL;
-    if (p->zstep_kernel < 0 || p->zstep_kernel > 2) return SAC_EINVAL;
+    if (p->zstep_kernel < 0 || p->zstep_kernel > 3) return SAC_EINVAL;
     if (p->bstep_kernel < 0 || p->bstep_kernel > 1) return SAC_EINVAL;
     if (p->adapt_rho < 0 || p->adapt_rho > 2) return SAC_EINVAL;
     if (p->adapt_rho && (!(p->rho_tau > 1.0) || !(p->rho_mu > 0.0) || !(p->rho_min > 0.0))) return SAC_EINVAL;
@@ -228,7 +228,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
         }
     }
     // the whole z-step and dual update on the chip, one PE slab at a time
-    P->use_zs = (p->prec == SAC_MIXED && p->zstep_kernel == 0 && zs_supported(G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
+    P->use_zs = (p->prec == SAC_MIXED && zs_preferred(p->zstep_kernel, G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
     if (P->use_zs) {
         P->zs_cfg = ZsCfg();
         zs_cfg_add(&P->zs_cfg, G.F, G.pe, G.ax1);

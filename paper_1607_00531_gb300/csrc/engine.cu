@@ -205,8 +205,8 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     zs_job_.assign(nj, 0);
     for (size_t i = 0; i < nj; ++i) {
         const Geometry& G = jobs_[i].G;
-        zs_job_[i] = (use_tc_ && prec == SAC_MIXED && p.zstep_kernel == 0 &&
-                      zs_supported(G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
+        zs_job_[i] = (use_tc_ && prec == SAC_MIXED && zs_preferred(p.zstep_kernel, G.nd, G.F, G.pe, G.ax1, G.ax2))
+                         ? 1 : 0;
     }
     d_stats_ = (double*)take(sizeof(double) * 8 * nj);
     // classes
@@ -498,7 +498,11 @@ int Engine::enqueue_iteration(int slot) {
     }
     const int nj = (int)jobs_.size();
     for (int q = 0; q < 4; ++q) {
-        prof_mark(slot, 2 + q, 0);
+        // (phases that launch nothing, e.g. with every job on the chip, get no marks)
+        bool any = !use_tc_ && ax_tiles_[q] > 0;
+        for (int gr = 0; use_tc_ && gr < ngeo_; ++gr) any = any || ztiles_[q * ngeo_ + gr] > 0;
+        const int pslot = any ? slot : -1;
+        prof_mark(pslot, 2 + q, 0);
         AxisLaunch A;
         A.jobs = d_jobs_;
         A.njobs = nj;
@@ -522,9 +526,10 @@ int Engine::enqueue_iteration(int slot) {
             A.total_tiles = ax_tiles_[q];
             ENG_CUDA(launch_axis_pass(A));
         }
-        prof_mark(slot, 2 + q, 1);
+        prof_mark(pslot, 2 + q, 1);
     }
-    prof_mark(slot, 6, 0);
+    const int uslot = (use_tc_ && admm_blocks_ == 0) ? -1 : slot;
+    prof_mark(uslot, 6, 0);
     if (use_tc_) {
         // z^{k+1} is in t2: ADMM update, residual sums and (in the last block
         // of each job) the stopping test, element-wise
@@ -537,7 +542,7 @@ int Engine::enqueue_iteration(int slot) {
         k_admm_check<<<nj, 256, 0, st_>>>(d_jobs_, nj, d_pref_ax_[3], d_part_, chk);
         ENG_CUDA(cudaGetLastError());
     }
-    prof_mark(slot, 6, 1);
+    prof_mark(uslot, 6, 1);
     if (zs_total_ > 0) {
         // on-chip z-step jobs: the contractions, the scaling, the dual update
         // and (the CTA finishing a job's last slab) the stopping test

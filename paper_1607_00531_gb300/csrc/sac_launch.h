@@ -127,6 +127,9 @@ struct ZsCfg {
     size_t smem = 0;                    // dynamic shared memory per CTA
 };
 bool zs_supported(int nd, const int F[3], int pe, int ax1, int ax2);
+// the z-step kernel choice (sac_params::zstep_kernel) takes the on-chip
+// kernel for this grid: 3 wherever supported, 0 for slabs of at least 8192 faces
+bool zs_preferred(int kernel, int nd, const int F[3], int pe, int ax1, int ax2);
 long long zs_slabs(const int F[3], int pe);
 long long zs_matrix_bytes(const int F[3], int pe, int ax1);
 void zs_cfg_add(ZsCfg* c, const int F[3], int pe, int ax1);

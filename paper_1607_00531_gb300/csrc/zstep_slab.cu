@@ -111,6 +111,19 @@ bool zs_supported(int nd, const int F[3], int pe, int ax1, int ax2) {
     return zs_smem_for(g.N1, g.N2, 3) <= zs::kMaxSmem;
 }
 
+// The on-chip kernel takes one slab per CTA at a time: its time per slab is
+// mostly the latency of the dependent phases, so small slabs go faster
+// through the per-axis passes.  Measured on GB300 (ADMM engine, us per
+// iteration of the z-step and dual update, on-chip / per-axis): 256 x 80
+// slabs 98 / 136, 128 x 64: 38 / 69, 96 x 60 (8 volumes): 132 / 114.
+constexpr long long kZsMinSlabFaces = 8192;
+bool zs_preferred(int kernel, int nd, const int F[3], int pe, int ax1, int ax2) {
+    if (kernel != 0 && kernel != 3) return false;
+    if (!zs_supported(nd, F, pe, ax1, ax2)) return false;
+    const ZsGeo g = zs_geo(F, pe, ax1);
+    return kernel == 3 || (long long)g.n1 * g.n2 >= kZsMinSlabFaces;
+}
+
 long long zs_slabs(const int F[3], int pe) { return F[pe]; }
 
 // operand chunks of a job: [C2 for A][C1 for B][C1 for B'][C2 for A']

@@ -56,7 +56,7 @@ def test_entry_points_reject_null_arrays(L):
 def test_zstep_fusion_decision_needs_no_device(L):
     # 2: the whole z-step on the chip (3D, last axis not the PE axis, at most
     # 256 faces along the first non-PE axis and 128 along the last; mixed
-    # precision, zstep_kernel 0); 1: passes 1 and 2 as one launch when both
+    # precision, zstep_kernel 0 for slabs of at least 8192 faces, 3 for any); 1: passes 1 and 2 as one launch when both
     # DCT matrices of the second non-PE axis fit beside the rings (axes up to
     # 96 faces); 0: pass by pass
     def fused(m, pe, prec, kern=0):
@@ -68,6 +68,8 @@ def test_zstep_fusion_decision_needs_no_device(L):
     assert fused((300, 9, 8), 1, "mixed") != 2         # 301 faces along the first non-PE axis
     assert fused((8, 9, 130), 1, "mixed") != 2         # 130 along the last
     assert fused((64, 60, 96), 2, "mixed") == 1        # PE last: per-axis passes, 1 + 2 fused
+    assert fused((96, 96, 60), 1, "mixed") == 1        # 96 x 60 slabs: below 8192 faces, per-axis
+    assert fused((96, 96, 60), 1, "mixed", 3) == 2     # ... on the chip when asked for
     assert fused((256, 256, 80), 1, "mixed", 2) == 1
     assert fused((64, 60, 96), 1, "mixed", 2) == 1
     assert fused((64, 60, 112), 1, "mixed", 2) == 0

@@ -36,12 +36,15 @@ def cu(a, dt):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
 
 
-@pytest.mark.parametrize("prec", ["mixed", "f64"])
-def test_batch_equals_solo(sac, prec):
+# zstep_kernel 3: the 3D volumes whose last axis is not the PE axis take the
+# on-chip z-step (in the engine with the stopping test fused) whatever their size
+@pytest.mark.parametrize("prec,kern", [("mixed", 0), ("mixed", 3), ("f64", 0)])
+def test_batch_equals_solo(sac, prec, kern):
     K = 12
     vols = volumes()
     dt = torch.float32 if prec == "mixed" else torch.float64
-    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, check_every=K)
+    p = sac.params(alpha=1.0, rho=100.0, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, check_every=K,
+                   zstep_kernel=kern)
     grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
     I1s = [cu(d["I1"], dt) for d in vols]
     I2s = [cu(d["I2"], dt) for d in vols]
@@ -59,14 +62,15 @@ def test_batch_equals_solo(sac, prec):
         assert diff <= 1e-12 * max(b.abs().max().item(), 1e-30), diff
 
 
-@pytest.mark.parametrize("prec", ["mixed", "f64"])
-def test_batch_adaptive_rho_equals_solo(sac, prec):
+@pytest.mark.parametrize("prec,kern", [("mixed", 0), ("mixed", 3), ("f64", 0)])
+def test_batch_adaptive_rho_equals_solo(sac, prec, kern):
     # the batched engine applies the adaptive rule on the device, in the
     # stopping test of each volume; the single-volume call on the host
     K = 12
     vols = volumes()[:4]
     dt = torch.float32 if prec == "mixed" else torch.float64
-    p = sac.params(alpha=1.0, rho=1e6, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, adapt_rho=2, rho_min=2e4)
+    p = sac.params(alpha=1.0, rho=1e6, max_iter=K, eps_abs=0.0, eps_rel=0.0, prec=prec, adapt_rho=2, rho_min=2e4,
+                   zstep_kernel=kern)
     grids = [sac.grid(d["m"], d["h"], d["pe"]) for d in vols]
     I1s = [cu(d["I1"], dt) for d in vols]
     I2s = [cu(d["I2"], dt) for d in vols]

@@ -461,7 +461,7 @@ TC_CASES = [
     ((80, 255, 24), 1),     # more tiles than SMs on the last axis (20480 lines)
     ((6, 10, 200), 1),      # contiguous axis of 200 faces: one tile as two column halves
     ((136, 150, 130), 1),   # 154 and 161 tiles: full tiles, then the last round as column halves
-    # on-chip z-step (one PE slab per CTA at a time; zstep_kernel 0 below)
+    # on-chip z-step (one PE slab per CTA at a time; zstep_kernel 3 below)
     ((256, 9, 80), 1),      # full slab width: 256 x 80 (N = 256, K = 80)
     ((30, 16, 128), 0),     # PE first, 128 faces along the last axis
     ((40, 300, 12), 1),     # 301 slabs: several per CTA; K padded from 12 to 16
@@ -489,7 +489,7 @@ def test_zstep_mixed_tensor_cores(sac, m, pe):
     u32 = u.astype(np.float32).astype(np.float64)
     z_ref32 = oracle.zstep(og, op, b32, u32)
     outs = {}
-    for kern in (0, 1, 2):
+    for kern in (0, 1, 2, 3):
         p = sac.params(alpha=2.0, rho=50.0, prec="mixed", zstep_kernel=kern)
         zt = cu(z)
         u_out, nr = sac.zstep(g, p, cu(b), cu(u), zt)
@@ -500,6 +500,7 @@ def test_zstep_mixed_tensor_cores(sac, m, pe):
         np.testing.assert_allclose(nr[:3], ref, rtol=1e-4)
     assert rel(outs[0], outs[1]) < TC_TOL
     assert rel(outs[2], outs[1]) < TC_TOL
+    assert rel(outs[3], outs[1]) < TC_TOL
     assert rel(outs[0], z_ref) < 2 * TC_TOL
 
 
