@@ -228,7 +228,8 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
         }
     }
     // the whole z-step and dual update on the chip, one PE slab at a time
-    P->use_zs = (p->prec == SAC_MIXED && zs_preferred(p->zstep_kernel, G.nd, G.F, G.pe, G.ax1, G.ax2)) ? 1 : 0;
+    P->use_zs = (p->prec == SAC_MIXED && zs_preferred(p->zstep_kernel, G.nd, G.F, G.pe, G.ax1, G.ax2) &&
+                 (p->zstep_kernel == 3 || zs_slabs(G.F, G.pe) <= zs_slab_budget())) ? 1 : 0;
     if (P->use_zs) {
         P->zs_cfg = ZsCfg();
         zs_cfg_add(&P->zs_cfg, G.F, G.pe, G.ax1);

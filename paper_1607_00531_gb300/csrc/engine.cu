@@ -208,6 +208,14 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         zs_job_[i] = (use_tc_ && prec == SAC_MIXED && zs_preferred(p.zstep_kernel, G.nd, G.F, G.pe, G.ax1, G.ax2))
                          ? 1 : 0;
     }
+    {
+        // automatic choice: on the chip only while the launch has at most
+        // two slabs per SM (all the jobs' slabs together)
+        long long zsl = 0;
+        for (size_t i = 0; i < nj; ++i)
+            if (zs_job_[i]) zsl += zs_slabs(jobs_[i].G.F, jobs_[i].G.pe);
+        if (p.zstep_kernel != 3 && zsl > zs_slab_budget()) zs_job_.assign(nj, 0);
+    }
     d_stats_ = (double*)take(sizeof(double) * 8 * nj);
     // classes
     std::vector<long long> hpref((nj + 1) * (4 + 8 + 8), 0);

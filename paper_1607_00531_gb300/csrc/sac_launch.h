@@ -130,6 +130,9 @@ bool zs_supported(int nd, const int F[3], int pe, int ax1, int ax2);
 // the z-step kernel choice (sac_params::zstep_kernel) takes the on-chip
 // kernel for this grid: 3 wherever supported, 0 for slabs of at least 8192 faces
 bool zs_preferred(int kernel, int nd, const int F[3], int pe, int ax1, int ax2);
+// slabs of one on-chip launch up to which kernel 0 keeps it (two per SM;
+// beyond, the per-axis passes are as fast or faster)
+long long zs_slab_budget();
 long long zs_slabs(const int F[3], int pe);
 long long zs_matrix_bytes(const int F[3], int pe, int ax1);
 void zs_cfg_add(ZsCfg* c, const int F[3], int pe, int ax1);

@@ -112,10 +112,13 @@ bool zs_supported(int nd, const int F[3], int pe, int ax1, int ax2) {
 }
 
 // The on-chip kernel takes one slab per CTA at a time: its time per slab is
-// mostly the latency of the dependent phases, so small slabs go faster
-// through the per-axis passes.  Measured on GB300 (ADMM engine, us per
-// iteration of the z-step and dual update, on-chip / per-axis): 256 x 80
-// slabs 98 / 136, 128 x 64: 38 / 69, 96 x 60 (8 volumes): 132 / 114.
+// mostly the latency of the dependent phases, so small slabs, and launches
+// of many slabs per SM, go faster through the per-axis passes.  Measured on
+// GB300 (ADMM engine, us per iteration of the z-step and dual update,
+// on-chip / per-axis): one 256 x 256 x 80 volume (257 slabs of 256 x 80) 98 /
+// 136, one 128 x 128 x 64 (129 of 128 x 64) 38 / 69; 96 x 60 slabs (eight
+// volumes) 132 / 114; whole iterations with two volumes of either size
+// equal, with four 128 x 64 volumes (516 slabs) 0.169 / 0.150 ms.
 constexpr long long kZsMinSlabFaces = 8192;
 bool zs_preferred(int kernel, int nd, const int F[3], int pe, int ax1, int ax2) {
     if (kernel != 0 && kernel != 3) return false;
@@ -125,6 +128,18 @@ bool zs_preferred(int kernel, int nd, const int F[3], int pe, int ax1, int ax2) 
 }
 
 long long zs_slabs(const int F[3], int pe) { return F[pe]; }
+
+long long zs_slab_budget() {
+    static const long long n = [] {
+        int d = 0, v = 0;
+        if (cudaGetDevice(&d) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) == cudaSuccess &&
+            v > 0)
+            return 2LL * v;
+        cudaGetLastError();
+        return 2LL * 152;
+    }();
+    return n;
+}
 
 // operand chunks of a job: [C2 for A][C1 for B][C1 for B'][C2 for A']
 __host__ __device__ inline long long zs_off_b(int N2) { return (long long)(N2 / 16) * zs::kC2Chunk; }

@@ -94,3 +94,32 @@ def test_bounded_wait_that_gives_up_returns_etimeout(sac):
         sac.set_wait_limit(sac.WAIT_BSTEP | sac.WAIT_ZSTEP, -1)
     out, _ = sac.bstep(g, p, *args)
     assert torch.equal(out, ref)
+
+
+def test_onchip_zstep_wait_that_gives_up_returns_etimeout(sac):
+    # the on-chip z-step's roles hand slabs to each other through mbarriers
+    # (DCT ring, operands in shared and tensor memory, converter syncs); with
+    # the wait limit at zero the first wait gives up, the roles leave their
+    # loops, the MMAs and copies in flight are drained and the call reports
+    # the timeout; with the default limit the same call gives the same z
+    m, pe = (40, 9, 24), 1
+    rng = np.random.default_rng(3)
+    shape = tuple(x + (a == pe) for a, x in enumerate(m))
+    h = (1.0 / 40, 1.0 / 9, 1.0 / 24)
+    b = 0.01 * rng.normal(size=shape)
+    u = 0.001 * rng.normal(size=shape)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=2.0, rho=50.0, prec="mixed", zstep_kernel=3)
+    assert sac.zstep_fused(g, p) == 2
+    z_ref = cu(np.zeros(shape))
+    sac.zstep(g, p, cu(b), cu(u), z_ref)
+    try:
+        sac.set_wait_limit(sac.WAIT_ZSTEP, 0)
+        with pytest.raises(sac.SacError) as e:
+            sac.zstep(g, p, cu(b), cu(u), cu(np.zeros(shape)))
+        assert e.value.status == sac.SAC_ETIMEOUT
+    finally:
+        sac.set_wait_limit(sac.WAIT_BSTEP | sac.WAIT_ZSTEP, -1)
+    z = cu(np.zeros(shape))
+    sac.zstep(g, p, cu(b), cu(u), z)
+    assert torch.equal(z, z_ref)
