@@ -504,6 +504,32 @@ def test_zstep_mixed_tensor_cores(sac, m, pe):
     assert rel(outs[0], z_ref) < 2 * TC_TOL
 
 
+@pytest.mark.parametrize("scale", [1e-12, 1e-3, 1e6, 1e18])
+def test_onchip_zstep_scaling_across_magnitudes(sac, scale):
+    # the on-chip z-step scales its split-FP16 operands by powers of two from
+    # each row's and the slab's maximum: the same relative accuracy for inputs
+    # far from unit size, and for a slab whose rows differ by 1e8 in magnitude
+    m, pe = (64, 5, 48), 1
+    h, _, _, b, z, u = case_data(m, pe, seed=60)
+    b = b * scale
+    u = u * scale
+    b[:, 2, :] *= 1e-8            # one slab much smaller than the others
+    b[5, :, :] *= 1e4             # one row of every slab much larger
+    og = oracle.Grid(m, h, pe)
+    b32 = b.astype(np.float32).astype(np.float64)
+    u32 = u.astype(np.float32).astype(np.float64)
+    z_ref32 = oracle.zstep(og, oracle.Params(alpha=2.0, rho=50.0), b32, u32)
+    g = sac.grid(m, h, pe)
+    p = sac.params(alpha=2.0, rho=50.0, prec="mixed", zstep_kernel=3)
+    assert sac.zstep_fused(g, p) == 2
+    zt = cu(z)
+    sac.zstep(g, p, cu(b), cu(u), zt)
+    out = zt.cpu().numpy()
+    assert rel(out, z_ref32) < TC_TOL, rel(out, z_ref32)
+    # the small slab relative to its own size
+    assert rel(out[:, 2, :], z_ref32[:, 2, :]) < TC_TOL, rel(out[:, 2, :], z_ref32[:, 2, :])
+
+
 # ---------------------------------------------------------------- the benchmark's volume
 
 def test_full_size_bstep_matches_the_oracle(sac):
