@@ -467,6 +467,9 @@ TC_CASES = [
     ((40, 300, 12), 1),     # 301 slabs: several per CTA; K padded from 12 to 16
     ((200, 3, 37), 1),      # last axis of 37 faces: element-wise loads and stores
     ((17, 5, 6), 0),        # both slab axes padded (17 -> 32, 6 -> 16)
+    ((2, 5, 3), 1),         # the smallest slabs: 2 x 3 faces
+    ((3, 2, 2), 0),         # 2 x 2 faces, PE first
+    ((128, 3, 128), 1),     # 128 x 128 slabs: the widest last axis
 ]
 
 
