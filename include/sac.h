@@ -113,8 +113,8 @@ typedef struct {
                             last axis is not the PE axis, with at most 256
                             faces along the first non-PE axis and 128 along
                             the last, slabs of at least 8192 faces and at
-                            most two slabs per SM in all, one on-chip launch
-                            per iteration
+                            most two slabs per SM in all (in a batch: every
+                            volume so), one on-chip launch per iteration
                             (all four DCT contractions, the scaling and the
                             dual update, split FP16); otherwise per-axis
                             passes (split TF32) where the grid allows, else

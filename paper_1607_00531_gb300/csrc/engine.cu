@@ -210,11 +210,16 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
     }
     {
         // automatic choice: on the chip only while the launch has at most
-        // two slabs per SM (all the jobs' slabs together)
+        // two slabs per SM (all the jobs' slabs together), and only when
+        // every job of the batch goes there (a mixed batch would run both
+        // kernel sets back to back every iteration)
         long long zsl = 0;
-        for (size_t i = 0; i < nj; ++i)
+        bool all = true;
+        for (size_t i = 0; i < nj; ++i) {
             if (zs_job_[i]) zsl += zs_slabs(jobs_[i].G.F, jobs_[i].G.pe);
-        if (p.zstep_kernel != 3 && zsl > zs_slab_budget()) zs_job_.assign(nj, 0);
+            else all = false;
+        }
+        if (p.zstep_kernel != 3 && (zsl > zs_slab_budget() || !all)) zs_job_.assign(nj, 0);
     }
     d_stats_ = (double*)take(sizeof(double) * 8 * nj);
     // classes
