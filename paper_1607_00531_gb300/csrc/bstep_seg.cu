@@ -17,7 +17,9 @@
 // the rest of the tile (reduced solve, back substitution, bound tests,
 // write-back) instead of in a burst with no arithmetic beside it.  (8 lines
 // per CTA and four CTAs per SM measured no faster: the warp holding the
-// boundary segments then covers a quarter of the CTA.)
+// boundary segments then covers a quarter of the CTA.  Nor did 8 lines of up
+// to 32 segments of 9 faces, three CTAs per SM at 80 registers: 63 us
+// against 49 us for lines of 257 faces, the same for lines of 129.)
 //
 // Per line the step is the first pass of the active-set method with an empty
 // working set (the unconstrained Gauss-Newton step of the b-subproblem):
