@@ -169,7 +169,8 @@ int sac_objective(const sac_grid* g, const sac_params* p, const void* I1, const 
    exits.  Grids whose scratch would not fit (about 4 doubles per 8 PE lines
    plus 1 double per 256 faces) are rejected with SAC_ENOMEM before any GPU
    work.  The first call on a device looks up the array's device address and
-   caches it: make that first call before any stream capture.  All calls
+   caches it (and looks it up again after cudaDeviceReset): make that first
+   call before any stream capture.  All calls
    share the array and it keeps the last call's contents; the status words
    are cleared at the start of every call, and calls that overlap on the GPU
    (on different streams or from several threads) race on the array.  No

@@ -7,10 +7,13 @@
 // library holds it until the process exits.  Host code must not use the
 // array's name as a device address (in host code it names a host-side
 // stand-in); the device address is looked up once per device with
-// cudaGetSymbolAddress, on that device's first call, and cached.  Every call
+// cudaGetSymbolAddress, on that device's first call, and cached (looked up
+// again if the device's context has changed since: after cudaDeviceReset).  Every call
 // shares the array: the status words are cleared at the start of each call,
 // and calls whose work overlaps on the GPU (different streams, or several
 // host threads) race on it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
 
@@ -29,6 +32,26 @@ namespace {
 std::mutex g_na_mu;
 constexpr int kMaxDevices = 64;
 void* g_na_ptr[kMaxDevices] = {nullptr};
+void* g_na_ctx[kMaxDevices] = {nullptr};   // the context the address belongs to
+
+// the calling thread's current context (cuCtxGetCurrent, fetched from the
+// driver at run time); null when unavailable
+void* current_context() {
+    static std::once_flag once;
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuCtxGetCurrent_v4000)f;
+        else
+            cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+    return (void*)c;
+}
 
 int scratch_address(void** out) {
     int dev = 0;
@@ -36,14 +59,18 @@ int scratch_address(void** out) {
         cudaGetLastError();
         return SAC_ECUDA;
     }
+    // (after cudaDeviceReset the device gets a new context, in which the
+    // array has a new address: looked up again then)
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    if (!g_na_ptr[dev] || ctx != g_na_ctx[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return SAC_ECUDA;
         }
         g_na_ptr[dev] = p;
+        g_na_ctx[dev] = current_context();   // (the lookup made the context current if it was not)
     }
     *out = g_na_ptr[dev];
     return SAC_OK;
