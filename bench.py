@@ -599,8 +599,44 @@ def main():
     btf.run(2, chunk=2)
     btf.run(kf, chunk=kf)
     f64_ms = btf.last_run_ms()
+    # the FP64 path's z-step passes (SIMT FP64 DCT contractions) against the
+    # GPU's FP64 rate, measured here as a cuBLAS DGEMM (4096^3, best of 3)
+    sac.profile_enable(True)
+    sac.profile_read(reset=True)
+    btf.run(kf, chunk=kf)
+    prof64 = sac.profile_read(reset=True)
+    sac.profile_enable(False)
     btf.close()
     f64_val = nf * kf / (f64_ms / 1e3)
+    f64_detail = {}
+    try:
+        import torch
+        A = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        B = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(A, B)
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(A, B)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        dgemm = 2 * 4096 ** 3 / (best / 1e3) / 1e12
+        del A, B
+        Fs = sac.face_shape(g)
+        ax = [a for a in range(3) if a != w.pe]
+        Ls = [Fs[ax[0]], Fs[ax[1]], Fs[ax[1]], Fs[ax[0]]]
+        passes = {}
+        for q in range(4):
+            ms_q, n_q = prof64.get(f"zpass{q}", (0.0, 0))
+            if n_q:
+                tf = 2 * Ls[q] * nf / (ms_q / n_q / 1e3) / 1e12
+                passes[f"zpass{q}"] = {"us": ms_q / n_q * 1e3, "tflops": tf, "frac_of_dgemm": tf / dgemm}
+        f64_detail = {"fp64_dgemm_tflops": dgemm, "zstep_passes": passes,
+                      "note": "SIMT FP64 DCT contractions (2 L flop per face per pass) against a measured cuBLAS DGEMM"}
+    except Exception as ex:   # reported, not fatal
+        f64_detail = {"error": str(ex)[:200]}
 
     # end to end through the single-volume public call (sac_admm_solve) with
     # host buffers: H2D inputs, K iterations (set-up of the DCT tables
@@ -750,7 +786,7 @@ def main():
                 "gpu_launches": launches, "clocks": clocks,
                 "profiled_run_ms_per_step": t_prof_ms / args.steps,
                 "f64_path": {"value": f64_val, "unit": UNIT, "iterations": kf,
-                             "mixed_over_f64": value / world / f64_val},
+                             "mixed_over_f64": value / world / f64_val, **f64_detail},
                 "time_to_solution": tts,
                 "gnpcg_preconditioners": pcg,
                 "serving": serving,
