@@ -271,7 +271,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     size_t o_tn[4];
     for (int q = 0; q < 4; ++q) o_tn[q] = take(sizeof(float) * (size_t)(P->use_tc ? P->tn_floats[q] : 0));
     size_t o_zs = take((size_t)P->zs_bytes);
-    const bool maps = P->use_tc || P->seg_S > 0;   // TMA tensor maps of the z-step passes / the b-step
+    const bool maps = P->use_tc || P->seg_S > 0 || P->use_zs;   // TMA tensor maps of the z-step / the b-step
     size_t o_tmap = take(maps ? tc_map_bytes() : 0);
     size_t o_arr[10];
     for (int i = 0; i < 10; ++i) o_arr[i] = take(sizeof(double) * (size_t)G.nf);
@@ -339,9 +339,10 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     J.active = 1;
     const bool tc_maps = P->use_tc && P->d_tmaps && b && u && t1 && t2;
     const bool seg_maps = P->seg_S > 0 && P->d_tmaps && I1 && I2 && b && z && u;
-    if (tc_maps || seg_maps) {
+    const bool zs_maps = P->use_zs && P->d_tmaps && b && z && u;
+    if (tc_maps || seg_maps || zs_maps) {
         // TMA tensor maps: X sources and outputs of the tensor-core passes,
-        // the b-step's staging copies
+        // the b-step's staging copies, the on-chip z-step's rows
         std::vector<unsigned char> maps(tc_map_bytes(), 0);
         J.tmaps = P->d_tmaps;
         if (tc_maps)
@@ -350,6 +351,8 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
         if (seg_maps)
             J.seg_tma = seg_encode_maps(G.n_outer, G.mpe, G.n_inner, (const float*)I1, (const float*)I2,
                                         (const float*)b, (const float*)z, (const float*)u, maps.data());
+        if (zs_maps)
+            J.zs_tma = zs_encode_maps(G.F, G.pe, G.ax1, (const float*)b, (const float*)u, (const float*)z, maps.data());
         SAC_CUDA(cudaMemcpyAsync(P->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
     }
     long long pref[26] = {0, P->line_tiles, 0, P->pass_tiles[0], 0, P->pass_tiles[1], 0, P->pass_tiles[2],

@@ -389,6 +389,9 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
             if (prec == SAC_MIXED)
                 J.seg_tma = seg_encode_maps(G.n_outer, G.mpe, G.n_inner, (const float*)J.I1, (const float*)J.I2,
                                             (const float*)J.b, (const float*)J.z, (const float*)J.u, maps.data());
+            if (zs_job_[i])
+                J.zs_tma = zs_encode_maps(G.F, G.pe, G.ax1, (const float*)J.b, (const float*)J.u, (const float*)J.z,
+                                          maps.data());
             ENG_CUDA(cudaMemcpyAsync(s + L.tmap, maps.data(), maps.size(), cudaMemcpyHostToDevice, st));
         }
         J.part = d_part_;

@@ -51,7 +51,7 @@ struct Job {
     const float* scale;  // [k1][k2] = rho / (alpha (lam1[k1] + lam2[k2]) + rho), FP32
     double* part;      // per-block partial sums of this job
     int active;        // 0: tiles of this job return at once
-    int pad_;
+    int zs_tma;        // 1: the on-chip z-step stages b, u, z rows with its tensor maps (zstep_slab.cu)
     int tc_T[4];       // tensor-core z-step: lines per tile of each pass
     const void* tmaps; // TMA tensor maps: tensor-core z-step X sources [pass][source], outputs [pass]; b-step rows
     int tc_tma;        // bit q: pass q loads X with the tensor maps; bit 4 + q: pass q stores with one

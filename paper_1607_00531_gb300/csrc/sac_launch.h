@@ -140,6 +140,11 @@ bool zs_cfg_finish(ZsCfg* c);
 // Host: a job's split FP16 DCT operands (zs_matrix_bytes bytes) from its
 // orthonormal DCT-II matrices C1 (along ax1) and C2 (along the last axis)
 void zs_arrange(const int F[3], int pe, int ax1, const double* C1, const double* C2, unsigned char* out);
+// Host: the row maps of the on-chip z-step (FP32 face arrays b, u, z of one
+// job) into `maps` (the job's tc_map_bytes() bytes, host memory); returns 1
+// when all three are encoded (rows a multiple of 16 bytes, arrays 16-byte
+// aligned), else 0 and the kernel loads the rows through registers
+int zs_encode_maps(const int F[3], int pe, int ax1, const float* b, const float* u, const float* z, void* maps);
 cudaError_t prepare_zslab();
 // prefix[j]: first slab of job j.  part: 5 partial sums per slab, FP64
 // (norms != 0, chk null or without counters), or FP32 with the fused
@@ -194,9 +199,11 @@ struct TcCfg {
     size_t smem = 0;                 // dynamic shared memory per CTA
 };
 // TMA tensor maps per job: [pass][source] X sources and [pass] outputs of the
-// tensor-core z-step, then the five staging maps of the segment b-step
-constexpr int kTcMaps = 17;
+// tensor-core z-step, the five staging maps of the segment b-step, then the
+// three row maps (b, u, z) of the on-chip z-step
+constexpr int kTcMaps = 20;
 constexpr int kSegMap0 = 12;
+constexpr int kZsMap0 = 17;
 size_t tc_map_bytes();
 // cuTensorMapEncodeTiled from the driver (null if unavailable)
 void* tensor_map_encoder();

@@ -40,7 +40,9 @@
 //   warps 0-11  loads of x (the next slab, while the tensor pipe works on
 //               this one), the conversions between contractions, the
 //               epilogue; warp w reaches TMEM lanes 32 (w % 4) .. + 31 and
-//               takes the 16-column chunks c = w / 4 (mod 3)
+//               takes the 16-column chunks c = w / 4 (mod 3).  The dual
+//               update reads b, u, z^k through TMA tensor copies of row
+//               pieces into the free B_X region (two pieces in flight)
 //   warp 12     TMEM owner; one thread issues the MMAs
 //   warp 13     one thread streams the DCT chunks (16 K values each, hi |
 //               lo) into a 3- or 4-stage shared-memory ring
@@ -52,6 +54,8 @@
 // Every wait is bounded; a wait that gives up raises the CTA's abort flag,
 // the roles leave their loops, MMAs and copies in flight are drained, TMEM
 // is freed and the status word gets kStTimeout.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <string.h>
 
@@ -97,6 +101,26 @@ __host__ __device__ inline ZsGeo zs_geo(const int F[3], int pe, int ax1) {
     g.si = (ax1 == 0) ? (long long)F[1] * F[2] : (long long)F[2];
     g.ss = (pe == 0) ? (long long)F[1] * F[2] : (long long)F[2];
     return g;
+}
+
+// Staging of the rows of b, u and z of one slab for its dual update: pieces
+// of P rows, each array's block blk bytes (a multiple of 128), the three
+// blocks of a piece within half of the B_X region (2 N1 N2 bytes); the rows
+// of a piece are one TMA box (a row: rowb bytes)
+struct ZsStage {
+    int P;
+    uint32_t rowb, blk, half;
+};
+__host__ __device__ inline ZsStage zs_stage(const ZsGeo& g) {
+    ZsStage st;
+    st.rowb = 4u * (uint32_t)g.n2;
+    st.half = 2u * (uint32_t)g.N1 * (uint32_t)g.N2;
+    int P = (int)(st.half / (3u * st.rowb));
+    if (P > g.n1) P = g.n1;
+    while (P > 1 && 3u * (((uint32_t)P * st.rowb + 127u) & ~127u) > st.half) --P;
+    st.P = P;
+    st.blk = ((uint32_t)P * st.rowb + 127u) & ~127u;
+    return st;
 }
 
 static uint32_t zs_slot_for(int N1) { return (uint32_t)(64 * N1 > (int)zs::kC2Chunk ? 64 * N1 : zs::kC2Chunk); }
@@ -232,6 +256,33 @@ void zs_arrange(const int F[3], int pe, int ax1, const double* C1, const double*
     }
 }
 
+// Host: the row maps of a job's b, u, z ([F0][F1][F2] FP32 faces, the last
+// axis contiguous): box n2 x P rows of one slab (P along ax1, 1 along pe)
+int zs_encode_maps(const int F[3], int pe, int ax1, const float* b, const float* u, const float* z, void* maps) {
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    CUtensorMap* out = (CUtensorMap*)maps + kZsMap0;
+    memset(out, 0, 3 * sizeof(CUtensorMap));
+    auto enc = (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
+    const ZsGeo g = zs_geo(F, pe, ax1);
+    if (!enc || pe > 1 || (g.n2 & 3) != 0 || g.n1 > 256 || g.n2 > 256) return 0;
+    const ZsStage st = zs_stage(g);
+    const float* src[3] = {b, u, z};
+    for (int a = 0; a < 3; ++a) {
+        const cuuint64_t dim[3] = {(cuuint64_t)F[2], (cuuint64_t)F[1], (cuuint64_t)F[0]};
+        const cuuint64_t str[2] = {(cuuint64_t)F[2] * 4, (cuuint64_t)F[1] * F[2] * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)g.n2, (cuuint32_t)(pe == 1 ? 1 : st.P), (cuuint32_t)(pe == 1 ? st.P : 1)};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (!src[a] || ((uintptr_t)src[a] & 15) ||
+            enc(&out[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)src[a], dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+                CUDA_SUCCESS) {
+            memset(out, 0, 3 * sizeof(CUtensorMap));
+            return 0;
+        }
+    }
+    return 1;
+}
+
 // ---------------------------------------------------------------- device helpers
 
 namespace zs {
@@ -260,6 +311,13 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
     hi = *reinterpret_cast<const uint32_t*>(&h);
     lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+// the PTX approximate reciprocal (one special-function instruction; relative
+// error within 2^-22 or so, below the 22-bit precision of the split operands)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -301,14 +359,16 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
     using namespace zs;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // barriers: ring full / empty, B_X full, accumulator full, A operand full,
-    // B_Y full, accumulator empty, converter sync, drain
-    __shared__ __align__(8) unsigned long long bar[2 * kRing + 7];
+    // B_Y full, accumulator empty, converter sync, drain, two staging buffers
+    __shared__ __align__(8) unsigned long long bar[2 * kRing + 9];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ signed char s_er[2][kMaxN1];   // row exponents of the slab in B_X (by slab parity; |e| < 128)
     __shared__ int s_max[2];          // max |x| of that slab (float bits)
     __shared__ float s_red[kCvWarps * 5];
-    __shared__ float s_l1[kMaxN1];    // lambda1 of the current slab's job
+    __shared__ __align__(16) float s_l1[kMaxN1];   // lambda1 of the current slab's job
+    __shared__ float s_l2[kMaxN2];    // lambda2 of the current slab's job
+    __shared__ float s_ar;            // alpha / rho of the current slab's job
     __shared__ int s_flag;
     volatile int* abort = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -322,6 +382,7 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
     const uint32_t b_ae = b_by + 8;
     const uint32_t b_cv = b_ae + 8;
     const uint32_t b_drain = b_cv + 8;
+    const uint32_t b_st = b_drain + 8;   // and b_st + 8
     const uint32_t s_base = smem_u32(smem_raw);
     const uint32_t s_bx = s_base, s_bxlo = s_base + cfg.off_bxlo;
     const uint32_t s_by = s_base + cfg.off_by, s_bylo = s_base + cfg.off_bylo;
@@ -339,6 +400,8 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
         mbar_init(b_ae, kCvWarps);
         mbar_init(b_cv, kCvWarps);
         mbar_init(b_drain, 1);
+        mbar_init(b_st, 1);
+        mbar_init(b_st + 8, 1);
         abort_flag = 0;
         s_max[0] = 0;
         s_max[1] = 0;
@@ -360,6 +423,7 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);   // this warp's TMEM lane quadrant
         const int row = 32 * q + lane;                            // its TMEM lane
         uint32_t n_acc = 0, n_cv = 0;
+        uint32_t n_st0 = 0, n_st1 = 0;   // completed phases of the two staging barriers
         bool ok = true;
         // converter-wide sync (bounded): every converter warp arrives, all wait
         auto cv_sync = [&]() -> bool {
@@ -416,33 +480,30 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
                     const float* br = bg + (long long)r * G.si;
                     const float* ur = ug + (long long)r * G.si;
                     if (vec) {
-                        // two core matrices' worth of loads in flight at a time
+                        // every load of the row's core matrices in flight at once
+                        float4 B[4][2], U[4][2];
 #pragma unroll
-                        for (int a0 = 0; a0 < 4; a0 += 2) {
-                            float4 B[2][2], U[2][2];
+                        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                                for (int hh = 0; hh < 2; ++hh) {
-                                    const int j = 8 * (gq + 4 * (a0 + a)) + 4 * hh;
-                                    if (j < G.n2) {
-                                        B[a][hh] = __ldg(reinterpret_cast<const float4*>(br + j));
-                                        U[a][hh] = __ldg(reinterpret_cast<const float4*>(ur + j));
-                                    } else {
-                                        B[a][hh] = make_float4(0.f, 0.f, 0.f, 0.f);
-                                        U[a][hh] = B[a][hh];
-                                    }
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const int j = 8 * (gq + 4 * a) + 4 * hh;
+                                if (j < G.n2) {
+                                    B[a][hh] = __ldg(reinterpret_cast<const float4*>(br + j));
+                                    U[a][hh] = __ldg(reinterpret_cast<const float4*>(ur + j));
+                                } else {
+                                    B[a][hh] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                    U[a][hh] = B[a][hh];
                                 }
+                            }
 #pragma unroll
-                            for (int a = 0; a < 2; ++a)
+                        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                                for (int hh = 0; hh < 2; ++hh) {
-                                    v[a0 + a][4 * hh + 0] = fmaf(us, U[a][hh].x, B[a][hh].x);
-                                    v[a0 + a][4 * hh + 1] = fmaf(us, U[a][hh].y, B[a][hh].y);
-                                    v[a0 + a][4 * hh + 2] = fmaf(us, U[a][hh].z, B[a][hh].z);
-                                    v[a0 + a][4 * hh + 3] = fmaf(us, U[a][hh].w, B[a][hh].w);
-                                }
-                        }
+                            for (int hh = 0; hh < 2; ++hh) {
+                                v[a][4 * hh + 0] = fmaf(us, U[a][hh].x, B[a][hh].x);
+                                v[a][4 * hh + 1] = fmaf(us, U[a][hh].y, B[a][hh].y);
+                                v[a][4 * hh + 2] = fmaf(us, U[a][hh].z, B[a][hh].z);
+                                v[a][4 * hh + 3] = fmaf(us, U[a][hh].w, B[a][hh].w);
+                            }
                     } else {
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
@@ -509,7 +570,76 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
             const bool vec = ((G.n2 & 3) == 0) &&
                              ((((uintptr_t)J.b) | ((uintptr_t)J.u) | ((uintptr_t)J.z)) & 15) == 0;
             const int nel = G.n1 * G.n2;
-            if (vec) {
+            if (vec && J.zs_tma) {
+                // b, u (and z^k for the norms) staged into the B_X region
+                // (free while this runs: A of the next slab is done) by TMA
+                // tensor copies of P rows each, two pieces in flight; the
+                // split depends on the slab's geometry alone
+                constexpr int na = NORMS ? 3 : 2;
+                const ZsStage SG = zs_stage(G);
+                const int np = (G.n1 + SG.P - 1) / SG.P;
+                const char* maps = (const char*)J.tmaps + (size_t)kZsMap0 * 128;
+                int issued = 0, used = 0;
+                auto issue = [&](int pc) {
+                    if (tid == 0) {
+                        const int r0 = pc * SG.P;
+                        const uint32_t bq = b_st + 8u * (uint32_t)(pc & 1);
+                        const uint32_t dst = s_bx + (uint32_t)(pc & 1) * SG.half;
+                        mbar_expect_tx(bq, (uint32_t)na * (uint32_t)SG.P * SG.rowb);
+#pragma unroll
+                        for (int a = 0; a < na; ++a)
+                            tma_tile3d(dst + (uint32_t)a * SG.blk, maps + (size_t)a * 128, 0, J.pe == 1 ? (int)s : r0,
+                                       J.pe == 1 ? r0 : (int)s, bq);
+                    }
+                    ++issued;
+                };
+                issue(0);
+                if (np > 1) issue(1);
+                bool good = true;
+                for (int pc = 0; pc < np; ++pc) {
+                    const int bf = pc & 1;
+                    if (!__all_sync(kFull, mbar_wait_ab(b_st + 8u * (uint32_t)bf, (bf ? n_st1 : n_st0) & 1u, abort))) {
+                        good = false;
+                        break;
+                    }
+                    if (bf) ++n_st1; else ++n_st0;
+                    ++used;
+                    const int r0 = pc * SG.P, rows = min(SG.P, G.n1 - r0);
+                    const unsigned char* sbase = smem_raw + (size_t)bf * SG.half;
+                    const float4* sb = reinterpret_cast<const float4*>(sbase);
+                    const float4* su = reinterpret_cast<const float4*>(sbase + SG.blk);
+                    const float4* sz = reinterpret_cast<const float4*>(sbase + 2 * SG.blk);
+                    const float4* zs = reinterpret_cast<const float4*>(stg) + (r0 * G.n2) / 4;
+                    const int n4p = (rows * G.n2) >> 2;
+                    for (int e = tid; e < n4p; e += kCvThreads) {
+                        const int f = 4 * e, il = f / G.n2, j = f - il * G.n2;
+                        const long long gi = (long long)(r0 + il) * G.si + j;
+                        const float4 Z = zs[e], B = sb[e], V = su[e];
+                        const float4 O = NORMS ? sz[e] : Z;
+                        float4 un;
+                        one(Z.x, B.x, V.x, O.x, un.x);
+                        one(Z.y, B.y, V.y, O.y, un.y);
+                        one(Z.z, B.z, V.z, O.z, un.z);
+                        one(Z.w, B.w, V.w, O.w, un.w);
+                        *reinterpret_cast<float4*>(zg + gi) = Z;
+                        *reinterpret_cast<float4*>(ug + gi) = un;
+                    }
+                    if (pc + 2 < np) {
+                        // every converter is done with this buffer before it is refilled
+                        if (!cv_sync()) {
+                            good = false;
+                            break;
+                        }
+                        issue(pc + 2);
+                    }
+                }
+                if (!good) {
+                    // copies still in flight land before the CTA exits
+                    for (int q = used; q < issued; ++q)
+                        mbar_wait_drain(b_st + 8u * (uint32_t)(q & 1), ((q & 1) ? n_st1 : n_st0) & 1u);
+                    return false;
+                }
+            } else if (vec) {
                 const int n4 = nel >> 2;
                 constexpr int U = 2;
                 for (int e0 = tid; e0 < n4; e0 += U * kCvThreads) {
@@ -639,44 +769,58 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
             if (!(ok = cv_sync())) break;
             if (tprev >= 0 && !(ok = epilogue(tprev))) break;
             if (tid == 0) s_max[buf ^ 1] = 0;
-            for (int k = tid; k < G.n1; k += kCvThreads) s_l1[k] = __ldg(J.lam1f + k);   // lambda1 for (d)
+            // lambda1, lambda2 and alpha / rho for (d), off its critical path
+            for (int k = tid; k < G.n1; k += kCvThreads) s_l1[k] = __ldg(J.lam1f + k);
+            for (int k = tid; k < G.n2; k += kCvThreads) s_l2[k] = __ldg(J.lam2f + k);
+            if (tid == 0) s_ar = (float)(J.alpha / J.rho);
             if (!(ok = cv_sync())) break;
-            // (c) first half of the next slab's x into B_X (free: A is done)
-            int nN1 = 0;
+            // (c) the first row octets of the next slab's x into B_X (free: A
+            // is done), one per converter warp
+            int nOct = 0, oc = 0;
             if (tn < total) {
                 const Job& Jn = jobs[find_job(prefix, njobs, tn)];
-                nN1 = zs_geo(Jn.F, Jn.pe, Jn.ax1).N1;
-                load_x(tn, 0, nN1 / 16, buf ^ 1);
+                nOct = zs_geo(Jn.F, Jn.pe, Jn.ax1).N1 / 8;
+                oc = nOct < kCvWarps ? nOct : kCvWarps;
+                load_x(tn, 0, oc, buf ^ 1);
             }
             // (d) D2 -> A operand of B': S[k1][k2] D2 2^(g - f - 8), with
             // S = rho / (alpha (lambda1[k1] + lambda2[k2]) + rho)
             if (!(ok = wait_acc())) break;
             if (live) {
-                // S = 1 / (1 + (alpha / rho) (lambda1 + lambda2)), one
-                // approximate reciprocal (MUFU) per element, lambda1 from
-                // shared memory (filled in (c))
-                const float ar = (float)(J.alpha / J.rho);
-                const float l2 = (row < G.n2) ? __ldg(J.lam2f + row) : 0.f;
+                // S = 1 / (1 + (alpha / rho) (lambda1 + lambda2)): one
+                // approximate reciprocal per element (rcp.approx; the
+                // division intrinsic took three times as long here), lambda1
+                // four values to a shared-memory load, lambda2 and alpha / rho
+                // from shared memory (filled in (b))
+                const float ar = s_ar;
+                const float l2 = (row < G.n2) ? s_l2[row] : 0.f;
                 const float fac = pow2f(X.g - X.f - kCExp);
                 chunks(0, nc, [&](int c, const uint32_t (&r)[16]) {
-                    uint32_t h[8], l[8];
-                    auto sc = [&](int k1) {
-                        return (k1 < G.n1 && row < G.n2) ? __fdividef(fac, fmaf(ar, s_l1[k1] + l2, 1.f)) : 0.f;
-                    };
+                    float lam[16];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int k1 = 16 * c + 2 * e;
-                        split2(__uint_as_float(r[2 * e]) * sc(k1), __uint_as_float(r[2 * e + 1]) * sc(k1 + 1), h[e], l[e]);
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 v4 = reinterpret_cast<const float4*>(s_l1 + 16 * c)[q4];
+                        lam[4 * q4] = v4.x;
+                        lam[4 * q4 + 1] = v4.y;
+                        lam[4 * q4 + 2] = v4.z;
+                        lam[4 * q4 + 3] = v4.w;
                     }
+                    auto sc = [&](int e) {
+                        return (16 * c + e < G.n1 && row < G.n2) ? fac * rcp_approx(fmaf(ar, lam[e] + l2, 1.f)) : 0.f;
+                    };
+                    uint32_t h[8], l[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        split2(__uint_as_float(r[2 * e]) * sc(2 * e), __uint_as_float(r[2 * e + 1]) * sc(2 * e + 1), h[e], l[e]);
                     tmem_st8(tl + kAop + 8u * c, h);
                     tmem_st8(tl + kAop + (uint32_t)(G.N1 / 2) + 8u * c, l);
                 });
                 tmem_st_wait();
             }
             signal(b_aop);
-            // (e) second half of the next slab's x
+            // (e) the rest of the next slab's x
             if (tn < total) {
-                load_x(tn, nN1 / 16, nN1 / 8, buf ^ 1);
+                load_x(tn, oc, nOct, buf ^ 1);
                 fence_async_smem();
             }
             if (!(ok = cv_sync())) break;
