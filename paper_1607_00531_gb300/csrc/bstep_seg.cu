@@ -351,6 +351,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // (launched with programmatic dependence: everything below reads the
+    // previous kernel's results)
+    pdl_wait();
     const long long total = prefix[njobs];
     if ((long long)blockIdx.x < total) stage_tile(jobs, njobs, prefix, blockIdx.x, Rg, Rg.b(0), bar);
     int it = 0;
@@ -686,13 +689,10 @@ cudaError_t launch_bstep_seg(const LineLaunch& L) {
     const long long cap = (long long)per_sm * sms;
     const unsigned grid = (unsigned)(L.total_tiles < cap ? L.total_tiles : cap);
     count_launch();
-    if (L.seg_S == 9)
-        seg::k_bstep_seg<9><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, L.seg_m, nb, L.rlist_out,
-                                                          L.rcount_out, L.rcap, L.status);
-    else
-        seg::k_bstep_seg<17><<<grid, block, smem, L.stream>>>(L.jobs, L.njobs, L.prefix, L.seg_m, nb, L.rlist_out,
-                                                           L.rcount_out, L.rcap, L.status);
-    return cudaGetLastError();
+    cudaError_t e = launch_k(L.pdl, L.seg_S == 9 ? seg::k_bstep_seg<9> : seg::k_bstep_seg<17>, dim3(grid), dim3(block),
+                             smem, L.stream, L.jobs, L.njobs, L.prefix, L.seg_m, nb, L.rlist_out, L.rcount_out, L.rcap,
+                             L.status);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // this translation unit's bounded-wait limit (tc_ptx.cuh), on the current device

@@ -519,8 +519,9 @@ static int dot_dev(Plan& P, const double* x, const double* y, double* out, cudaS
 }
 
 static int max_abs_d1_dev(Plan& P, const double* b, double* out, cudaStream_t st) {
-    SAC_CUDA(launch_max_abs_d1(P.d_job, 1, P.d_pref_elem, P.elem_blocks, b, P.d_part, st));
-    SAC_CUDA(launch_reduce(P.d_part, (int)P.elem_blocks, -1, P.d_out + 12, st));
+    int nb = 0;
+    SAC_CUDA(launch_max_abs_d1(P.d_job, P.G.n_outer, P.G.mpe, P.G.n_inner, 1216, b, P.d_part, &nb, st));
+    SAC_CUDA(launch_reduce(P.d_part, nb, -1, P.d_out + 12, st));
     SAC_TRY(read_back(out, P.d_out + 12, sizeof(double), st));
     return SAC_OK;
 }

@@ -508,6 +508,10 @@ int Engine::enqueue_iteration(int slot) {
         L.seg_S = C.seg;
         L.seg_G = C.segG;
         L.seg_m = C.maxm;
+        // programmatic dependent launch (the kernels wait for their
+        // predecessor's results on the device); not with the profiling event
+        // nodes between the kernels
+        L.pdl = slot < 0 ? 1 : 0;
         ENG_CUDA(launch_bstep(mixed ? 1 : 0, L));
     }
     prof_mark(slot, pass, 1);
@@ -565,7 +569,7 @@ int Engine::enqueue_iteration(int slot) {
         prof_mark(slot, 7, 0);
         const AdmmCheck chk = check_args();
         ENG_CUDA(launch_zslab(d_jobs_, nj, d_pref_zs_, zs_total_, zs_cfg_, d_part_ + 5 * admm_blocks_, 1, &chk,
-                              d_status_, st_));
+                              d_status_, st_, slot < 0 ? 1 : 0));
         prof_mark(slot, 7, 1);
     }
     return SAC_OK;

@@ -604,6 +604,8 @@ __global__ void __launch_bounds__(256) k_bstep_list(const Job* __restrict__ jobs
     S* sB = sI2 + (size_t)W * RLc;
     S* sZ = sB + (size_t)W * RLf;
     S* sU = sZ + (size_t)W * RLf;
+    // (launched with programmatic dependence: the list is the previous kernel's)
+    pdl_wait();
     const long long n = min(*rcount, rcap);
     for (long long e = (long long)blockIdx.x * W + w; e < n; e += (long long)gridDim.x * W) {
         const unsigned long long key = rlist[e];
@@ -857,9 +859,9 @@ cudaError_t launch_bstep_k(const LineLaunch& L) {
     size_t sm = line_smem_bstep(L.W, L.RLc, L.RLf, sizeof(T), sizeof(S));
     if (L.list_blocks <= 0) return cudaSuccess;
     count_launch();
-    kern<<<(unsigned)L.list_blocks, 32 * L.W, sm, L.stream>>>(L.jobs, L.W, L.RLc, L.RLf, L.n_sqp, L.rlist,
-                                                             L.rcount, L.rcap, L.status);
-    return cudaGetLastError();
+    cudaError_t e = launch_k(L.pdl, kern, dim3((unsigned)L.list_blocks), dim3(32 * L.W), sm, L.stream, L.jobs, L.W,
+                             L.RLc, L.RLf, L.n_sqp, L.rlist, L.rcount, L.rcap, L.status);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T, typename S>

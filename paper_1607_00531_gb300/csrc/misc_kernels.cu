@@ -100,38 +100,42 @@ __global__ void __launch_bounds__(256) k_hessvec(const Job* __restrict__ jobs, i
     }
 }
 
-// largest |b_{i+1} - b_i| / h along PE over the faces of a job (per-block
-// maxima); thread -> (outer index o, PE row i, inner index n) with n fastest
-__global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ jobs, int njobs,
-                                                    const long long* __restrict__ prefix,
-                                                    const double* __restrict__ b, double* __restrict__ part) {
-    __shared__ long long sStart[2];
-    const long long t = blockIdx.x;
-    if (t >= prefix[njobs]) return;
-    const int jid = find_job(prefix, njobs, t);
-    const Job& J = jobs[jid];
-    const long long f0 = (t - prefix[jid]) * 256, f = f0 + threadIdx.x;
-    const long long per_outer = (long long)J.mpe * J.n_inner;
-    if (threadIdx.x == 0) {
-        // the block's first cell as (outer index, offset): one division per block
-        const long long o = f0 / per_outer;
-        sStart[0] = o;
-        sStart[1] = f0 - o * per_outer;
-    }
-    __syncthreads();
+// largest |b_{i+1} - b_i| / h along PE over the faces of one job (per-block
+// maxima, one per block of the launch).  For an outer index o the cells (i,
+// n) of PE row i < mpe and inner index n are contiguous, cell k at face
+// o (mpe + 1) n_inner + k with its PE neighbour n_inner faces on; a block
+// takes chunks of 8 x 256 cells of one outer index (grid stride), every load
+// of a chunk in flight at once
+constexpr int kD1Chunk = 8 * 256;
+__global__ void __launch_bounds__(256) k_max_abs_d1(const Job* __restrict__ job, const double* __restrict__ b,
+                                                    double* __restrict__ part) {
+    const Job& J = *job;
+    const long long ni = J.n_inner, per_outer = (long long)J.mpe * ni;
+    const long long cpr = (per_outer + kD1Chunk - 1) / kD1Chunk;   // chunks per outer index
+    const long long nch = (long long)J.n_outer * cpr;
     // |d| as the bits of a non-negative double: their unsigned order is the
     // numeric order, and a NaN sorts above +inf; the maximum runs on the
     // integer units (FP64 comparisons and shuffles are slow on this GPU)
     unsigned long long mx = 0ull;
-    const long long ncell_rows = (long long)J.n_outer * per_outer;   // one entry per cell
-    if (f < ncell_rows) {
-        long long o = sStart[0], rem = sStart[1] + threadIdx.x;
-        while (rem >= per_outer) {   // (at most 256 / per_outer + 1 steps)
-            rem -= per_outer;
-            ++o;
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        const long long o = c / cpr, k0 = (c - o * cpr) * kD1Chunk;
+        const double* __restrict__ row = b + o * (long long)(J.mpe + 1) * ni;
+        double lo[8], hi[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const long long k = k0 + e * 256 + threadIdx.x;
+            lo[e] = 0.0;
+            hi[e] = 0.0;
+            if (k < per_outer) {
+                lo[e] = __ldg(row + k);
+                hi[e] = __ldg(row + k + ni);
+            }
         }
-        const long long a = o * (J.mpe + 1) * (long long)J.n_inner + rem;   // face (o, i, n)
-        mx = (unsigned long long)__double_as_longlong(b[a + J.n_inner] - b[a]) & 0x7fffffffffffffffull;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const unsigned long long v = (unsigned long long)__double_as_longlong(hi[e] - lo[e]) & 0x7fffffffffffffffull;
+            mx = v > mx ? v : mx;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -255,11 +259,15 @@ cudaError_t launch_hessvec(const Job* jobs, int njobs, const long long* prefix, 
     k_hessvec<<<(unsigned)total_blocks, 256, 0, st>>>(jobs, njobs, prefix, diag, off, v, out, part);
     return cudaGetLastError();
 }
-cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
-                              const double* b, double* part, cudaStream_t st) {
-    if (total_blocks <= 0) return cudaSuccess;
+cudaError_t launch_max_abs_d1(const Job* job, long long n_outer, long long mpe, long long n_inner, int max_blocks,
+                              const double* b, double* part, int* nparts, cudaStream_t st) {
+    const long long per_outer = mpe * n_inner;
+    const long long nch = n_outer * ((per_outer + kD1Chunk - 1) / kD1Chunk);
+    const int grid = (int)(nch < max_blocks ? nch : max_blocks);
+    *nparts = grid;
+    if (grid <= 0) return cudaSuccess;
     count_launch();
-    k_max_abs_d1<<<(unsigned)total_blocks, 256, 0, st>>>(jobs, njobs, prefix, b, part);
+    k_max_abs_d1<<<grid, 256, 0, st>>>(job, b, part);
     return cudaGetLastError();
 }
 cudaError_t launch_reduce(const double* part, int nparts, int ncomp, double* out, cudaStream_t st) {

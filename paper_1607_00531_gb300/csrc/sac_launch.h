@@ -29,6 +29,24 @@ inline cudaError_t allow_max_dyn_smem(const void* k) {
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
+// A kernel launch; with pdl != 0 programmatic dependent launch is allowed
+// (the kernel may start before the previous kernel of the stream ends, and
+// waits for it in pdl_wait before it touches its results)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(int pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
 // records the code behind a SAC_ECUDA (sac_last_cuda_error)
 void note_cuda_error(int code);
 cudaError_t prepare_bstep_f64();
@@ -61,6 +79,7 @@ struct LineLaunch {
     // of seg_lines() lines
     int seg_S, seg_G;
     int seg_m;                   // longest line of the launch (cells): shared memory
+    int pdl;                     // programmatic dependent launch allowed (launch_k)
 };
 
 // faces per lane for a line of m cells (m + 1 faces); 0 if too long
@@ -150,7 +169,7 @@ cudaError_t prepare_zslab();
 // (norms != 0, chk null or without counters), or FP32 with the fused
 // stopping test (chk->counters: the CTA finishing a job's last slab tests it)
 cudaError_t launch_zslab(Job* jobs, int njobs, const long long* prefix, long long total, const ZsCfg& cfg,
-                         double* part, int norms, const AdmmCheck* chk, int* status, cudaStream_t st);
+                         double* part, int norms, const AdmmCheck* chk, int* status, cudaStream_t st, int pdl = 0);
 
 // prec: 0 FP64, 1 FP32, 2 FP64 compute on FP32 storage
 cudaError_t launch_bstep(int prec, const LineLaunch& L);
@@ -273,7 +292,10 @@ cudaError_t launch_corrected(int prec, const Job* job, long long nc, const doubl
 cudaError_t launch_restrict(int nd, const int M[3], bool f32, const void* I, void* Ic, cudaStream_t st);
 cudaError_t launch_prolong(int nd, int pe, const int M[3], const double* bc, const double* zc, double* bf, double* zf,
                            double* uf, cudaStream_t st);
-cudaError_t launch_max_abs_d1(const Job* jobs, int njobs, const long long* prefix, long long total_blocks,
-                              const double* b, double* part, cudaStream_t st);
+// per-block maxima of |b_{i+1} - b_i| / h along PE of one job (its line
+// view: n_outer x mpe x n_inner cells) into part[0 .. *nparts), *nparts <=
+// max_blocks
+cudaError_t launch_max_abs_d1(const Job* job, long long n_outer, long long mpe, long long n_inner, int max_blocks,
+                              const double* b, double* part, int* nparts, cudaStream_t st);
 
 }  // namespace sac

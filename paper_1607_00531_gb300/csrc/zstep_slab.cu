@@ -411,6 +411,9 @@ __global__ void __launch_bounds__(zs::kThreads, 1)
     fence_before();
     __syncthreads();
     fence_after();
+    // (launched with programmatic dependence: everything below reads or
+    // writes the previous kernels' data, the list counters included)
+    pdl_wait();
     const uint32_t tmem = tmem_slot;
     const long long dt = gridDim.x;
     // the next iteration's b-step list counters (fused stopping-test form)
@@ -1014,7 +1017,7 @@ cudaError_t prepare_zslab() {
 }
 
 cudaError_t launch_zslab(Job* jobs, int njobs, const long long* prefix, long long total, const ZsCfg& cfg,
-                         double* part, int norms, const AdmmCheck* chk, int* status, cudaStream_t st) {
+                         double* part, int norms, const AdmmCheck* chk, int* status, cudaStream_t st, int pdl) {
     if (total <= 0) return cudaSuccess;
     if (cfg.smem == 0 || cfg.smem > zs::kMaxSmem) return cudaErrorInvalidValue;
     const long long nsm = zs_sm_count();
@@ -1023,11 +1026,9 @@ cudaError_t launch_zslab(Job* jobs, int njobs, const long long* prefix, long lon
     AdmmCheck none;
     memset(&none, 0, sizeof(none));
     const AdmmCheck& c = chk ? *chk : none;
-    if (norms || c.counters)
-        k_zslab<1><<<grid, zs::kThreads, cfg.smem, st>>>(jobs, njobs, prefix, total, cfg, part, c, status);
-    else
-        k_zslab<0><<<grid, zs::kThreads, cfg.smem, st>>>(jobs, njobs, prefix, total, cfg, part, c, status);
-    return cudaGetLastError();
+    const cudaError_t e = launch_k(pdl, (norms || c.counters) ? k_zslab<1> : k_zslab<0>, dim3(grid), dim3(zs::kThreads),
+                                   cfg.smem, st, jobs, njobs, prefix, total, cfg, part, c, status);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t set_wait_tests_zs(long long tests) { return cudaMemcpyToSymbol(g_wait_tests, &tests, sizeof(tests)); }

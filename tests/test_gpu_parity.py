@@ -199,6 +199,30 @@ def test_admm_rejects_infeasible_start(sac):
     assert e.value.status == sac.SAC_EINFEASIBLE
 
 
+# one PE difference just above / below the bound, placed in the first, a
+# middle and the last (partial) chunk of cells of the feasibility check (chunks
+# of 2048 cells of one outer index: 9 x 300 x 40 cells, 6 chunks per index)
+@pytest.mark.parametrize("where", [(0, 0, 0), (4, 150, 17), (8, 299, 39)])
+def test_admm_feasibility_check_at_every_chunk(sac, where):
+    m, pe = (9, 300, 40), 1
+    h = (1.0 / 9, 1.0 / 300, 1.0 / 40)
+    rng = np.random.default_rng(5)
+    I1 = rng.normal(size=m)
+    I2 = rng.normal(size=m)
+    o, i, n = where
+    for excess, infeasible in ((1e-6, True), (-1e-6, False)):
+        b = np.zeros((9, 301, 40))
+        b[o, i + 1:, n] = (1.0 + excess) * h[1]    # one difference (cell (o, i, n)) of (1 + excess) h
+        g = sac.grid(m, h, pe)
+        p = sac.params(prec="f64", max_iter=1)
+        if infeasible:
+            with pytest.raises(sac.SacError) as e:
+                sac.admm_solve(g, p, cu(I1), cu(I2), cu(b))
+            assert e.value.status == sac.SAC_EINFEASIBLE
+        else:
+            sac.admm_solve(g, p, cu(I1), cu(I2), cu(b))
+
+
 @pytest.mark.parametrize("m,pe", [((37, 50), 1), ((9, 70, 21), 1), ((40, 7, 9), 0), ((5, 256, 11), 1)])
 def test_hessvec_and_preconditioners_f64(sac, m, pe):
     h, I1, I2, b, _, _ = case_data(m, pe, seed=40)
