@@ -1,16 +1,17 @@
 // bstep_seg.cu -- fast path of the ADMM b-step (Sec. 4.2, Eq. admmStep1) with
 // one thread per (line, segment), FP32 storage and arithmetic.
 //
-// A CTA takes NL = kLines neighbouring PE lines and cuts each of them into G
-// segments of S faces; thread (g, l) = (tid / NL, tid % NL) takes segment g of
-// line l.  The lines must be strided (PE axis not the last one): face p of
-// the NL lines is then a run of NL consecutive floats of every face and cell
-// array, and the CTA stages the five arrays of its lines (I1, I2, b, z, u) in
+// A CTA takes NL = kLines neighbouring PE lines of one outer index (the
+// index's last tile holds the rest when the inner extent is not a multiple)
+// and cuts each of them into G segments of S faces; thread (g, l) = (tid /
+// NL, tid % NL) takes segment g of line l.  The lines must be strided (PE
+// axis not the last one): face p of the tile's lines is then a run of
+// consecutive floats of every face and cell array, and the CTA stages the five arrays of its lines (I1, I2, b, z, u) in
 // shared memory as [p][line] rows (all later reads, including the image
 // values at the displaced points, are shared-memory reads): ten TMA tensor
-// copies of 16 lines x half the rows, issued by one warp and completing on an
-// mbarrier, or per-thread asynchronous copies where the rows are not 16-byte
-// aligned.  The CTAs are persistent (two per SM for lines of 257 faces, about
+// copies of 16 lines x half the rows (lines past the inner extent read as
+// zeros), issued by one warp and completing on an mbarrier, or per-thread
+// asynchronous copies where the rows are not 16-byte aligned.  The CTAs are persistent (two per SM for lines of 257 faces, about
 // 100 KB each) and take tiles strided by the grid; as soon as a tile's forward
 // elimination is done, its images, z and u are dead and the CTA starts the
 // copies of its next tile (b into a second buffer), so that they run under
@@ -196,28 +197,41 @@ __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
 }
 
-// copies rows [0, R) of the tile's lines of one array (R rows per outer
-// slab) into dst[row][line]; vec: the NL lines are NL consecutive, 16-byte
-// aligned floats of every row
+// copies rows [0, R) of the tile's nl lines (inner indices x .. x + nl - 1
+// of outer index o; R rows per outer slab) of one array into dst[row][line];
+// vec: those lines are nl consecutive, 16-byte aligned floats of every row
+// (nl a multiple of 4)
 __device__ __forceinline__ void stage(float* __restrict__ dst, const float* __restrict__ src, int R, int ni,
-                                      long long L0, long long nlines, bool vec) {
+                                      long long o, int x, int nl, bool vec) {
+    const float* base = src + o * (long long)R * ni + x;
     if (vec) {
-        const long long o = L0 / ni;
-        const float* base = src + o * (long long)R * ni + (L0 - o * ni);
-        for (int c = threadIdx.x; c < R * (kLines / 4); c += blockDim.x) {
-            const int row = c / (kLines / 4), q = c % (kLines / 4);
+        const int n4 = nl / 4;
+        for (int c = threadIdx.x; c < R * n4; c += blockDim.x) {
+            const int row = c / n4, q = c - row * n4;
             cp_async16(dst + row * kLines + 4 * q, base + (long long)row * ni + 4 * q);
         }
     } else {
         for (int e = threadIdx.x; e < R * kLines; e += blockDim.x) {
             const int row = e / kLines, l = e % kLines;
-            const long long L = L0 + l;
-            if (L < nlines) {
-                const long long o = L / ni;
-                cp_async4(dst + e, src + o * (long long)R * ni + (long long)row * ni + (L - o * ni));
-            }
+            if (l < nl) cp_async4(dst + e, base + (long long)row * ni + l);
         }
     }
+}
+
+// tile t of job jid: outer index o, first inner index x (a multiple of
+// kLines), lines nl; the tiles of one outer index are consecutive
+struct TileLines {
+    long long o;
+    int x, nl;
+};
+__device__ __forceinline__ TileLines tile_lines(const Job& J, const long long* __restrict__ prefix, int jid, long long t) {
+    const int ni = J.n_inner, tpr = (ni + kLines - 1) / kLines;
+    const long long tt = t - prefix[jid];
+    TileLines r;
+    r.o = tt / tpr;
+    r.x = (int)(tt - r.o * tpr) * kLines;
+    r.nl = min(kLines, ni - r.x);
+    return r;
 }
 
 // Rows per TMA box (two boxes per array and tile): images from row -2 to at
@@ -264,7 +278,7 @@ __device__ __forceinline__ void stage_tile(const Job* __restrict__ jobs, int njo
     const Job& J = jobs[jid];
     if (!J.active) return;
     const int m = J.mpe, ni = J.n_inner;
-    const long long L0 = (t - prefix[jid]) * NL;
+    const TileLines TL = tile_lines(J, prefix, jid, t);
     if (J.seg_tma) {
         // the last full warp: lane 0 sets the transaction count, lanes 0..9
         // issue one box each (array i / 2, half i % 2)
@@ -277,10 +291,10 @@ __device__ __forceinline__ void stage_tile(const Job* __restrict__ jobs, int njo
             }
             __syncwarp();
             if (q < 10) {
-                // lines L0 .. L0 + 15: inner index x (a multiple of 16:
-                // 64-byte aligned), outer index o
-                const long long o = L0 / ni;
-                const int x = (int)(L0 - o * ni), ai = q >> 1, hf = q & 1;
+                // inner indices x .. x + 15 (x a multiple of 16: 64-byte
+                // aligned; those past n_inner read as zeros), outer index o
+                const long long o = TL.o;
+                const int x = TL.x, ai = q >> 1, hf = q & 1;
                 const int rows = (ai < 2) ? ri : rf;
                 float* dst = (ai == 0) ? R.I1 - 2 * NL : (ai == 1) ? R.I2 - 2 * NL : (ai == 2) ? sB : (ai == 3) ? R.z : R.u;
                 const char* map = (const char*)J.tmaps + (size_t)(kSegMap0 + ai) * 128;
@@ -289,16 +303,15 @@ __device__ __forceinline__ void stage_tile(const Job* __restrict__ jobs, int njo
         }
         return;
     }
-    const long long nlines = (long long)J.n_outer * ni;
-    // with ni a multiple of NL and 16-byte aligned arrays, a tile is one
-    // aligned run of NL floats in every row
+    // with ni a multiple of 4 and 16-byte aligned arrays, a tile is one
+    // aligned run of nl floats in every row
     const uintptr_t any = (uintptr_t)J.I1 | (uintptr_t)J.I2 | (uintptr_t)J.b | (uintptr_t)J.z | (uintptr_t)J.u;
-    const bool vec = (ni % NL) == 0 && (any & 15) == 0;
-    stage(R.I1, (const float*)J.I1, m, ni, L0, nlines, vec);
-    stage(R.I2, (const float*)J.I2, m, ni, L0, nlines, vec);
-    stage(sB, (const float*)J.b, m + 1, ni, L0, nlines, vec);
-    stage(R.z, (const float*)J.z, m + 1, ni, L0, nlines, vec);
-    stage(R.u, (const float*)J.u, m + 1, ni, L0, nlines, vec);
+    const bool vec = (ni % 4) == 0 && (any & 15) == 0;
+    stage(R.I1, (const float*)J.I1, m, ni, TL.o, TL.x, TL.nl, vec);
+    stage(R.I2, (const float*)J.I2, m, ni, TL.o, TL.x, TL.nl, vec);
+    stage(sB, (const float*)J.b, m + 1, ni, TL.o, TL.x, TL.nl, vec);
+    stage(R.z, (const float*)J.z, m + 1, ni, TL.o, TL.x, TL.nl, vec);
+    stage(R.u, (const float*)J.u, m + 1, ni, TL.o, TL.x, TL.nl, vec);
     for (int e = threadIdx.x; e < 8 * NL; e += blockDim.x) {
         // zero rows -2, -1, m, m+1 of both images
         const int r = e / NL, l = e % NL;
@@ -392,14 +405,13 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         if (tn < total) stage_tile(jobs, njobs, prefix, tn, Rg, Rg.b(it + 1), bar);
         continue;
     }
-    const long long nlines = (long long)J.n_outer * ni;
-    const long long L0 = (t - prefix[jid]) * NL;
+    const TileLines TL = tile_lines(J, prefix, jid, t);
     const float* sI1 = Rg.I1;
     const float* sI2 = Rg.I2;
     const float* sZ = Rg.z;
     const float* sU = Rg.u;
-    const long long L = L0 + lane;
-    const bool valid = L < nlines;   // rows of lanes past the last line are not staged
+    const long long L = TL.o * ni + TL.x + lane;   // the lane's line
+    const bool valid = lane < TL.nl;   // rows of lanes past the outer index's last line are not staged
     if (jid != cjid) {
         cjid = jid;
         inv_h = (float)(1.0 / J.hpe);   // (1/h rounded once, as in the warp kernels)
@@ -557,10 +569,9 @@ __global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
         }
         fence_async_smem();
         if (issuer) {
-            const long long o = L0 / ni;
             sPend[0] = (long long)(const char*)J.tmaps + (long long)(kSegMap0 + 2) * 128;
-            sPend[1] = L0 - o * ni;
-            sPend[2] = o;
+            sPend[1] = TL.x;
+            sPend[2] = TL.o;
             sPend[3] = face_box_rows(m);
             sPend[4] = it & 1;
         }
@@ -607,7 +618,9 @@ int seg_encode_maps(int n_outer, int m, int ni, const float* I1, const float* I2
     CUtensorMap* out = (CUtensorMap*)maps + kSegMap0;
     memset(out, 0, 5 * sizeof(CUtensorMap));
     auto enc = (PFN_cuTensorMapEncodeTiled_v12000)tensor_map_encoder();
-    if (!enc || n_outer < 1 || m < 1 || ni < seg::kLines || ni % seg::kLines != 0) return 0;
+    // (rows a multiple of 16 bytes; a tile's lines past n_inner read as zeros
+    // and are not stored)
+    if (!enc || n_outer < 1 || m < 1 || ni < seg::kLines || ni % 4 != 0) return 0;
     const float* src[5] = {I1, I2, b, z, u};
     for (int i = 0; i < 5; ++i) {
         if (!src[i] || ((uintptr_t)src[i] & 15)) return 0;

@@ -204,7 +204,7 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     P->line_tiles = line_tiles(G.n_outer, G.n_inner, W);
     P->seg_S = seg_faces(G.mpe, G.n_inner, p->n_sqp, p->prec == SAC_MIXED, p->bstep_kernel);
     P->seg_G = seg_warps(G.mpe, P->seg_S);
-    P->seg_tiles = seg_tiles((long long)G.n_outer * G.n_inner);
+    P->seg_tiles = seg_tiles(G.n_outer, G.n_inner);
     const int axes[4] = {G.ax1, G.ax2, G.ax2, G.ax1};
     for (int q = 0; q < 4; ++q) P->pass_tiles[q] = axis_pass_tiles(G.F, axes[q]);
     P->elem_blocks = (G.nf + 255) / 256;

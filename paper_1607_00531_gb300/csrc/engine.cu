@@ -260,7 +260,7 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         c.lines = 0;
         for (int q = 0; q < c.count; ++q) {
             const Geometry& G = jobs_[c.first + q].G;
-            hp[q + 1] = hp[q] + (c.seg ? seg_tiles(jobs_[c.first + q].nlines) : line_tiles(G.n_outer, G.n_inner, W));
+            hp[q + 1] = hp[q] + (c.seg ? seg_tiles(G.n_outer, G.n_inner) : line_tiles(G.n_outer, G.n_inner, W));
             c.lines += jobs_[c.first + q].nlines;
         }
         c.tiles = hp[c.count];

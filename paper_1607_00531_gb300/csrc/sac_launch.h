@@ -123,7 +123,11 @@ int seg_lines();   // lines per CTA
 // the kernel then stages its tiles with per-thread asynchronous copies
 int seg_encode_maps(int n_outer, int m, int ni, const float* I1, const float* I2, const float* b, const float* z,
                     const float* u, void* maps);
-inline long long seg_tiles(long long nlines) { return (nlines + seg_lines() - 1) / seg_lines(); }
+// tiles of the segment b-step: runs of seg_lines() lines of one outer index
+// (the last run of an index partial when n_inner is not a multiple)
+inline long long seg_tiles(long long n_outer, long long n_inner) {
+    return n_outer * ((n_inner + seg_lines() - 1) / seg_lines());
+}
 size_t seg_smem_bytes(int mpe);   // dynamic shared memory of a CTA
 cudaError_t launch_bstep_seg(const LineLaunch& L);
 cudaError_t prepare_bstep_seg();

@@ -421,6 +421,13 @@ SEG_CASES = [
     ((9, 70, 32), 1),       # 71 faces, 18 tiles
     ((24, 143, 256), 1),    # 144 faces, 384 tiles: more tiles than resident CTAs (next tile prefetched)
     ((20, 256, 256), 1),    # 257 faces, 320 tiles: the same with segments of 17
+    # inner extents a multiple of 4 but not of 16: TMA-staged tiles within one
+    # outer index, the index's last tile partial (its lines past the extent
+    # read as zeros and are not stored)
+    ((9, 70, 20), 1),       # 71 faces, 2 tiles per outer index (16 + 4 lines)
+    ((6, 96, 60), 1),       # 97 faces, 4 tiles per outer index (16, 16, 16, 12): the 96 x 96 x 60 lines
+    ((3, 143, 44), 1),      # 144 faces, 16 segments of 9, tiles of 16, 16, 12 lines
+    ((4, 256, 36), 1),      # 257 faces, segments of 17, tiles of 16, 16, 4 lines
 ]
 
 
@@ -447,7 +454,8 @@ def test_bstep_mixed_segment_kernel(sac, m, pe):
     assert np.max(np.abs(outs[0] - outs[1])) / h[pe] <= 1e-4
 
 
-@pytest.mark.parametrize("m,pe", [((9, 70, 21), 1), ((5, 256, 11), 1), ((9, 70, 32), 1), ((3, 256, 32), 1)])
+@pytest.mark.parametrize("m,pe", [((9, 70, 21), 1), ((5, 256, 11), 1), ((9, 70, 32), 1), ((3, 256, 32), 1),
+                                  ((6, 96, 60), 1)])
 def test_bstep_mixed_segment_kernel_queues_blocked_lines(sac, m, pe):
     # (the last two: TMA-staged tiles, queued lines restored in the tile's
     # shared-memory buffer before its tensor store)
