@@ -331,8 +331,10 @@ __device__ __forceinline__ void store_b(const long long* pend, const Regions& R)
     tma_store3d(map, smem_u32(src + rf * kLines), x, rf, z);
 }
 
+// (segments of 9 faces: at least three CTAs per SM, 80 registers without
+// spills, so that short lines get more warps per SM; 17: two, 128 registers)
 template <int S>
-__global__ void __launch_bounds__(kLines * kMaxSeg, 512 / (kLines * kMaxSeg))
+__global__ void __launch_bounds__(kLines * kMaxSeg, S <= 9 ? 3 : 2)
     k_bstep_seg(const Job* __restrict__ jobs, int njobs, const long long* __restrict__ prefix, int mmax,
                 float near_bound, unsigned long long* __restrict__ rlist, int* __restrict__ rcount, int rcap,
                 int* __restrict__ status) {
