@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -310,6 +311,75 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     return SAC_OK;
 }
 
+// Host-side DCT tables of a plan that depend on its geometry alone (the DCT-II
+// matrices along ax1 and ax2 and their arrangements for the tensor-core
+// kernels), computed once and kept for the last few geometries of the
+// process: rebuilding them (65,536 cosines for a 256-face axis, then the
+// arranged copies) took longer than many iterations of the solve.
+struct HostTables {
+    long long key[17];
+    std::vector<double> C1, C2;
+    std::vector<float> C1f, C2f;
+    std::vector<float> tc[4], tn[4];
+    std::vector<unsigned char> zs;
+};
+static std::shared_ptr<const HostTables> host_tables(const Plan& P) {
+    static std::mutex mu;
+    static std::vector<std::shared_ptr<const HostTables>> cache;   // most recent last
+    constexpr size_t kKeep = 8;
+    const Geometry& G = P.G;
+    long long key[17] = {G.F[0], G.F[1], G.F[2], G.ax1, G.ax2, G.pe, P.use_tc, P.use_zs, P.zs_bytes};
+    for (int q = 0; q < 4; ++q) {
+        key[9 + q] = P.use_tc ? P.tc_floats[q] : 0;
+        key[13 + q] = P.use_tc ? P.tn_floats[q] : 0;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < cache.size(); ++i)
+            if (memcmp(cache[i]->key, key, sizeof(key)) == 0) {
+                std::shared_ptr<const HostTables> hit = cache[i];
+                cache.erase(cache.begin() + (long)i);
+                cache.push_back(hit);
+                return hit;
+            }
+    }
+    auto T = std::make_shared<HostTables>();
+    memcpy(T->key, key, sizeof(key));
+    const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+    T->C1.resize((size_t)L1 * L1);
+    T->C2.resize((size_t)L2 * L2);
+    dct2_matrix(L1, T->C1.data());
+    dct2_matrix(L2, T->C2.data());
+    T->C1f.assign(T->C1.begin(), T->C1.end());
+    T->C2f.assign(T->C2.begin(), T->C2.end());
+    if (P.use_tc) {
+        // pass 0: C1, pass 1: C2, pass 2: C2^T, pass 3: C1^T, split TF32 and pre-arranged
+        std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
+        for (int i = 0; i < L1; ++i)
+            for (int j = 0; j < L1; ++j) C1t[(size_t)i * L1 + j] = T->C1[(size_t)j * L1 + i];
+        for (int i = 0; i < L2; ++i)
+            for (int j = 0; j < L2; ++j) C2t[(size_t)i * L2 + j] = T->C2[(size_t)j * L2 + i];
+        const double* Ms[4] = {T->C1.data(), T->C2.data(), C2t.data(), C1t.data()};
+        for (int q = 0; q < 4; ++q) {
+            if (P.tc_floats[q] == 0) continue;
+            T->tc[q].assign((size_t)P.tc_floats[q], 0.f);
+            tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], T->tc[q].data());
+            if (P.tn_floats[q]) {
+                T->tn[q].assign((size_t)P.tn_floats[q], 0.f);
+                tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], T->tn[q].data());
+            }
+        }
+    }
+    if (P.use_zs) {
+        T->zs.assign((size_t)P.zs_bytes, 0);
+        zs_arrange(G.F, G.pe, G.ax1, T->C1.data(), T->C2.data(), T->zs.data());
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back(T);
+    if (cache.size() > kKeep) cache.erase(cache.begin());
+    return T;
+}
+
 int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, void* b, void* z, void* u, void* t1,
                 void* t2, cudaStream_t st) {
     SAC_TRY(prepare_kernels());
@@ -361,13 +431,13 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                           0, P->zs_slabs};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
+    // the tables depend on the geometry and the parameters only: once per plan
+    if (P->tables_up) return SAC_OK;
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
-    std::vector<double> C1((size_t)L1 * L1), C2((size_t)L2 * L2), l1(L1), l2(L2);
-    dct2_matrix(L1, C1.data());
-    dct2_matrix(L2, C2.data());
+    const std::shared_ptr<const HostTables> T = host_tables(*P);
+    std::vector<double> l1(L1), l2(L2);
     neumann_eigs(L1, G.h[G.ax1], l1.data());
     neumann_eigs(L2, G.h[G.ax2], l2.data());
-    std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end());
     {
         // spectral scaling of the z-step, rho / (alpha (lam1 + lam2) + rho), in FP64 then FP32
         std::vector<float> sc((size_t)L1 * L2);
@@ -376,35 +446,17 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                 sc[(size_t)i * L2 + j] = (float)(p->rho / (p->alpha * (l1[i] + l2[j]) + p->rho));
         SAC_CUDA(cudaMemcpyAsync(P->d_scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice, st));
     }
-    if (P->use_tc) {
-        // pass 0: C1, pass 1: C2, pass 2: C2^T, pass 3: C1^T, split TF32 and pre-arranged
-        std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
-        for (int i = 0; i < L1; ++i)
-            for (int j = 0; j < L1; ++j) C1t[(size_t)i * L1 + j] = C1[(size_t)j * L1 + i];
-        for (int i = 0; i < L2; ++i)
-            for (int j = 0; j < L2; ++j) C2t[(size_t)i * L2 + j] = C2[(size_t)j * L2 + i];
-        const double* Ms[4] = {C1.data(), C2.data(), C2t.data(), C1t.data()};
-        for (int q = 0; q < 4; ++q) {
-            if (P->tc_floats[q] == 0) continue;
-            std::vector<float> arr((size_t)P->tc_floats[q], 0.f);
-            tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
-            SAC_CUDA(cudaMemcpyAsync(P->d_Ctc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
-            if (P->tn_floats[q]) {
-                std::vector<float> tn((size_t)P->tn_floats[q], 0.f);
-                tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], tn.data());
-                SAC_CUDA(cudaMemcpyAsync(P->d_Ctn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
-            }
-        }
+    for (int q = 0; q < 4; ++q) {
+        if (!T->tc[q].empty())
+            SAC_CUDA(cudaMemcpyAsync(P->d_Ctc[q], T->tc[q].data(), T->tc[q].size() * 4, cudaMemcpyHostToDevice, st));
+        if (!T->tn[q].empty())
+            SAC_CUDA(cudaMemcpyAsync(P->d_Ctn[q], T->tn[q].data(), T->tn[q].size() * 4, cudaMemcpyHostToDevice, st));
     }
-    if (P->use_zs) {
-        std::vector<unsigned char> zsm((size_t)P->zs_bytes);
-        zs_arrange(G.F, G.pe, G.ax1, C1.data(), C2.data(), zsm.data());
-        SAC_CUDA(cudaMemcpyAsync(P->d_Czs, zsm.data(), zsm.size(), cudaMemcpyHostToDevice, st));
-    }
-    SAC_CUDA(cudaMemcpyAsync(P->d_C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
-    SAC_CUDA(cudaMemcpyAsync(P->d_C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
-    SAC_CUDA(cudaMemcpyAsync(P->d_C1f, C1f.data(), C1f.size() * 4, cudaMemcpyHostToDevice, st));
-    SAC_CUDA(cudaMemcpyAsync(P->d_C2f, C2f.data(), C2f.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!T->zs.empty()) SAC_CUDA(cudaMemcpyAsync(P->d_Czs, T->zs.data(), T->zs.size(), cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C1, T->C1.data(), T->C1.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C2, T->C2.data(), T->C2.size() * 8, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C1f, T->C1f.data(), T->C1f.size() * 4, cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemcpyAsync(P->d_C2f, T->C2f.data(), T->C2f.size() * 4, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_lam1, l1.data(), l1.size() * 8, cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_lam2, l2.data(), l2.size() * 8, cudaMemcpyHostToDevice, st));
     {
@@ -412,6 +464,7 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
         SAC_CUDA(cudaMemcpyAsync(P->d_lam1f, l1f.data(), l1f.size() * 4, cudaMemcpyHostToDevice, st));
         SAC_CUDA(cudaMemcpyAsync(P->d_lam2f, l2f.data(), l2f.size() * 4, cudaMemcpyHostToDevice, st));
     }
+    P->tables_up = 1;
     SAC_CUDA(cudaMemsetAsync(P->d_status, 0, 256, st));
     // the host copies above read pageable memory: the runtime has consumed it on return
     return SAC_OK;

@@ -50,6 +50,7 @@ struct Plan {
     long long zs_slabs, zs_bytes;
     ZsCfg zs_cfg;
     int rcap;
+    int tables_up;            // the DCT tables of this plan are in ws (plan_upload)
     // device pointers inside ws
     Job* d_job;
     long long* d_pref_line;
@@ -79,7 +80,8 @@ struct Plan {
 
 // plan layout; with ws == NULL only computes plan->bytes
 int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* plan);
-// upload the job descriptor, prefixes and DCT tables (stream-ordered)
+// upload the job descriptor, prefixes and (on the plan's first upload) the
+// DCT tables (stream-ordered)
 int plan_upload(Plan* plan, const sac_params* p, const void* I1, const void* I2, void* b, void* z, void* u,
                 void* t1, void* t2, cudaStream_t st);
 // line-launch description for this plan
