@@ -311,28 +311,11 @@ int plan_layout(const sac_grid* g, const sac_params* p, void* ws, Plan* P) {
     return SAC_OK;
 }
 
-// Host-side DCT tables of a plan that depend on its geometry alone (the DCT-II
-// matrices along ax1 and ax2 and their arrangements for the tensor-core
-// kernels), computed once and kept for the last few geometries of the
-// process: rebuilding them (65,536 cosines for a 256-face axis, then the
-// arranged copies) took longer than many iterations of the solve.
-struct HostTables {
-    long long key[17];
-    std::vector<double> C1, C2;
-    std::vector<float> C1f, C2f;
-    std::vector<float> tc[4], tn[4];
-    std::vector<unsigned char> zs;
-};
-static std::shared_ptr<const HostTables> host_tables(const Plan& P) {
+std::shared_ptr<const HostTables> host_tables(const int F[3], int ax1, int ax2, int pe, bool tc, bool zs) {
     static std::mutex mu;
     static std::vector<std::shared_ptr<const HostTables>> cache;   // most recent last
     constexpr size_t kKeep = 8;
-    const Geometry& G = P.G;
-    long long key[17] = {G.F[0], G.F[1], G.F[2], G.ax1, G.ax2, G.pe, P.use_tc, P.use_zs, P.zs_bytes};
-    for (int q = 0; q < 4; ++q) {
-        key[9 + q] = P.use_tc ? P.tc_floats[q] : 0;
-        key[13 + q] = P.use_tc ? P.tn_floats[q] : 0;
-    }
+    const long long key[8] = {F[0], F[1], F[2], ax1, ax2, pe, tc ? 1 : 0, zs ? 1 : 0};
     {
         std::lock_guard<std::mutex> lk(mu);
         for (size_t i = 0; i < cache.size(); ++i)
@@ -345,14 +328,14 @@ static std::shared_ptr<const HostTables> host_tables(const Plan& P) {
     }
     auto T = std::make_shared<HostTables>();
     memcpy(T->key, key, sizeof(key));
-    const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
+    const int L1 = F[ax1], L2 = F[ax2];
     T->C1.resize((size_t)L1 * L1);
     T->C2.resize((size_t)L2 * L2);
     dct2_matrix(L1, T->C1.data());
     dct2_matrix(L2, T->C2.data());
     T->C1f.assign(T->C1.begin(), T->C1.end());
     T->C2f.assign(T->C2.begin(), T->C2.end());
-    if (P.use_tc) {
+    if (tc) {
         // pass 0: C1, pass 1: C2, pass 2: C2^T, pass 3: C1^T, split TF32 and pre-arranged
         std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
         for (int i = 0; i < L1; ++i)
@@ -361,18 +344,20 @@ static std::shared_ptr<const HostTables> host_tables(const Plan& P) {
             for (int j = 0; j < L2; ++j) C2t[(size_t)i * L2 + j] = T->C2[(size_t)j * L2 + i];
         const double* Ms[4] = {T->C1.data(), T->C2.data(), C2t.data(), C1t.data()};
         for (int q = 0; q < 4; ++q) {
-            if (P.tc_floats[q] == 0) continue;
-            T->tc[q].assign((size_t)P.tc_floats[q], 0.f);
-            tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], T->tc[q].data());
-            if (P.tn_floats[q]) {
-                T->tn[q].assign((size_t)P.tn_floats[q], 0.f);
-                tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], T->tn[q].data());
+            const long long nfl = tc_matrix_floats(F, ax1, ax2, q);
+            if (nfl == 0) continue;
+            T->tc[q].assign((size_t)nfl, 0.f);
+            tc_arrange_matrix(F, ax1, ax2, q, Ms[q], T->tc[q].data());
+            const long long ntn = tcn_matrix_floats(F, ax1, ax2, q);
+            if (ntn) {
+                T->tn[q].assign((size_t)ntn, 0.f);
+                tcn_arrange_matrix(F, ax1, ax2, q, Ms[q], T->tn[q].data());
             }
         }
     }
-    if (P.use_zs) {
-        T->zs.assign((size_t)P.zs_bytes, 0);
-        zs_arrange(G.F, G.pe, G.ax1, T->C1.data(), T->C2.data(), T->zs.data());
+    if (zs) {
+        T->zs.assign((size_t)zs_matrix_bytes(F, pe, ax1), 0);
+        zs_arrange(F, pe, ax1, T->C1.data(), T->C2.data(), T->zs.data());
     }
     std::lock_guard<std::mutex> lk(mu);
     cache.push_back(T);
@@ -434,7 +419,7 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
     // the tables depend on the geometry and the parameters only: once per plan
     if (P->tables_up) return SAC_OK;
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
-    const std::shared_ptr<const HostTables> T = host_tables(*P);
+    const std::shared_ptr<const HostTables> T = host_tables(G.F, G.ax1, G.ax2, G.pe, P->use_tc != 0, P->use_zs != 0);
     std::vector<double> l1(L1), l2(L2);
     neumann_eigs(L1, G.h[G.ax1], l1.data());
     neumann_eigs(L2, G.h[G.ax2], l2.data());

@@ -398,52 +398,33 @@ int Engine::build(const std::vector<EngineJob>& in, const sac_params& p, void* w
         J.Czs = zs_job_[i] ? (const void*)(s + L.zs) : nullptr;
         J.active = 1;
         if (E.fresh) {
-            // tables (host-computed, FP64 then FP32 / split TF32 copies)
+            // tables: the geometry's DCT matrices and arranged operands (host
+            // cache), eigenvalues and the spectral scale of this job
             const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
-            std::vector<double> C1((size_t)L1 * L1), C2((size_t)L2 * L2), l1(L1), l2(L2);
-            dct2_matrix(L1, C1.data());
-            dct2_matrix(L2, C2.data());
+            const std::shared_ptr<const HostTables> T = host_tables(G.F, G.ax1, G.ax2, G.pe, use_tc_, L.zs_bytes > 0);
+            std::vector<double> l1(L1), l2(L2);
             neumann_eigs(L1, G.h[G.ax1], l1.data());
             neumann_eigs(L2, G.h[G.ax2], l2.data());
-            std::vector<float> C1f(C1.begin(), C1.end()), C2f(C2.begin(), C2.end()), sc((size_t)L1 * L2);
+            std::vector<float> sc((size_t)L1 * L2);
             std::vector<float> l1f(l1.begin(), l1.end()), l2f(l2.begin(), l2.end());
             ENG_CUDA(cudaMemcpyAsync(s + L.l1f, l1f.data(), l1f.size() * 4, cudaMemcpyHostToDevice, st));
             ENG_CUDA(cudaMemcpyAsync(s + L.l2f, l2f.data(), l2f.size() * 4, cudaMemcpyHostToDevice, st));
             for (int a = 0; a < L1; ++a)
                 for (int c = 0; c < L2; ++c) sc[(size_t)a * L2 + c] = (float)(p.rho / (p.alpha * (l1[a] + l2[c]) + p.rho));
-            ENG_CUDA(cudaMemcpyAsync(s + L.C1, C1.data(), C1.size() * 8, cudaMemcpyHostToDevice, st));
-            ENG_CUDA(cudaMemcpyAsync(s + L.C2, C2.data(), C2.size() * 8, cudaMemcpyHostToDevice, st));
-            ENG_CUDA(cudaMemcpyAsync(s + L.C1f, C1f.data(), C1f.size() * 4, cudaMemcpyHostToDevice, st));
-            ENG_CUDA(cudaMemcpyAsync(s + L.C2f, C2f.data(), C2f.size() * 4, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C1, T->C1.data(), T->C1.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C2, T->C2.data(), T->C2.size() * 8, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C1f, T->C1f.data(), T->C1f.size() * 4, cudaMemcpyHostToDevice, st));
+            ENG_CUDA(cudaMemcpyAsync(s + L.C2f, T->C2f.data(), T->C2f.size() * 4, cudaMemcpyHostToDevice, st));
             ENG_CUDA(cudaMemcpyAsync(s + L.l1, l1.data(), l1.size() * 8, cudaMemcpyHostToDevice, st));
             ENG_CUDA(cudaMemcpyAsync(s + L.l2, l2.data(), l2.size() * 8, cudaMemcpyHostToDevice, st));
             ENG_CUDA(cudaMemcpyAsync(s + L.scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice, st));
-            if (use_tc_) {
-                std::vector<double> C1t((size_t)L1 * L1), C2t((size_t)L2 * L2);
-                for (int a = 0; a < L1; ++a)
-                    for (int c = 0; c < L1; ++c) C1t[(size_t)a * L1 + c] = C1[(size_t)c * L1 + a];
-                for (int a = 0; a < L2; ++a)
-                    for (int c = 0; c < L2; ++c) C2t[(size_t)a * L2 + c] = C2[(size_t)c * L2 + a];
-                const double* Ms[4] = {C1.data(), C2.data(), C2t.data(), C1t.data()};
-                for (int q = 0; q < 4; ++q) {
-                    const long long nfl = tc_matrix_floats(G.F, G.ax1, G.ax2, q);
-                    if (!nfl) continue;
-                    std::vector<float> arr((size_t)nfl, 0.f);
-                    tc_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], arr.data());
-                    ENG_CUDA(cudaMemcpyAsync(s + L.tc[q], arr.data(), arr.size() * 4, cudaMemcpyHostToDevice, st));
-                    const long long ntn = tcn_matrix_floats(G.F, G.ax1, G.ax2, q);
-                    if (ntn) {
-                        std::vector<float> tn((size_t)ntn, 0.f);
-                        tcn_arrange_matrix(G.F, G.ax1, G.ax2, q, Ms[q], tn.data());
-                        ENG_CUDA(cudaMemcpyAsync(s + L.tn[q], tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
-                    }
-                }
+            for (int q = 0; q < 4; ++q) {
+                if (!T->tc[q].empty())
+                    ENG_CUDA(cudaMemcpyAsync(s + L.tc[q], T->tc[q].data(), T->tc[q].size() * 4, cudaMemcpyHostToDevice, st));
+                if (!T->tn[q].empty())
+                    ENG_CUDA(cudaMemcpyAsync(s + L.tn[q], T->tn[q].data(), T->tn[q].size() * 4, cudaMemcpyHostToDevice, st));
             }
-            if (L.zs_bytes) {
-                std::vector<unsigned char> zsm(L.zs_bytes);
-                zs_arrange(G.F, G.pe, G.ax1, C1.data(), C2.data(), zsm.data());
-                ENG_CUDA(cudaMemcpyAsync(s + L.zs, zsm.data(), zsm.size(), cudaMemcpyHostToDevice, st));
-            }
+            if (L.zs_bytes) ENG_CUDA(cudaMemcpyAsync(s + L.zs, T->zs.data(), T->zs.size(), cudaMemcpyHostToDevice, st));
             count_launch();
             k_init_state<<<256, 256, 0, st>>>(G.nf, E.b, s + L.b32, s + L.z, s + L.u, prec == SAC_MIXED);
             ENG_CUDA(cudaGetLastError());

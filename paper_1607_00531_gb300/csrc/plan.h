@@ -6,6 +6,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <memory>
+#include <vector>
+
 #include "../../include/sac.h"
 #include "sac_dev.cuh"
 #include "sac_launch.h"
@@ -29,6 +32,21 @@ int check_params(const sac_params* p);
 // operator it diagonalises (Sec. 4.2, Eq. dctdiag), computed on the host.
 void dct2_matrix(int L, double* C);
 void neumann_eigs(int L, double h, double* lam);
+
+// Host-side DCT tables that depend on a grid's geometry alone: the DCT-II
+// matrices along ax1 and ax2 (FP64 and FP32) and, when asked for, their
+// arrangements for the per-axis tensor-core passes (tc) and the on-chip
+// z-step (zs).  Computed once and kept for the last eight geometries of the
+// process (rebuilding them, 65,536 cosines for a 256-face axis and then the
+// arranged copies, took longer than many iterations of a solve).
+struct HostTables {
+    long long key[8];
+    std::vector<double> C1, C2;
+    std::vector<float> C1f, C2f;
+    std::vector<float> tc[4], tn[4];   // per pass (empty where unused)
+    std::vector<unsigned char> zs;
+};
+std::shared_ptr<const HostTables> host_tables(const int F[3], int ax1, int ax2, int pe, bool tc, bool zs);
 
 // Device-side layout of a workspace for one volume.
 struct Plan {
