@@ -241,7 +241,11 @@ int sac_zstep(const sac_grid* g, const sac_params* p, const double* b, const dou
    ||b - z|| <= eps_pri and rho h^d ||z^k - z^{k+1}|| <= eps_dual (Eq.
    admmStop, k+1 iterates) or after max_iter iterations.  hist (host, may be
    NULL): 6 doubles per iteration {r_pri, r_dual, eps_pri, eps_dual, rho, 0}.
-   Returns SAC_OK (converged), SAC_ENOTCONV (cap) or an error. */
+   Returns SAC_OK (converged), SAC_ENOTCONV (cap) or an error.  The DCT
+   tables of a grid's geometry are built on the host by the first call for it
+   and kept (for the last eight geometries of the process, shared by all
+   threads and by the batched engine and server), so later calls only copy
+   them into ws. */
 int sac_admm_solve(const sac_grid* g, const sac_params* p, const void* I1, const void* I2,
                    double* b, double* z, double* u, int* iters, double* r_pri, double* r_dual,
                    double* hist, void* ws, size_t ws_bytes, void* stream);
