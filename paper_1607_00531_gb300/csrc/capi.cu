@@ -416,6 +416,7 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
                           0, P->zs_slabs};
     SAC_CUDA(cudaMemcpyAsync(P->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
     SAC_CUDA(cudaMemcpyAsync(P->d_pref_line, pref, sizeof(pref), cudaMemcpyHostToDevice, st));
+    SAC_CUDA(cudaMemsetAsync(P->d_status, 0, 256, st));   // status words and list counters, every upload
     // the tables depend on the geometry and the parameters only: once per plan
     if (P->tables_up) return SAC_OK;
     const int L1 = G.F[G.ax1], L2 = G.F[G.ax2];
@@ -450,7 +451,6 @@ int plan_upload(Plan* P, const sac_params* p, const void* I1, const void* I2, vo
         SAC_CUDA(cudaMemcpyAsync(P->d_lam2f, l2f.data(), l2f.size() * 4, cudaMemcpyHostToDevice, st));
     }
     P->tables_up = 1;
-    SAC_CUDA(cudaMemsetAsync(P->d_status, 0, 256, st));
     // the host copies above read pageable memory: the runtime has consumed it on return
     return SAC_OK;
 }
